@@ -1,0 +1,60 @@
+"""Write the oracle's expected values for the GPU parity tests (calls only oracle/).
+
+    python tests/golden/make_golden.py
+
+Each file records the FP64 oracle flow of one configuration: per step the axis, bond
+dimensions, ln c_n, the ln Z/N estimate, X^(n), the cut gaps and the leading Gram spectra
+(normalised by the largest eigenvalue). A flow whose cut splits a degenerate multiplet
+(gap < 1e-10) is cut-ambiguous from that step on; the file records the first such step.
+"""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import hotrg_ref as R  # noqa: E402
+
+CONFIGS = {
+    # 4D, beta = 0.1497, h = 0, Dcut = 4, 16 steps to 16^4 (the small FP64 configuration)
+    "flow_d4_b0.1497_h0_D4_n16": dict(d=4, beta=0.1497, h=0.0, Dcut=4, nsteps=16),
+    # same at Dcut = 5: no degenerate multiplet at any cut, so every step is comparable
+    "flow_d4_b0.1497_h0_D5_n16": dict(d=4, beta=0.1497, h=0.0, Dcut=5, nsteps=16),
+    # with a field (breaks the Z2 symmetry; h = 1e-6 as in the differentiation scans)
+    "flow_d4_b0.1497_h1e-6_D4_n8": dict(d=4, beta=0.1497, h=1e-6, Dcut=4, nsteps=8),
+    # 2D, Dcut = 8, 40 steps to 2^40 sites
+    "flow_d2_b0.3_h0_D8_n40": dict(d=2, beta=0.3, h=0.0, Dcut=8, nsteps=40),
+}
+
+AMBIGUOUS_GAP = 1e-10
+
+
+def flow_record(cfg):
+    f = R.run(**cfg)
+    steps = []
+    first_ambiguous = None
+    for n in range(cfg["nsteps"]):
+        gaps = {str(b): (None if g == float("inf") else g) for b, g in f.gaps[n].items()}
+        if first_ambiguous is None and any(g is not None and g < AMBIGUOUS_GAP for g in gaps.values()):
+            first_ambiguous = n + 1
+        spec = {}
+        for b, lam in f.spectra[n].items():
+            top = lam[: cfg["Dcut"] + 2]
+            spec[str(b)] = [float(x) for x in (top / lam[0])]
+        steps.append(dict(step=n + 1, axis=f.axes[n], dims=list(f.dims[n]), ln_c=f.ln_c[n + 1],
+                          lnz=f.lnz[n + 1], x=f.x[n], gaps=gaps, spectra=spec))
+    return dict(config=cfg, ln_c0=f.ln_c[0], lnz_final=f.lnz[-1], first_ambiguous_step=first_ambiguous,
+                steps=steps, source="oracle/hotrg_ref.py run(), FP64")
+
+
+def main():
+    for name, cfg in CONFIGS.items():
+        rec = flow_record(cfg)
+        with open(os.path.join(HERE, name + ".json"), "w") as fh:
+            json.dump(rec, fh, indent=1)
+        print(name, rec["lnz_final"], "first ambiguous step:", rec["first_ambiguous_step"])
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix (no GPU).
+
+Each test names the passage of arXiv:1906.06060 it checks. The references used here
+(enumeration, Onsager, transfer matrix, closed forms) are in oracle/exact.py and share no code
+with the tensor-network oracle in oracle/hotrg_ref.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import exact as E
+from oracle import hotrg_ref as R
+from tests.inputs import random_site_tensor
+
+
+# ------------------------------------------------------------------ Sec. 2: T^(0) and W
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("beta,h", [(0.1497, 0.0), (0.44, 0.3), (1.0, -0.2), (0.05, 1e-6)])
+def test_initial_tensor_closed_form(d, beta, h):
+    T = R.initial_tensor(d, beta, h)
+    C = E.initial_tensor_closed_form(d, beta, h)
+    # the oracle sums e^{bh} and -e^{-bh}: odd entries carry its cancellation, so the
+    # tolerance is relative to the largest entry
+    np.testing.assert_allclose(T, C, rtol=1e-14, atol=1e-15 * np.abs(C).max())
+
+
+@pytest.mark.parametrize("beta", [0.01, 0.1497, 0.7])
+def test_bond_weight_factorises_boltzmann_weight(beta):
+    W = R.bond_weight(beta)
+    s = np.array([1.0, -1.0])
+    np.testing.assert_allclose(W @ W.T, np.exp(beta * np.outer(s, s)), rtol=1e-15)
+
+
+# ------------------------------------------------------------------ Eqs. (TNrep), (tTr): exact
+@pytest.mark.parametrize("beta,h", [(0.1497, 0.0), (0.3, 0.01), (0.3, -0.2), (0.8, 0.05)])
+def test_4d_lossless_steps_match_enumeration(beta, h):
+    """After k lossless steps, Eq. (tTr) is Z of a lattice with L_a = 2^{k_a}."""
+    f = R.run(4, beta, h, 16, 2)
+    assert f.dims == [(4, 4, 4, 2), (16, 16, 4, 4)]
+    assert abs(2 * f.lnz[1] - E.lnz_bruteforce(beta, h, (1, 1, 1, 2))) < 1e-13 * 4
+    assert abs(4 * f.lnz[2] - E.lnz_bruteforce(beta, h, (1, 1, 2, 2))) < 1e-13 * 6
+
+
+@pytest.mark.parametrize("beta,h", [(0.2, 0.0), (0.5, 0.1)])
+def test_3d_lossless_steps_match_enumeration(beta, h):
+    f = R.run(3, beta, h, 16, 3)
+    for n, L in [(1, (1, 1, 2)), (2, (1, 2, 2)), (3, (2, 2, 2))]:
+        assert abs(2 ** n * f.lnz[n] - E.lnz_bruteforce(beta, h, L)) < 1e-12
+
+
+@pytest.mark.parametrize("beta,h", [(0.3, 0.0), (0.4407, 0.0), (0.44, 0.05), (0.9, -0.3)])
+def test_2d_4x4_lattice_matches_enumeration(beta, h):
+    """4 lossless steps (Dcut=16) give the periodic 4x4 lattice, 65,536 configurations."""
+    f = R.run(2, beta, h, 16, 4)
+    assert f.dims[-1] == (16, 16)
+    assert abs(16 * f.lnz[4] - E.lnz_bruteforce(beta, h, (4, 4))) < 1e-12
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("beta,h", [(0.1497, 0.0), (0.3, 0.01), (0.3, -0.01)])
+def test_4d_periodic_2to4_lattice_matches_enumeration(beta, h):
+    """The 16-site periodic 2^4 lattice (65,536 configurations): two lossless steps (t, z),
+    then the exact periodic 2x2 contraction in (x, y)."""
+    f = R.run(4, beta, h, 16, 2, keep_tensor=True)
+    L = sum(math.ldexp(c, -k) for k, c in enumerate(f.ln_c))
+    lnz = 16 * L + E.lnz_periodic_2x2_xy(f.tensor)
+    assert abs(lnz - E.lnz_bruteforce(beta, h, (2, 2, 2, 2))) < 1e-12 * 20
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 12, 30])
+@pytest.mark.parametrize("beta,h", [(0.5, 0.1), (1.3, -0.02)])
+def test_1d_chain_matches_transfer_matrix(n, beta, h):
+    f = R.run(1, beta, h, 4, n)
+    assert abs(f.lnz[-1] - E.lnz_1d(beta, h, 2 ** n) / 2 ** n) < 1e-14
+
+
+@pytest.mark.parametrize("d,Dcut", [(2, 3), (3, 4), (4, 3)])
+def test_infinite_temperature_gives_ln2(d, Dcut):
+    f = R.run(d, 0.0, 0.0, Dcut, 4 * d)
+    assert abs(f.lnz[-1] - math.log(2.0)) < 1e-14
+
+
+# ------------------------------------------------------------------ truncated flows
+def test_onsager_forms_agree():
+    for beta in (0.2, 0.3, 0.6):
+        assert abs(E.lnz_onsager(beta) - E.lnz_onsager_double(beta)) < 1e-11
+
+
+@pytest.mark.parametrize("beta", [0.3, 0.6])
+def test_2d_flow_converges_to_onsager(beta):
+    """Off-critical 2D flow: the error against Onsager falls as Dcut grows (the paper's
+    monotone delta f, Sec. 3) and is below 1e-8 at Dcut=16 after 40 steps (2^40 sites)."""
+    errs = [abs(R.run(2, beta, 0.0, D, 40).lnz[-1] - E.lnz_onsager(beta)) for D in (4, 8, 16)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-8
+
+
+def test_4d_high_temperature_series():
+    f = R.run(4, 0.1497, 0.0, 5, 16)
+    assert abs(f.lnz[-1] - E.lnz_high_temperature_4d(0.1497)) < 1e-3
+
+
+def test_field_reversal_symmetry():
+    """Z(h) = Z(-h) (spin-flip symmetry of Eq. (pf))."""
+    a = R.run(4, 0.1497, 0.01, 5, 8)
+    b = R.run(4, 0.1497, -0.01, 5, 8)
+    assert abs(a.lnz[-1] - b.lnz[-1]) < 1e-13 * abs(a.lnz[-1])
+
+
+def test_axis_order_invariance():
+    """T^(0) is isotropic, so any axis cycle gives the same flow (relabelled axes)."""
+    a = R.run(4, 0.1497, 0.0, 5, 8, order=[3, 2, 1, 0])
+    b = R.run(4, 0.1497, 0.0, 5, 8, order=[0, 1, 2, 3])
+    assert abs(a.lnz[-1] - b.lnz[-1]) < 1e-13
+
+
+def test_normalisation_invariance():
+    """Isometries are scale-invariant, so the ln Z estimate does not depend on the norm used."""
+    a = R.run(4, 0.1497, 0.0, 5, 8)
+    b = R.run(4, 0.1497, 0.0, 5, 8, norm=lambda T: float(np.max(np.abs(T))))
+    assert abs(a.lnz[-1] - b.lnz[-1]) < 1e-13
+
+
+def test_isometries_orthonormal_and_left_right_spectra_equal():
+    T = R.initial_tensor(4, 0.1497, 0.0)
+    T /= R.frobenius(T)
+    for a in (3, 2, 1):
+        for b in range(4):
+            if b == a:
+                continue
+            G = R.gram(T, a, b)
+            Gp = R.gram(T, a, b, side="primed")
+            l1, l2 = np.linalg.eigvalsh(G), np.linalg.eigvalsh(Gp)
+            np.testing.assert_allclose(l1, l2, rtol=1e-12, atol=1e-14 * l1.max())
+            iso = R.isometry_from_gram(G, T.shape[b], 5)
+            U = iso.U.reshape(-1, iso.chi)
+            np.testing.assert_allclose(U.T @ U, np.eye(iso.chi), atol=1e-13)
+        T, _ = R.coarse_grain(T, a, 5)
+        T /= R.frobenius(T)
+
+
+# ------------------------------------------------------------------ contraction pins (random)
+@pytest.mark.parametrize("d,dims,a", [(2, (3, 2), 1), (3, (2, 3, 2), 0), (4, (2, 2, 3, 2), 3),
+                                      (4, (3, 2, 2, 2), 1)])
+def test_gram_half_contractions_match_two_site_unfolding(d, dims, a):
+    T = random_site_tensor(dims, seed=d * 10 + a)
+    M = R.two_site_tensor(T, T, a)
+    # position of (b1, b2) in M's unprimed block
+    pos = 0
+    for b in range(d):
+        if b == a:
+            pos += 1
+            continue
+        X = np.moveaxis(M, (pos, pos + 1), (0, 1)).reshape(dims[b] ** 2, -1)
+        np.testing.assert_allclose(R.gram(T, a, b), X @ X.T, rtol=1e-12, atol=1e-12)
+        pos += 2
+
+
+@pytest.mark.parametrize("Dcut", [2, 3])
+def test_isometry_keeps_the_dominant_subspace(Dcut):
+    """U spans the top-chi eigenvectors: the weight it keeps equals the sum of kept
+    eigenvalues, computed on the explicit two-site tensor."""
+    dims, a, b = (2, 2, 2, 2), 3, 1
+    T = random_site_tensor(dims, seed=7)
+    M = R.two_site_tensor(T, T, a)
+    X = np.moveaxis(M, (2, 3), (0, 1)).reshape(4, -1)
+    iso = R.isometry_from_gram(R.gram(T, a, b), 2, Dcut)
+    kept = np.linalg.norm(iso.U.reshape(4, -1).T @ X) ** 2
+    assert abs(kept - iso.eigenvalues[:iso.chi].sum()) < 1e-11 * kept
+    assert np.all(np.diff(iso.eigenvalues) <= 0)
+
+
+@pytest.mark.parametrize("d,dims,a,Dcut", [(2, (3, 2), 1, 4), (2, (3, 3), 0, 5), (3, (2, 3, 2), 0, 3),
+                                           (4, (2, 2, 2, 2), 3, 3), (4, (2, 3, 2, 2), 1, 4),
+                                           (4, (3, 2, 2, 3), 0, 16)])
+def test_sliced_squeeze_matches_whole_network(d, dims, a, Dcut):
+    T = random_site_tensor(dims, seed=100 + d + a)
+    U = {}
+    for b in range(d):
+        if b != a:
+            U[b] = R.isometry_from_gram(R.gram(T, a, b), dims[b], Dcut).U
+    np.testing.assert_allclose(R.squeeze(T, T, a, U), R.squeeze_direct(T, T, a, U),
+                               rtol=1e-12, atol=1e-12)
+    # distinct site tensors too (the contraction must not rely on T1 == T2)
+    T2 = random_site_tensor(dims, seed=200 + d + a)
+    np.testing.assert_allclose(R.squeeze(T, T2, a, U), R.squeeze_direct(T, T2, a, U),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_x_indicator_phases():
+    """X^(n) -> 1 in the disordered and -> 2 in the ordered phase (Sec. 3, Eq. (x))."""
+    hot = R.run(4, 0.10, 0.0, 4, 24)
+    cold = R.run(4, 0.25, 0.0, 4, 24)
+    assert abs(hot.x[-1] - 1.0) < 1e-3
+    assert abs(cold.x[-1] - 2.0) < 1e-3
+
+
+def test_dims_schedule_reaches_dcut_at_step_3():
+    assert R.dims_schedule(4, 10, 4) == [[2, 2, 2, 2], [4, 4, 4, 2], [10, 10, 4, 4],
+                                         [10, 10, 10, 10], [10, 10, 10, 10]]
+    assert R.squeeze_flops([10] * 4, 0, 10) == pytest.approx(2e15)
+
+
+# ------------------------------------------------------------------ planted mistakes
+def test_planted_mistakes_are_caught(monkeypatch):
+    """A dropped weight, a transposed operand or a wrong leg must fail one of the pins above."""
+    beta, h = 0.3, 0.01
+    ref = E.lnz_bruteforce(beta, h, (1, 1, 2, 2))
+
+    # (1) dropped 2^{-n} weight on ln c_n
+    orig_ldexp = R.math.ldexp
+    monkeypatch.setattr(R.math, "ldexp", lambda x, n: x)
+    bad = R.run(4, beta, h, 16, 2)
+    monkeypatch.setattr(R.math, "ldexp", orig_ldexp)
+    assert abs(4 * bad.lnz[2] - ref) > 1e-3
+
+    # (2) second site's tensor transposed (u <-> p) in the squeeze: caught by the random pin
+    T = random_site_tensor((2, 3, 2, 2), seed=5)
+    d = 4
+    Tt = np.transpose(T, list(range(d, 2 * d)) + list(range(d)))
+    U = {b: R.isometry_from_gram(R.gram(T, 1, b), T.shape[b], 4).U for b in (0, 2, 3)}
+    assert not np.allclose(R.squeeze(T, Tt, 1, U), R.squeeze_direct(T, T, 1, U), atol=1e-6)
+
+    # (3) Gram half-contraction on the wrong leg of site 1 (u_a instead of p_a)
+    Tr = random_site_tensor((2, 2, 3, 2), seed=6)
+    good = R.gram(Tr, 3, 1)
+    Q1 = R.half_gram(Tr, 1, 3)
+    Q2 = R.half_gram(Tr, 1, 3)
+    wrong = np.einsum("ikab,jlab->ijkl", Q1, Q2).reshape(4, 4)
+    assert not np.allclose(wrong, good, rtol=1e-6)
