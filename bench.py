@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the 4D HOTRG coarse-graining step (arXiv:1906.06060, Sec. 2) on GB300.
+
+Workload: 4D Ising, beta = 0.1497, h = 0, Dcut = 10 (the 40-step flow to 1024^4). A bench
+"step" is one coarse-graining step of the whole path (Gram matrices, eigensolver, operand
+construction, squeeze GEMM, epilogue, norm/ln accumulation). W warm-up steps (W >= 3 reaches
+the steady-state bond dimensions 10^4) run untimed, then K steady-state steps are timed with CUDA
+events on the library's stream. Metric: algorithmic TFLOP/s of the squeeze (2 prod(chi_b) P^3
+per step = 2 Dcut^15 at steady state; split-precision extra passes are not counted).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|bf16x6|fp64]
+    python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
+
+Multi-GPU (torchrun, one process per GPU): the single-flow workload does not shard, so each rank
+runs an independent replica; value = total flops of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4D HOTRG TFLOP/s & % tensor peak at Dcut=10, mixed vs FP64, |Δf/f|≤1e-7"
+GEMM_SRC = os.path.join(ROOT, "paper_1906_06060_gb300", "csrc", "gemm_tc.cu")
+PROFILE = os.path.join(ROOT, "profiles", "ncu_squeeze_gemm_dcut10_summary.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6", "fp64"])
+    ap.add_argument("--x6-steps", type=int, default=0)
+    ap.add_argument("--dcut", type=int, default=10)
+    ap.add_argument("--beta", type=float, default=0.1497)
+    ap.add_argument("--h", type=float, default=0.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-slices", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"4D Ising HOTRG, beta={a.beta}, h={a.h}, Dcut={a.dcut}: steady-state "
+                        f"coarse-graining steps (bond dims {a.dcut}^4) of the 40-step flow to 1024^4",
+            "d": 4, "Dcut": a.dcut, "beta": a.beta, "h": a.h, "precision": a.precision,
+            "x6_steps": a.x6_steps,
+            "l2": "inputs larger than L2 (T 800 MB fp64, GEMM operands several GB per step)",
+            "parallelism": "replicas" if a.gpus > 1 else "single GPU"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def steady_flops(dcut):
+    return 2.0 * float(dcut) ** 15
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(dcut, slices):
+    """Time the FP64 oracle's squeeze on `slices` slices of a steady-state step (random T with
+    bond dims dcut^4 and random orthonormal isometries: the cost does not depend on the values).
+    Returns (seconds, algorithmic flops)."""
+    import numpy as np
+    from oracle import hotrg_ref as R
+    rng = np.random.default_rng(0)
+    D = dcut
+    T = rng.standard_normal((D,) * 8)
+    T /= np.linalg.norm(T)
+    U = {}
+    for b in (1, 2, 3):
+        q, _ = np.linalg.qr(rng.standard_normal((D * D, D)))
+        U[b] = q.reshape(D, D, D)
+    t0 = time.perf_counter()
+    R.squeeze(T, T, 0, U, max_slices=slices)
+    dt = time.perf_counter() - t0
+    return dt, slices * 2.0 * float(D) ** 12
+
+
+def cpu_threads():
+    return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return None
+    for _ in range(a.warmup):
+        oracle_sample(a.dcut, a.cpu_slices)
+    times, flops = [], 0.0
+    for _ in range(a.steps):
+        dt, f = oracle_sample(a.dcut, a.cpu_slices)
+        times.append(dt)
+        flops += f
+    total = sum(times)
+    value = flops / total / 1e12
+    sample = (f"{a.cpu_slices} slice(s) of one steady-state Dcut={a.dcut} squeeze per step "
+              f"(2 Dcut^12 flops each), oracle/hotrg_ref.py squeeze(), FP64 NumPy/BLAS")
+    return {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def traffic_from_profile():
+    """Per-launch DRAM bytes of the squeeze GEMM from the committed ncu summary, valid only if
+    the kernel source is unchanged since the capture."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(GEMM_SRC, "rb").read()).hexdigest()[:16]
+    kv = {}
+    for line in text.splitlines():
+        if "=" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("gemm_tc_sha") != sha:
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(a, rank, world, dist):
+    import torch
+    from paper_1906_06060_gb300 import HOTRG
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    kw = dict(precision=a.precision, fp64_steps=2, x6_steps=a.x6_steps, stream=stream)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    flow = HOTRG(4, a.beta, a.h, a.dcut, **kw)
+    for _ in range(a.warmup):
+        flow.step()
+    flow.free_energy()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    flow.timing_start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        ev0.record(stream)
+        for _ in range(a.steps):
+            flow.step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    t = flow.timing_stop()
+    ms = ev0.elapsed_time(ev1)
+    lnz = flow.free_energy()[0][0]
+    flow.close()
+    step_flops = t["step_flops"]
+    # max time over ranks, total flops over ranks
+    if dist:
+        buf = torch.tensor([ms, step_flops], dtype=torch.float64, device=dev)
+        mx = buf.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = buf.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, flops_all = float(mx[0]), float(sm[1])
+    else:
+        ms_max, flops_all = ms, step_flops
+    if rank != 0:
+        return None
+    value = flops_all / (ms_max * 1e-3) / 1e12
+    pk, src = peaks()
+    gemm_ms = t["ms_gemm"] / max(1, t["gemm_launches"])
+    achieved = (t["gemm_flops"] / max(1, t["gemm_launches"])) / (gemm_ms * 1e-3) / 1e12
+    peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic_from_profile(),
+            "peak_source": f"{src} bf16 sustained (kernel timed inside long steps)",
+            "kernel": "k_gemm_split (tcgen05 squeeze GEMM)" if a.precision != "fp64" else "k_gemm_f64",
+            "tensor_pipe_tflops": (t["gemm_tensor_flops"] / max(1, t["gemm_launches"])) / (gemm_ms * 1e-3) / 1e12,
+            "note": "achieved counts algorithmic flops (2MNK) only; the split passes multiply tensor work "
+                    "by 3 (bf16x3) or 6 (bf16x6)"}
+    if a.precision == "fp64":
+        roof.update({"bound": "alu", "peak": 1.25, "peak_source": "nominal GB300 FP64 rate",
+                     "frac": achieved / 1.25})
+    out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "bf16",
+           "data": "synthetic", "config": workload_config(a),
+           "steps_per_s": a.steps / (ms_max * 1e-3), "roofline": roof,
+           "phases_ms_per_step": {k[3:]: v / a.steps for k, v in t.items() if k.startswith("ms_")},
+           "gpu_launches": int(t["kernel_launches"]), "lnz_per_site_after": lnz}
+    out["clocks"] = clk.summary()
+    return out
+
+
+def e2e(a):
+    """Same metric through the public API from host inputs: context creation (beta, h copied
+    from host), W + K steps with the free energy read back to the host after every step."""
+    import torch
+    from paper_1906_06060_gb300 import HOTRG
+    torch.cuda.synchronize()
+    nsteps = a.warmup + a.steps
+    t0 = time.perf_counter()
+    flow = HOTRG(4, a.beta, a.h, a.dcut, precision=a.precision, fp64_steps=2, x6_steps=a.x6_steps)
+    flops = 0.0
+    dims = [2, 2, 2, 2]
+    for n in range(nsteps):
+        ax = 3 - (n % 4)
+        P = math.prod(dims)
+        chi = [min(dims[b] ** 2, a.dcut) for b in range(4) if b != ax]
+        flops += 2.0 * math.prod(chi) * P ** 3
+        dims = [dims[b] if b == ax else min(dims[b] ** 2, a.dcut) for b in range(4)]
+        flow.step()
+        flow.free_energy()
+    dt = time.perf_counter() - t0
+    flow.close()
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16.0 / nsteps,
+            "d2h_bytes_per_step": 3 * 8 + 4, "steps": nsteps,
+            "note": "wall clock: context creation + every step + host read of ln Z/N after each step"}
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        td.init_process_group("nccl" if a.impl == "ours" else "gloo")
+        dist = td
+    if a.impl == "reference":
+        out = run_reference(a, rank, world)
+        if out:
+            print(json.dumps(out))
+        if dist:
+            dist.destroy_process_group()
+        return
+    if a.warmup < 3:
+        print("warm-up must be >= 3 steps", file=sys.stderr)
+        sys.exit(2)
+    from paper_1906_06060_gb300 import build
+    build.build()
+    out = run_ours(a, rank, world, dist)
+    if out is not None:
+        if not a.no_e2e:
+            out["e2e"] = e2e(a)
+        if not a.no_cpu_baseline and world == 1:
+            dt, f = oracle_sample(a.dcut, a.cpu_slices)
+            out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_threads(),
+                                   "kind": "oracle",
+                                   "sample": f"{a.cpu_slices} slice(s) of one steady-state Dcut={a.dcut} "
+                                             f"squeeze (2 Dcut^12 flops each, {dt:.1f} s), FP64 NumPy/BLAS"}
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

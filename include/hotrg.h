@@ -1,0 +1,194 @@
+/*
+ * hotrg.h - C ABI of the GB300 HOTRG coarse-graining library (libhotrg.so).
+ *
+ * The library computes the higher-order tensor renormalisation group flow of the
+ * d-dimensional Ising model (d = 1..4) as used in arXiv:1906.06060:
+ *   Sec. 2, Eq. (pf)        partition function Z_N = sum_s prod_<ij> e^{b s_i s_j} prod_i e^{b h s_i}
+ *   Sec. 2, after Eq. (pf)  initial site tensor T^(0) = sum_s V_s prod_{2d legs} W[s, leg], W = U sqrt(L)
+ *   Sec. 2, Eqs. (SS),(ST) with S -> T   one coarse-graining step (isometries + squeeze)
+ *   Sec. 2, Eq. (tTr)       periodic trace of the coarse-grained tensor
+ *   Sec. 3, Eqs. (matA),(x) the degeneracy indicator X^(n)
+ * Normalisation (not written in the paper): c_n = ||T^(n)||_F, T <- T / c_n and
+ *   ln Z_N / N = sum_{k=0}^{n} 2^{-k} ln c_k + 2^{-n} ln Tr T^(n),   N = 2^n sites.
+ *
+ * Tensor layout used everywhere in this ABI ("natural layout"): a site tensor of a
+ * d-dimensional lattice is a row-major array T[u_0..u_{d-1}, p_0..p_{d-1}], where u_b is the
+ * leg towards the lower neighbour along axis b (x=0, y=1, z=2, t=3) and p_b the leg towards the
+ * upper one. Both legs of axis b have the same bond dimension D_b. P = prod_b D_b.
+ *
+ * Conventions
+ *  - Every int-returning function returns 0 (HOTRG_OK) or a negative hotrg_status; none aborts.
+ *  - A context's first error is sticky: later calls on it return the same code.
+ *  - Calls are ordered on the context's CUDA stream. hotrg_step only enqueues work; query
+ *    functions (free energy, observables, spectra, get_tensor) synchronise that stream.
+ *  - The library never allocates device memory: the caller passes one device workspace of at
+ *    least hotrg_workspace_size() bytes (256-byte aligned) and keeps it alive until
+ *    hotrg_destroy. Host pointers passed in are only accessed during the call.
+ *  - One context must not be used from two host threads at once.
+ */
+#ifndef HOTRG_H_
+#define HOTRG_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hotrg_status {
+  HOTRG_OK = 0,
+  HOTRG_EINVAL = -1,   /* bad argument: d, beta, Dcut, axis, sizes, null pointer */
+  HOTRG_ENOMEM = -2,   /* workspace smaller than hotrg_workspace_size() */
+  HOTRG_ENUMERIC = -3, /* NaN/Inf or zero norm, or Tr T <= 0 */
+  HOTRG_ENOCONV = -4,  /* eigensolver did not converge within its sweep limit */
+  HOTRG_ETIMEOUT = -5, /* a bounded device-side wait gave up */
+  HOTRG_EDEVICE = -6,  /* CUDA runtime/driver error, or no sm_103 device */
+  HOTRG_ESTATE = -7,   /* call not valid in the context's state (e.g. step log full) */
+  HOTRG_ENOTSUP = -8   /* valid request that this build does not provide */
+} hotrg_status;
+
+typedef enum hotrg_precision {
+  HOTRG_FP64 = 0,   /* every contraction in FP64 on the CUDA cores */
+  HOTRG_BF16X3 = 1, /* squeeze GEMM on tcgen05 tensor cores with split operands x = hi + lo
+                       (bf16 each); products hi*hi + hi*lo + lo*hi accumulate in FP32 (TMEM):
+                       O(2^-16) relative error per product. Gram matrices, eigensolver, norms
+                       and ln sums stay FP64; other intermediates are FP32. */
+  HOTRG_BF16X6 = 2  /* as BF16X3 with three planes x = hi + mid + lo and the six products
+                       hh, hm, mh, hl, mm, lh: O(2^-24) per product, twice the tensor work */
+} hotrg_precision;
+
+typedef struct hotrg_opts {
+  int precision;          /* hotrg_precision (default HOTRG_FP64) */
+  int fp64_steps;         /* in BF16X3/X6 modes the first fp64_steps steps run in FP64 (default 2) */
+  int x6_steps;           /* in BF16X3 mode, steps fp64_steps+1 .. x6_steps use the 6-pass GEMM
+                             (the early steps weigh 2^-n in ln Z/N; default 0) */
+  int batch;              /* independent (beta, h) instances in the context (default 1) */
+  const double *beta;     /* [batch] host array; NULL: all instances use the beta argument */
+  const double *h;        /* [batch] host array; NULL: all instances use the h argument */
+  void *stream;           /* cudaStream_t for all work; NULL = legacy default stream */
+  void *workspace;        /* device pointer, >= hotrg_workspace_size() bytes, 256-B aligned */
+  size_t workspace_bytes;
+  int max_steps;          /* capacity of the per-step logs, 1..64 (default 64) */
+  double wait_timeout_s;  /* bound on any device-side spin wait, seconds (default 4) */
+} hotrg_opts;
+
+typedef struct hotrg_obs {
+  int steps;              /* coarse-graining steps done */
+  int last_axis;          /* axis of the last step (-1 if none) */
+  double lnz_per_site;    /* ln Z_N / N estimate after the last step, N = 2^steps */
+  double last_ln_c;       /* ln c_n of the last step */
+  double x_indicator;     /* X^(n) of Eq. (x) along the last axis (1 for steps == 0) */
+} hotrg_obs;
+
+typedef struct hotrg_ctx hotrg_ctx;
+
+/* Fill *o with the defaults listed in hotrg_opts. */
+void hotrg_opts_default(hotrg_opts *o);
+
+/* Bytes of device workspace for a context of dimension d (1..4) and bond cut Dcut (2..16) with
+ * the given options (precision, batch and max_steps are read; NULL means defaults).
+ * Errors: EINVAL for d or Dcut out of range, batch < 1, or bytes == NULL. */
+int hotrg_workspace_size(int d, int Dcut, const hotrg_opts *opt, size_t *bytes);
+
+/* Create a context (Sec. 2): builds T^(0) = sum_s V_s prod W[s, leg] for every instance on the
+ * device, normalises it (c_0) and starts the ln Z accumulator at ln c_0.
+ * beta > 0 and finite, h finite (per instance when opt->beta / opt->h are given).
+ * *out receives a host object freed by hotrg_destroy; the workspace stays caller-owned.
+ * Errors: EINVAL (d not in 1..4, Dcut not in 2..16, bad beta/h, batch < 1, opt NULL),
+ * ENOMEM (workspace too small or misaligned), EDEVICE (no sm_103 device / CUDA error). */
+int hotrg_init(hotrg_ctx **out, int d, double beta, double h, int Dcut, const hotrg_opts *opt);
+
+/* One coarse-graining step along `axis` (0..d-1), or the next axis of the cycle t,z,y,x
+ * (d-1 .. 0) when axis == -1 (Sec. 2, Eqs. (SS),(ST) with S -> T, for every instance):
+ *   1. Gram matrices G_b of the two-site unfolding for each transverse axis b (FP64),
+ *   2. symmetric eigendecomposition, keep chi_b = min(D_b^2, Dcut) leading eigenvectors,
+ *      each sign-fixed so that its largest-magnitude component is positive,
+ *   3. squeeze T' = U..U (T T) U..U (the O(Dcut^15) contraction),
+ *   4. c_n = ||T'||_F, T <- T'/c_n, ln Z accumulator += 2^{-n} ln c_n.
+ * Enqueues work on the stream and returns. Errors: EINVAL (axis), ESTATE (log full). */
+int hotrg_step(hotrg_ctx *c, int axis);
+
+/* ln Z_N / N = accumulator + 2^{-n} ln Tr T^(n) (Eq. (tTr)) and f = -(ln Z_N / N) / beta, one
+ * value per instance written to the caller's host arrays (either may be NULL). Synchronises.
+ * Errors: ENUMERIC (Tr T <= 0), and any sticky device error. */
+int hotrg_free_energy(hotrg_ctx *c, double *lnz_per_site, double *f_per_site);
+
+/* Observables of instance `instance` after the last step (see hotrg_obs). Synchronises. */
+int hotrg_observables(hotrg_ctx *c, int instance, hotrg_obs *out);
+
+/* Eigenvalues (descending, all D_b^2 of them) of the Gram matrix G_axis of step `step`
+ * (1-based) of instance `instance`, copied to buf[0..cap). *n_out = number available (0 if
+ * `axis` was the step's own axis). Synchronises. Errors: EINVAL (step/axis/instance). */
+int hotrg_spectra(hotrg_ctx *c, int step, int axis, int instance, double *buf, int cap, int *n_out);
+
+/* ln c_n of steps 0..steps of `instance` (n_out = steps + 1 values). Synchronises. */
+int hotrg_ln_norms(hotrg_ctx *c, int instance, double *buf, int cap, int *n_out);
+
+/* Current bond dimensions (d ints) and the normalised tensor of `instance` in natural layout
+ * (P^2 doubles) copied to host memory; `host` may be NULL to query dims only. Synchronises.
+ * Errors: EINVAL (cap < P^2 when host != NULL). */
+int hotrg_get_tensor(hotrg_ctx *c, int instance, int *dims, double *host, size_t cap);
+
+/* Replace the tensor of `instance` by a host array in natural layout with bond dimensions
+ * dims[0..d) (each 1..Dcut). Used to coarse-grain arbitrary tensors. It does not normalise and
+ * does not touch the ln Z accumulator. Errors: EINVAL. */
+int hotrg_set_tensor(hotrg_ctx *c, int instance, const int *dims, const double *host);
+
+/* Checkpoint: size of, save to and restore from a host buffer holding the full flow state
+ * (tensors, dims, accumulators, step logs). load requires a context created with the same
+ * d, Dcut, batch and precision. Synchronise. Errors: EINVAL (size/format mismatch). */
+int hotrg_state_size(hotrg_ctx *c, size_t *bytes);
+int hotrg_state_save(hotrg_ctx *c, void *host, size_t cap);
+int hotrg_state_load(hotrg_ctx *c, const void *host, size_t size);
+
+/* Phase timing, for benchmarks: after hotrg_timing_start, every phase the context enqueues is
+ * bracketed by CUDA events on its stream; hotrg_timing_stop synchronises and returns the summed
+ * event durations (ms) and work counters since the start. Timing adds two event records per
+ * phase and per GEMM launch. */
+typedef struct hotrg_timing {
+  double ms_step;           /* whole steps */
+  double ms_isometry;       /* Gram matrices and eigensolver */
+  double ms_operands;       /* GEMM operand construction: transposes, mode products, splits */
+  double ms_gemm;           /* squeeze GEMM launches */
+  double ms_epilogue;       /* primed-side isometry contractions into the new tensor */
+  double ms_norm;           /* norm, scale, trace, X^(n) */
+  long long steps;          /* steps taken (per instance count: batch x steps in step_flops) */
+  long long gemm_launches;  /* squeeze GEMM kernels launched */
+  long long kernel_launches;/* all library kernels launched in this process since start */
+  double gemm_flops;        /* algorithmic flops of those GEMMs, 2 M N K each */
+  double gemm_tensor_flops; /* flops the tensor pipe executed (x 3 or x 6 split passes) */
+  double step_flops;        /* algorithmic squeeze flops of the steps, 2 prod(chi_b) P^3 */
+} hotrg_timing;
+
+int hotrg_timing_start(hotrg_ctx *c);
+int hotrg_timing_stop(hotrg_ctx *c, hotrg_timing *out);
+
+/* Release the context's host object. The workspace is not touched. NULL is a no-op. */
+void hotrg_destroy(hotrg_ctx *c);
+
+/* Static description of a status code. */
+const char *hotrg_strerror(int code);
+
+/* ---------------------------------------------------------------------------------------
+ * Kernel-level entry point: the squeeze GEMM of the split-precision paths on its own (Sec. 2
+ * cost statement: the O(Dcut^15) contraction is this GEMM), for tests and benchmarks.
+ *   C[m][n] = sum_k A[m][k] * Bt[n][k],  m < M, n < N, k < K   (M >= 128, N >= 256, K >= 64)
+ * A (M x lda floats, row-major) and Bt (N x ldb floats, row-major) are device FP32 arrays that
+ * are split into bf16 planes in `scratch` (device, >= hotrg_gemm_scratch_bytes(M,N,K) bytes,
+ * 256-B aligned) before the tcgen05 GEMM; C is device FP32 with leading dimension ldc.
+ * npass: 1 = hi*hi only, 3 = BF16X3 products, 6 = BF16X6 products. Enqueued on `stream`; not
+ * synchronised. Errors: EINVAL (sizes, npass, alignment), EDEVICE. */
+size_t hotrg_gemm_scratch_bytes(long long M, long long N, long long K);
+int hotrg_gemm_split(const float *A, long long lda, const float *Bt, long long ldb, float *C,
+                     long long ldc, long long M, long long N, long long K, int npass,
+                     void *scratch, size_t scratch_bytes, void *stream);
+
+/* Status of the last hotrg_gemm_split call that used `scratch` (0 = ok, HOTRG_ETIMEOUT if a
+ * pipeline wait of the GEMM kernel gave up). The word lives in the first bytes of scratch and
+ * is cleared by each GEMM call. Synchronises `stream`. */
+int hotrg_gemm_status(const void *scratch, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,199 @@
+"""GB300 (sm_103a) HOTRG coarse-graining of the d-dimensional Ising model (arXiv:1906.06060).
+
+Every step of the flow runs in libhotrg.so (hand-written CUDA); this module only marshals
+arguments and provides device memory and streams through PyTorch.
+
+    from paper_1906_06060_gb300 import HOTRG
+    with HOTRG(d=4, beta=0.1497, h=0.0, Dcut=10, precision="bf16x3") as flow:
+        for _ in range(40):
+            flow.step()
+        lnz, f = flow.free_energy()
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_int, c_size_t, c_void_p
+
+import numpy as np
+
+from . import _lib
+from ._lib import HOTRG_BF16X3, HOTRG_BF16X6, HOTRG_FP64, HotrgError, check
+
+__all__ = ["HOTRG", "HotrgError", "gemm_split", "workspace_bytes", "PRECISIONS"]
+
+PRECISIONS = {"fp64": HOTRG_FP64, "bf16x3": HOTRG_BF16X3, "bf16x6": HOTRG_BF16X6}
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libhotrg needs a CUDA device (GB300, sm_103a); there is no CPU path")
+    return torch
+
+
+def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0):
+    lib = _lib.load()
+    o = _lib.Opts()
+    lib.hotrg_opts_default(byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.batch = int(batch)
+    o.fp64_steps = int(fp64_steps)
+    o.x6_steps = int(x6_steps)
+    o.max_steps = int(max_steps)
+    o.wait_timeout_s = float(wait_timeout_s)
+    return o
+
+
+def workspace_bytes(d: int, Dcut: int, precision="fp64", batch: int = 1, fp64_steps: int = 2,
+                    max_steps: int = 64, x6_steps: int = 0) -> int:
+    o = _opts(precision, batch, fp64_steps, max_steps, x6_steps=x6_steps)
+    n = c_size_t(0)
+    check(_lib.load().hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
+    return int(n.value)
+
+
+class HOTRG:
+    """One HOTRG flow context (or a batch of independent (beta, h) instances).
+
+    beta, h: scalars, or sequences of equal length `batch` for a temperature/field scan.
+    precision: "fp64", "bf16x3" or "bf16x6" (tensor-core squeeze with split operands);
+    fp64_steps / x6_steps: precision schedule of the split modes (see include/hotrg.h).
+    """
+
+    def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
+                 max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0):
+        torch = _torch()
+        lib = _lib.load()
+        betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))
+        hs = np.atleast_1d(np.asarray(h, dtype=np.float64))
+        batch = max(betas.size, hs.size)
+        if betas.size == 1:
+            betas = np.full(batch, betas[0])
+        if hs.size == 1:
+            hs = np.full(batch, hs[0])
+        if betas.size != batch or hs.size != batch:
+            raise ValueError("beta and h must be scalars or of equal length")
+        self.d, self.Dcut, self.batch, self.precision = d, Dcut, batch, precision
+        self.beta = betas
+        self.h = hs
+        o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps)
+        n = c_size_t(0)
+        check(lib.hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ws = torch.empty(int(n.value), dtype=torch.uint8, device=self.stream.device)
+        self._beta_buf = (c_double * batch)(*betas)
+        self._h_buf = (c_double * batch)(*hs)
+        o.beta = ctypes.cast(self._beta_buf, ctypes.POINTER(c_double))
+        o.h = ctypes.cast(self._h_buf, ctypes.POINTER(c_double))
+        o.stream = c_void_p(self.stream.cuda_stream)
+        o.workspace = c_void_p(self._ws.data_ptr())
+        o.workspace_bytes = int(n.value)
+        self._ctx = c_void_p()
+        check(lib.hotrg_init(byref(self._ctx), d, float(betas[0]), float(hs[0]), Dcut, byref(o)), "hotrg_init")
+
+    # -- flow ---------------------------------------------------------------------------------
+    def step(self, axis: int = -1) -> None:
+        check(_lib.load().hotrg_step(self._ctx, int(axis)), "hotrg_step")
+
+    def free_energy(self):
+        """(ln Z/N, f) per instance as numpy arrays."""
+        lnz = (c_double * self.batch)()
+        f = (c_double * self.batch)()
+        check(_lib.load().hotrg_free_energy(self._ctx, lnz, f), "hotrg_free_energy")
+        return np.array(lnz[:]), np.array(f[:])
+
+    def observables(self, instance: int = 0) -> dict:
+        ob = _lib.Obs()
+        check(_lib.load().hotrg_observables(self._ctx, int(instance), byref(ob)), "hotrg_observables")
+        return {k: getattr(ob, k) for k, _ in _lib.Obs._fields_}
+
+    def spectra(self, step: int, axis: int, instance: int = 0) -> np.ndarray:
+        buf = (c_double * 256)()
+        n = c_int(0)
+        check(_lib.load().hotrg_spectra(self._ctx, step, axis, instance, buf, 256, byref(n)), "hotrg_spectra")
+        return np.array(buf[: n.value])
+
+    def ln_norms(self, instance: int = 0) -> np.ndarray:
+        buf = (c_double * 65)()
+        n = c_int(0)
+        check(_lib.load().hotrg_ln_norms(self._ctx, instance, buf, 65, byref(n)), "hotrg_ln_norms")
+        return np.array(buf[: n.value])
+
+    def dims(self) -> tuple:
+        dims = (c_int * 4)()
+        check(_lib.load().hotrg_get_tensor(self._ctx, 0, dims, None, 0), "hotrg_get_tensor")
+        return tuple(dims[: self.d])
+
+    def get_tensor(self, instance: int = 0) -> np.ndarray:
+        dims = self.dims()
+        out = np.empty(dims + dims, dtype=np.float64)
+        check(_lib.load().hotrg_get_tensor(self._ctx, instance, None,
+                                           out.ctypes.data_as(ctypes.POINTER(c_double)), out.size),
+              "hotrg_get_tensor")
+        return out
+
+    def set_tensor(self, T: np.ndarray, instance: int = 0) -> None:
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        if T.ndim != 2 * self.d:
+            raise ValueError("tensor rank must be 2d")
+        dims = (c_int * 4)(*T.shape[: self.d])
+        check(_lib.load().hotrg_set_tensor(self._ctx, instance, dims,
+                                           T.ctypes.data_as(ctypes.POINTER(c_double))), "hotrg_set_tensor")
+
+    def state_save(self) -> bytes:
+        lib = _lib.load()
+        n = c_size_t(0)
+        check(lib.hotrg_state_size(self._ctx, byref(n)), "hotrg_state_size")
+        buf = ctypes.create_string_buffer(n.value)
+        check(lib.hotrg_state_save(self._ctx, buf, n.value), "hotrg_state_save")
+        return buf.raw
+
+    def state_load(self, blob: bytes) -> None:
+        check(_lib.load().hotrg_state_load(self._ctx, blob, len(blob)), "hotrg_state_load")
+
+    def timing_start(self) -> None:
+        check(_lib.load().hotrg_timing_start(self._ctx), "hotrg_timing_start")
+
+    def timing_stop(self) -> dict:
+        t = _lib.Timing()
+        check(_lib.load().hotrg_timing_stop(self._ctx, byref(t)), "hotrg_timing_stop")
+        return {k: getattr(t, k) for k, _ in _lib.Timing._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            _lib.load().hotrg_destroy(self._ctx)
+            self._ctx = None
+            self._ws = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_split(A, Bt, npass: int = 3, C=None, stream=None):
+    """C = A @ Bt^T through the tcgen05 kernel (A: M x K, Bt: N x K, float32 CUDA tensors);
+    npass 1 / 3 / 6 selects hi*hi, BF16X3 or BF16X6 products."""
+    torch = _torch()
+    lib = _lib.load()
+    assert A.dtype == torch.float32 and Bt.dtype == torch.float32 and A.is_cuda and Bt.is_cuda
+    M, K = A.shape
+    N = Bt.shape[0]
+    if C is None:
+        C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    stream = stream or torch.cuda.current_stream()
+    nbytes = lib.hotrg_gemm_scratch_bytes(M, N, K)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=A.device)
+    check(lib.hotrg_gemm_split(c_void_p(A.data_ptr()), A.stride(0), c_void_p(Bt.data_ptr()), Bt.stride(0),
+                                c_void_p(C.data_ptr()), C.stride(0), M, N, K, npass,
+                                c_void_p(scratch.data_ptr()), nbytes, c_void_p(stream.cuda_stream)),
+          "hotrg_gemm_split")
+    check(lib.hotrg_gemm_status(c_void_p(scratch.data_ptr()), c_void_p(stream.cuda_stream)), "gemm status")
+    return C

@@ -1,0 +1,169 @@
+// FP64 symmetric eigensolver for the Gram matrices (n = D_b^2 <= 256), one CTA per matrix.
+//
+// Method: cyclic two-sided Jacobi with the round-robin (tournament) parallel ordering of
+// Brent & Luk (1985): each round rotates n/2 disjoint (p, q) pairs at once, n - 1 rounds make a
+// sweep. Rotation angle as in Rutishauser's formulation (tan of the angle from
+// theta = (a_qq - a_pp) / (2 a_pq)), so that a'_pq = 0, a'_pp = a_pp - t a_pq, a'_qq = a_qq + t a_pq.
+// Converged when a whole sweep finds no off-diagonal entry above the rotation threshold
+// (|a_pq| > 1e-18 sqrt|a_pp a_qq| and > 2^-53 ||A||_F: below that an entry is rounding noise of
+// the matrix and rotating it changes no eigenvector beyond working precision).
+// Then (arXiv:1906.06060 Sec. 2 / HOTRG truncation): eigenvalues sorted descending (stable),
+// the first chi eigenvectors kept, each sign-fixed so its largest-magnitude component is
+// positive (lowest index on a tie).
+#include "kernels.h"
+
+namespace hotrg {
+
+namespace {
+
+constexpr int kEigThreads = 512;
+constexpr int kMaxSweeps = 40;
+
+__device__ void sm_red_sum(double* sred, double v, int tid) {
+  sred[tid] = v;
+  __syncthreads();
+  for (int w = kEigThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) sred[tid] += sred[tid + w];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict__ G, int n, int chi,
+                                                        double* __restrict__ evals,
+                                                        double* __restrict__ Uout,
+                                                        double* __restrict__ work, int* status) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  const int np = n + (n & 1);          // padded to even (index n is a dummy)
+  const int npairs = np / 2;
+  // shared: per-pair data
+  int* sp = reinterpret_cast<int*>(sm);                   // [128] p
+  int* sq = sp + 128;                                     // [128] q
+  double* sc = sm + 128;                                  // [128] c
+  double* ss = sc + 128;                                  // [128] s
+  double* st = ss + 128;                                  // [128] t
+  double* sred = st + 128;                                // [kEigThreads] reduction
+
+  double* A = work;                    // n x n
+  double* V = work + (long long)n * n; // n x n
+  for (int e = tid; e < n * n; e += kEigThreads) {
+    A[e] = G[e];
+    V[e] = (e / n == e % n) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+
+  // matrix scale for the absolute rotation threshold
+  {
+    double f = 0.0;
+    for (int e = tid; e < n * n; e += kEigThreads) f += A[e] * A[e];
+    sm_red_sum(sred, f, tid);
+  }
+  const double floor_abs = 0x1p-53 * sqrt(sred[0]);
+  __syncthreads();
+  __shared__ int s_rot;
+  int sweep = 0;
+  for (;; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    if (sweep >= kMaxSweeps) {
+      if (tid == 0) atomic_status(status, ST_NOCONV);
+      break;
+    }
+    __syncthreads();
+    for (int round = 0; round < np - 1; ++round) {
+      if (tid < npairs) {
+        auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (np - 1)) + 1; };
+        int p = player(tid), q = player(np - 1 - tid);
+        if (p > q) { int x = p; p = q; q = x; }
+        double c = 1.0, s = 0.0, t = 0.0;
+        if (q < n) {
+          const double apq = A[(long long)p * n + q];
+          const double app = A[(long long)p * n + p], aqq = A[(long long)q * n + q];
+          if (fabs(apq) > floor_abs && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+            s_rot = 1;
+            const double theta = (aqq - app) / (2.0 * apq);
+            t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        } else {
+          p = q = -1;
+        }
+        sp[tid] = p; sq[tid] = q; sc[tid] = c; ss[tid] = s; st[tid] = t;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = tid; e < npairs * n; e += kEigThreads) {
+        const int k = e / n, r = e % n;
+        const int p = sp[k], q = sq[k];
+        if (p < 0 || ss[k] == 0.0) continue;
+        const double c = sc[k], s = ss[k];
+        const double arp = A[(long long)r * n + p], arq = A[(long long)r * n + q];
+        A[(long long)r * n + p] = c * arp - s * arq;
+        A[(long long)r * n + q] = s * arp + c * arq;
+        const double vrp = V[(long long)r * n + p], vrq = V[(long long)r * n + q];
+        V[(long long)r * n + p] = c * vrp - s * vrq;
+        V[(long long)r * n + q] = s * vrp + c * vrq;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < npairs * n; e += kEigThreads) {
+        const int k = e / n, r = e % n;
+        const int p = sp[k], q = sq[k];
+        if (p < 0 || ss[k] == 0.0) continue;
+        const double c = sc[k], s = ss[k];
+        const double apr = A[(long long)p * n + r], aqr = A[(long long)q * n + r];
+        A[(long long)p * n + r] = c * apr - s * aqr;
+        A[(long long)q * n + r] = s * apr + c * aqr;
+      }
+      __syncthreads();
+    }
+    const int rotated = s_rot;
+    __syncthreads();  // every thread has read the flag before it is reset
+    if (!rotated) break;  // a full sweep without a rotation: converged
+  }
+  // eigenvalues and ranks (descending, stable in the index)
+  double* lam = sred;  // reuse: n <= 256 <= kEigThreads
+  for (int i = tid; i < n; i += kEigThreads) lam[i] = A[(long long)i * n + i];
+  __syncthreads();
+  int* perm = sp;      // reuse 256 ints (sp and sq are contiguous)
+  for (int i = tid; i < n; i += kEigThreads) {
+    const double li = lam[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double lj = lam[j];
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    perm[rank] = i;
+  }
+  __syncthreads();
+  for (int k = tid; k < n; k += kEigThreads) evals[k] = lam[perm[k]];
+  // sign-fixed eigenvectors: one warp per kept vector
+  const int warp = tid / 32, lane = tid % 32;
+  for (int k = warp; k < chi; k += kEigThreads / 32) {
+    const int col = perm[k];
+    double best = -1.0;
+    int bidx = n;
+    for (int r = lane; r < n; r += 32) {
+      const double a = fabs(V[(long long)r * n + col]);
+      if (a > best) { best = a; bidx = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    const double sgn = V[(long long)bidx * n + col] < 0 ? -1.0 : 1.0;
+    for (int r = lane; r < n; r += 32) Uout[(long long)k * n + r] = sgn * V[(long long)r * n + col];
+  }
+}
+
+}  // namespace
+
+void launch_eig(const double* G, int n, int chi, double* evals, double* U, double* work, int* status,
+                cudaStream_t s) {
+  const size_t smem = sizeof(double) * (128 + 128 + 128 + 128 + kEigThreads);
+  k_jacobi<<<1, kEigThreads, smem, s>>>(G, n, chi, evals, U, work, status);
+  count_launches(1);
+}
+
+}  // namespace hotrg

@@ -1,0 +1,72 @@
+// FP64 squeeze GEMM on the CUDA cores: C[m][n] = sum_k A[m][k] Bt[n][k] (both operands K-major).
+// This is the plain FP64 path of the O(Dcut^15) contraction (arXiv:1906.06060 Sec. 2 cost
+// statement). 64 x 64 output tiles, K chunks of 16, 4 x 4 register blocking per thread.
+#include "kernels.h"
+
+namespace hotrg {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, long long lda,
+                                                  const double* __restrict__ Bt, long long ldb,
+                                                  double* __restrict__ C, long long ldc, long long M,
+                                                  long long N, long long K) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const long long m0 = (long long)blockIdx.y * BM, n0 = (long long)blockIdx.x * BN;
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (long long k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < (BM * BK) / 256; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = e % BK, rr = e / BK;
+      const long long k = k0 + kk;
+      const long long m = m0 + rr, n = n0 + rr;
+      As[kk][rr] = (m < M && k < K) ? A[m * lda + k] : 0.0;
+      Bs[kk][rr] = (n < N && k < K) ? Bt[n * ldb + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long n = n0 + tx * 4 + j;
+      if (n < N) C[m * ldc + n] = acc[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+void launch_gemm_f64(const double* A, long long lda, const double* Bt, long long ldb, double* C,
+                     long long ldc, long long M, long long N, long long K, cudaStream_t s) {
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+  k_gemm_f64<<<grid, 256, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K);
+  count_launches(1);
+}
+
+}  // namespace hotrg

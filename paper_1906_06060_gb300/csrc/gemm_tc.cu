@@ -1,0 +1,456 @@
+// Squeeze GEMM on the 5th-generation tensor cores (sm_103a): the O(Dcut^15) contraction of
+// arXiv:1906.06060 Sec. 2 (cost statement), written as C[m][n] = sum_k A[m][k] Bt[n][k].
+//
+// Precision: each FP32 operand is split into bf16 planes, x = hi + lo (2 planes) or
+// x = hi + mid + lo (3 planes), each plane the bf16 rounding of what the previous ones left.
+// The GEMM sums the plane products ("passes") whose combined order is at most 2^-16: with two
+// planes hi*hi + hi*lo + lo*hi (3 passes), with three planes hh, hm, mh, hl, mm, lh (6 passes),
+// accumulating in FP32 in tensor memory. Dropped terms and split residuals are O(2^-16)
+// relative per product for 3 passes and O(2^-24) for 6 passes.
+//
+// Accumulation: the tensor core's FP32 accumulate rounds toward zero, so a long chain of MMAs
+// into one TMEM accumulator drifts systematically towards zero by about (chain length) x 2^-25
+// relative - for K = 10^4 and 3 passes about 1e-4, far above what the free energy tolerates.
+// The accumulator is therefore restarted for every 64-wide k-block (chain: npass x 4 MMAs, the
+// small cross terms first so the large hi*hi products meet a small accumulator) and each
+// k-block's partial sum is folded into an FP32 register accumulator with round-to-nearest adds.
+//
+// Kernel structure (one CTA per SM, persistent over output tiles, 320 threads):
+//   warp 0      TMA producer: per (k-block, pass) loads a 128x64 A tile and a 256x64 B tile
+//               (bf16, 128-byte swizzle) into a 4-stage shared-memory ring.
+//   warp 1      MMA issuer: one thread issues tcgen05.mma.cta_group::1.kind::f16 (M=128,
+//               N=256, K=16) for one k-block into one of two TMEM buffers (2 x 256 FP32
+//               columns), releases ring stages and hands the buffer over with tcgen05.commit.
+//   warps 2-9   fold/epilogue: warp w reads TMEM lanes 32*(w%4).. (its hardware quadrant),
+//               columns 128*((w-2)/4).. of the buffer, adds them into 128 FP32 registers per
+//               thread and frees the buffer; after the last k-block it stores its 128 columns.
+// Every mbarrier wait is bounded by a timeout; on expiry the CTA records ST_TIMEOUT, drains
+// the copies and MMAs it issued (again with a bound), frees TMEM and returns.
+#include <cuda.h>
+
+#include <cstring>
+
+#include "kernels.h"
+
+namespace hotrg {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64;
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 320;
+constexpr int TC_FOLD_THREADS = 256;  // warps 2-9
+constexpr uint32_t A_TILE = TC_BM * TC_BK * 2;  // 16 KB
+constexpr uint32_t B_TILE = TC_BN * TC_BK * 2;  // 32 KB
+constexpr uint32_t STAGE_BYTES = A_TILE + B_TILE;
+constexpr uint32_t TMEM_COLS = 2 * TC_BN;
+constexpr int GROUP_M = 16;
+constexpr size_t TC_SMEM = 1024 + TC_STAGES * STAGE_BYTES + 256;
+
+// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                           ((uint32_t)(TC_BM >> 4) << 24);
+
+struct TmapSet {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
+};
+
+// plane index of A and B for each pass, smallest products first, hi*hi last
+//   npass 1: hh      npass 3: hl, lh, hh      npass 6: lh, mm, hl, mh, hm, hh  (h=0, m=1, l=2)
+__constant__ int8_t kPassA1[1] = {0};
+__constant__ int8_t kPassB1[1] = {0};
+__constant__ int8_t kPassA3[3] = {0, 1, 0};
+__constant__ int8_t kPassB3[3] = {1, 0, 0};
+__constant__ int8_t kPassA6[6] = {2, 1, 0, 1, 0, 0};
+__constant__ int8_t kPassB6[6] = {0, 1, 2, 0, 1, 0};
+
+struct TcParams {
+  long long M, N;
+  int num_m, num_n, num_kb, npass;
+  float* C;
+  long long ldc;
+  int* status;
+  unsigned long long timeout_ns;
+  int vec4;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait. Returns false if another role aborted or this wait exceeded timeout_ns.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                       unsigned long long timeout_ns, bool honour_abort = true) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (honour_abort && *abort_flag) return false;
+    if (globaltimer_ns() - t0 > timeout_ns) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+// Shared-memory matrix descriptor, K-major operand staged by TMA with 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this layout, bits 16-29),
+// stride byte offset 1024 B between 8-row groups (bits 32-45), version 1 (bits 46-47),
+// base offset 0 (tiles are 1024-B aligned), layout SWIZZLE_128B = 2 (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void raster(int tile, int num_m, int num_n, int& mt, int& nt) {
+  const int per_group = GROUP_M * num_n;
+  const int g = tile / per_group;
+  const int first_m = g * GROUP_M;
+  const int gsz = min(num_m - first_m, GROUP_M);
+  const int local = tile - g * per_group;
+  mt = first_m + local % gsz;
+  nt = local / gsz;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_split(const __grid_constant__ TmapSet maps, TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + TC_STAGES * A_TILE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TC_STAGES * B_TILE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t full0 = smem_u32(bars);
+  const uint32_t empty0 = full0 + 8 * TC_STAGES;
+  const uint32_t tfull0 = empty0 + 8 * TC_STAGES;
+  const uint32_t tempty0 = tfull0 + 16;
+  const uint32_t final_bar = tempty0 + 16;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, TC_FOLD_THREADS);
+    }
+    mbar_init(final_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const int nplanes = p.npass == 1 ? 1 : (p.npass == 3 ? 2 : 3);
+  if (warp == 0 && lane < 2 * nplanes) {
+    const CUtensorMap* m = lane < nplanes ? &maps.a[lane] : &maps.b[lane - nplanes];
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int total = p.num_m * p.num_n;
+  const int kiters = p.num_kb * p.npass;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      long long issued = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+        int mt, nt;
+        raster(tile, p.num_m, p.num_n, mt, nt);
+        for (int it = 0; it < kiters; ++it) {
+          const int kb = it / p.npass, ps = it % p.npass;
+          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.timeout_ns)) { ok = false; break; }
+          const uint32_t fb = full0 + 8 * stage;
+          mbar_expect_tx(fb, STAGE_BYTES);
+          const int pa = p.npass == 6 ? kPassA6[ps] : (p.npass == 3 ? kPassA3[ps] : kPassA1[ps]);
+          const int pb = p.npass == 6 ? kPassB6[ps] : (p.npass == 3 ? kPassB3[ps] : kPassB1[ps]);
+          const CUtensorMap* ma = &maps.a[pa];
+          const CUtensorMap* mb = &maps.b[pb];
+          tma_load_2d(smem_u32(sA + stage * A_TILE), ma, fb, kb * TC_BK, mt * TC_BM);
+          tma_load_2d(smem_u32(sB + stage * B_TILE), mb, fb, kb * TC_BK, nt * TC_BN);
+          ++issued;
+          if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+      if (!ok) {
+        // drain: the last min(STAGES, issued) loads must land before the CTA exits
+        for (long long i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i)
+          mbar_wait(full0 + 8 * (int)(i % TC_STAGES), (uint32_t)((i / TC_STAGES) & 1), abort_flag,
+                    p.timeout_ns, false);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int buf = 0;
+      uint32_t bphase = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+        for (int kb = 0; kb < p.num_kb && ok; ++kb) {
+          if (!mbar_wait(tempty0 + 8 * buf, bphase ^ 1, abort_flag, p.timeout_ns)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(buf * TC_BN);
+          for (int ps = 0; ps < p.npass; ++ps) {
+            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.timeout_ns)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + stage * A_TILE);
+            const uint32_t b0 = smem_u32(sB + stage * B_TILE);
+#pragma unroll
+            for (int k = 0; k < TC_BK / 16; ++k)
+              mma_bf16(d_tmem, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), IDESC, (ps | k) != 0);
+            mma_commit(empty0 + 8 * stage);
+            if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(tfull0 + 8 * buf);
+          if (++buf == 2) { buf = 0; bphase ^= 1; }
+        }
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      mma_commit(final_bar);
+      mbar_wait(final_bar, 0, abort_flag, p.timeout_ns, false);
+    }
+  } else {
+    const int q = warp & 3;          // TMEM lane quadrant this warp may access
+    const int half = (warp - 2) >> 2;  // which 128 of the 256 columns
+    int buf = 0;
+    uint32_t bphase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+      int mt, nt;
+      raster(tile, p.num_m, p.num_n, mt, nt);
+      float acc[128];
+#pragma unroll
+      for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+      for (int kb = 0; kb < p.num_kb; ++kb) {
+        const bool w = mbar_wait(tfull0 + 8 * buf, bphase, abort_flag, p.timeout_ns);
+        if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN + half * 128);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t r[32];
+          tmem_ld32(taddr + c * 32, r);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[c * 32 + j] += __uint_as_float(r[j]);
+        }
+        tc_fence_before();
+        mbar_arrive(tempty0 + 8 * buf);
+        if (++buf == 2) { buf = 0; bphase ^= 1; }
+      }
+      if (!ok) break;
+      const long long row = (long long)mt * TC_BM + q * 32 + lane;
+      const long long col0 = (long long)nt * TC_BN + half * 128;
+      if (row < p.M && col0 < p.N) {
+        float* dst = p.C + row * p.ldc + col0;
+        if (p.vec4 && col0 + 128 <= p.N) {
+#pragma unroll
+          for (int j = 0; j < 128; j += 4)
+            *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 128; ++j)
+            if (col0 + j < p.N) dst[j] = acc[j];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomic_status(p.status, ST_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+__global__ void k_split_rows(const float* __restrict__ X, long long ldx, long long rows, long long cols,
+                             Planes<__nv_bfloat16> out, long long ld) {
+  const long long total = rows * cols;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / cols, c = i % cols;
+    store_planes(out, r * ld + c, X[r * ldx + c]);
+  }
+}
+
+// ------------------------------------------------------------------ host: tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld,
+              int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
+                      long long ldb, float* C, long long ldc, long long M, long long N, long long K,
+                      int npass, int* status, double timeout_s, cudaStream_t s) {
+  if (M < TC_BM || N < TC_BN || K < TC_BK || (npass != 1 && npass != 3 && npass != 6)) return HOTRG_EINVAL;
+  const int nplanes = npass == 1 ? 1 : (npass == 3 ? 2 : 3);
+  if (A.nparts < nplanes || B.nparts < nplanes) return HOTRG_EINVAL;
+  if ((lda % 8) || (ldb % 8) || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
+  if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return HOTRG_EINVAL;
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  TmapSet maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int i = 0; i < nplanes; ++i) {
+    if (!al16(A.p[i]) || !al16(B.p[i])) return HOTRG_EINVAL;
+    if (!make_map(&maps.a[i], A.p[i], M, K, lda, TC_BM) || !make_map(&maps.b[i], B.p[i], N, K, ldb, TC_BN))
+      return HOTRG_EDEVICE;
+  }
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) !=
+        cudaSuccess)
+      return HOTRG_EDEVICE;
+    attr_set = true;
+  }
+  TcParams p;
+  p.M = M;
+  p.N = N;
+  p.num_m = (int)((M + TC_BM - 1) / TC_BM);
+  p.num_n = (int)((N + TC_BN - 1) / TC_BN);
+  p.num_kb = (int)((K + TC_BK - 1) / TC_BK);
+  p.npass = npass;
+  p.C = C;
+  p.ldc = ldc;
+  p.status = status;
+  p.timeout_ns = (unsigned long long)(timeout_s * 1e9);
+  p.vec4 = ((ldc % 4) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+  const long long tiles = (long long)p.num_m * p.num_n;
+  if (tiles > 0x7fffffffLL) return HOTRG_EINVAL;
+  const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
+  k_gemm_split<<<grid, TC_THREADS, TC_SMEM, s>>>(maps, p);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
+}
+
+void launch_split_rows(const float* X, long long ldx, long long rows, long long cols,
+                       const Planes<__nv_bfloat16>& out, long long ld, cudaStream_t s) {
+  const long long total = rows * cols;
+  long long g = (total + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  k_split_rows<<<(int)g, 256, 0, s>>>(X, ldx, rows, cols, out, ld);
+  count_launches(1);
+}
+
+}  // namespace hotrg

@@ -1,0 +1,169 @@
+// Gram matrices of the two-site unfolding (arXiv:1906.06060 Sec. 2: the isometry U of Eq. (SS)
+// comes from the HOSVD of the merged pair; its left factor is the eigenbasis of this Gram matrix).
+//
+// G_b[(b1 b2), (b1~ b2~)] = sum over every other leg of the merged pair M
+//                         = sum_{al, al~} Q1[(b1,al)][(b1~,al~)] Q2[(b2,al)][(b2~,al~)]
+// Q1 contracts site 1 over all legs except (u_b, p_a); Q2 site 2 over all except (u_b, u_a).
+// Both are X X^T of an unfolding of T with nr = D_b D_a rows and P^2 / nr columns, computed in
+// FP64 on the CUDA cores by split-K 64x64 tiles and a fixed-order reduction (deterministic).
+#include "kernels.h"
+
+namespace hotrg {
+
+namespace {
+
+constexpr int GT = 64;           // output tile edge
+constexpr int GK = 16;           // column chunk
+constexpr int kGramCTAs = 304;   // 2 x 152 SMs
+
+struct LegInfo {
+  int nrest;                     // number of remaining legs (2d - 2)
+  int dim[kMaxLegs];             // remaining legs, natural order
+  long long stride[kMaxLegs];
+};
+
+__global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ T, LegInfo li,
+                                                   long long S1, long long S2, int Da, int nr,
+                                                   long long K, int ntile, int nsplit,
+                                                   double* __restrict__ partial) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  __shared__ long long coloff[GK];
+  __shared__ long long rowoffA[GT], rowoffB[GT];
+  const int tid = threadIdx.x;
+  const int tile = blockIdx.x, split = blockIdx.y;
+  const int r0 = (tile / ntile) * GT, c0 = (tile % ntile) * GT;
+  const long long kper = (K + nsplit - 1) / nsplit;
+  const long long kb = (long long)split * kper;
+  const long long ke = min(K, kb + kper);
+  if (tid < GT) {
+    const int ra = r0 + tid, rb = c0 + tid;
+    rowoffA[tid] = ra < nr ? (long long)(ra / Da) * S1 + (long long)(ra % Da) * S2 : -1;
+    rowoffB[tid] = rb < nr ? (long long)(rb / Da) * S1 + (long long)(rb % Da) * S2 : -1;
+  }
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (long long kc = kb; kc < ke; kc += GK) {
+    if (tid < GK) {
+      long long col = kc + tid;
+      long long off = -1;
+      if (col < ke) {
+        off = 0;
+        for (int l = li.nrest - 1; l >= 0; --l) {
+          const long long c = col % li.dim[l];
+          col /= li.dim[l];
+          off += c * li.stride[l];
+        }
+      }
+      coloff[tid] = off;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < (GT * GK) / 256; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = e % GK, rr = e / GK;
+      const long long co = coloff[kk];
+      const long long ra = rowoffA[rr], rb = rowoffB[rr];
+      As[kk][rr] = (co >= 0 && ra >= 0) ? T[ra + co] : 0.0;
+      Bs[kk][rr] = (co >= 0 && rb >= 0) ? T[rb + co] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* out = partial + (long long)split * nr * nr;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty * 4 + i;
+    if (r >= nr) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx * 4 + j;
+      if (c < nr) out[(long long)r * nr + c] = acc[i][j];
+    }
+  }
+}
+
+__global__ void k_reduce_splits(const double* __restrict__ partial, int nsplit, int nn,
+                                double* __restrict__ Q) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += partial[(long long)k * nn + e];
+  Q[e] = s;
+}
+
+__global__ void k_gram_combine(const double* __restrict__ Q1, const double* __restrict__ Q2, int Db,
+                               int Da, double* __restrict__ G) {
+  const int n = Db * Db, nr = Db * Da;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int row = e / n, col = e % n;
+  const int b1 = row / Db, b2 = row % Db, c1 = col / Db, c2 = col % Db;
+  double s = 0.0;
+  for (int al = 0; al < Da; ++al) {
+    const double* q1 = Q1 + (long long)(b1 * Da + al) * nr + c1 * Da;
+    const double* q2 = Q2 + (long long)(b2 * Da + al) * nr + c2 * Da;
+    for (int at = 0; at < Da; ++at) s = fma(q1[at], q2[at], s);
+  }
+  G[e] = s;
+}
+
+}  // namespace
+
+int gram_nsplit() { return kGramCTAs; }
+
+void launch_half_gram(const double* T, Geom g, int l1, int l2, double* partial, double* Q,
+                      cudaStream_t s) {
+  const int d = g.d;
+  auto leg_dim = [&](int l) { return g.D[l % d]; };
+  auto leg_stride = [&](int l) { return l < d ? g.Sn[l] * g.P : g.Sn[l - d]; };
+  LegInfo li;
+  li.nrest = 0;
+  for (int l = 0; l < 2 * d; ++l) {
+    if (l == l1 || l == l2) continue;
+    li.dim[li.nrest] = leg_dim(l);
+    li.stride[li.nrest] = leg_stride(l);
+    ++li.nrest;
+  }
+  const int Da = leg_dim(l2);
+  const int nr = leg_dim(l1) * Da;
+  const long long K = g.P * g.P / nr;
+  const int ntile = (nr + GT - 1) / GT;
+  const int tiles = ntile * ntile;
+  int nsplit = kGramCTAs / tiles;
+  if (nsplit < 1) nsplit = 1;
+  if (nsplit > K) nsplit = (int)K;
+  dim3 grid(tiles, nsplit);
+  k_half_gram<<<grid, 256, 0, s>>>(T, li, leg_stride(l1), leg_stride(l2), Da, nr, K, ntile, nsplit,
+                                    partial);
+  count_launches(1);
+  const int nn = nr * nr;
+  k_reduce_splits<<<(nn + 255) / 256, 256, 0, s>>>(partial, nsplit, nn, Q);
+  count_launches(1);
+}
+
+void launch_gram_combine(const double* Q1, const double* Q2, int Db, int Da, double* G,
+                         cudaStream_t s) {
+  const int n = Db * Db;
+  k_gram_combine<<<(n * n + 255) / 256, 256, 0, s>>>(Q1, Q2, Db, Da, G);
+  count_launches(1);
+}
+
+}  // namespace hotrg

@@ -1,0 +1,928 @@
+// Host side of libhotrg: context, workspace plan, the coarse-graining step sequence and the
+// C ABI declared in include/hotrg.h (arXiv:1906.06060 Sec. 2).
+//
+// One step along axis a, for each instance (b runs over the transverse axes, c3 = the last one,
+// "others" = the rest; T1 = T2 = T by translation invariance):
+//   1. Q1_b, Q2_b, G_b (gram.cu), eigendecomposition -> U_b[k][b1 b2] (eig.cu)
+//   2. B operand once per step:  Bt[(j, n)][k] = sum_x U_c3[j][k_c3][x] T[k | c3 := x][n]
+//      (the c3 isometry of site 1's unprimed leg, moved onto site 2)
+//   3. per chunk (k_o for the other transverse axes):
+//        X = T with U_o[k_o] applied to u_o (mode products)
+//        A operand Y[m][k] = X[u = (k_b.., m_a)][p = (m_b.., k_a)]       (m: site-1 primed legs)
+//        O[m][(j, n)] = sum_k Y[m][k] Bt[(j, n)][k]                       (the O(D^15) GEMM)
+//        T'[(k_o, j, m_a)][(k'_b, n_a)] = sum prod_b U_b[k'_b][m_b n_b] O[m][(j, n)]  (epilogue)
+//   4. c_n = ||T'||_F, T <- T'/c_n, L += 2^-n ln c_n, Tr T, X^(n).
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace hotrg;
+
+struct hotrg_ctx {
+  int d = 0, Dcut = 0, batch = 1, precision = HOTRG_FP64, fp64_steps = 2, x6_steps = 0, max_steps = 64;
+  double timeout_s = 4.0;
+  cudaStream_t stream = nullptr;
+  int dims[kMaxD] = {1, 1, 1, 1};
+  int steps = 0, last_axis = -1, sticky = 0;
+  int hist_dims[64][kMaxD] = {};  // bond dimensions before step n+1
+  int hist_axis[64] = {};
+  long long Pmax = 1;
+  std::vector<double> beta, h;
+  // device buffers carved from the workspace
+  double *T = nullptr, *Tnext = nullptr, *dbeta = nullptr, *dh = nullptr, *L = nullptr;
+  double *lnc_log = nullptr, *spec_log = nullptr, *out3 = nullptr, *cval = nullptr;
+  double *norm_partial = nullptr, *gpartial = nullptr, *Q1 = nullptr, *Q2 = nullptr;
+  double *G = nullptr, *U = nullptr, *ework = nullptr;
+  int* status = nullptr;
+  void *Tt = nullptr, *Bt = nullptr, *X1 = nullptr, *X2 = nullptr, *Y = nullptr, *O = nullptr;
+  void *R1 = nullptr, *R2 = nullptr;
+  size_t sz_Tt = 0, sz_Bt = 0, sz_X = 0, sz_Y = 0, sz_O = 0, sz_R1 = 0, sz_R2 = 0;
+  long long spec_stride = 0;  // doubles per instance in spec_log
+  // phase timing (hotrg_timing_start/stop): CUDA events recorded on `stream`
+  struct Ev {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<Ev> evs;
+  long long launch0 = 0, t_gemm_launches = 0, t_steps = 0;
+  double t_gemm_flops = 0, t_gemm_tflops = 0, t_step_flops = 0;
+};
+
+namespace {
+enum Phase { PH_STEP = 0, PH_ISO, PH_OPERANDS, PH_GEMM, PH_EPILOGUE, PH_NORM, PH_COUNT };
+
+// Records a start event now and an end event when it goes out of scope (timing enabled only).
+struct PhaseScope {
+  hotrg_ctx* c;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseScope(hotrg_ctx* ctx, int ph) : c(ctx), phase(ph) {
+    if (c->timing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, c->stream);
+  }
+  ~PhaseScope() {
+    cudaEvent_t b = nullptr;
+    if (a && cudaEventCreate(&b) == cudaSuccess) {
+      cudaEventRecord(b, c->stream);
+      c->evs.push_back({phase, a, b});
+    }
+  }
+};
+}  // namespace
+
+namespace {
+
+constexpr long long kAlign = 256;
+constexpr int kSpecCap = kMaxGram;  // eigenvalues stored per (step, axis)
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// Sizes (bytes) of the per-step scratch buffers for one configuration.
+struct StepNeeds {
+  size_t Tt, Bt, X, Y, O, R1, R2;
+};
+
+// mixed: 0 = FP64 path, 2 or 3 = tensor-core path with that many bf16 planes per operand
+StepNeeds needs_for(int d, const int* dims, int a, int Dcut, int planes) {
+  const bool mixed = planes > 0;
+  Geom g = make_geom(d, dims);
+  const long long P = g.P;
+  const long long ldk = mixed ? round_up(P, 64) : P;
+  int chi[kMaxD];
+  int trans[kMaxD], nt = 0;
+  for (int b = 0; b < d; ++b) {
+    chi[b] = dims[b];
+    if (b != a) {
+      const long long sq = (long long)dims[b] * dims[b];
+      chi[b] = (int)(sq < Dcut ? sq : Dcut);
+      trans[nt++] = b;
+    }
+  }
+  const int c3 = nt ? trans[nt - 1] : -1;
+  const long long chi3 = c3 >= 0 ? chi[c3] : 1;
+  const size_t es = mixed ? 4 : 8;  // intermediate element size (float / double)
+  StepNeeds n;
+  n.Tt = (size_t)(P * P) * es;
+  n.Bt = (size_t)(chi3 * P * ldk) * (mixed ? 2 * planes : 8);  // bf16 planes, or double
+  n.X = (size_t)(P * P) * es;
+  n.Y = (size_t)(P * ldk) * (mixed ? 2 * planes : 8);
+  n.O = (size_t)(P * chi3 * P) * es;
+  // epilogue intermediates: contract the other transverse axes in order
+  long long cur = P * chi3 * P;
+  size_t r[2] = {0, 0};
+  for (int i = 0; i < nt - 1 && i < 2; ++i) {
+    const int b = trans[i];
+    cur = cur / ((long long)dims[b] * dims[b]) * chi[b];
+    r[i] = (size_t)cur * es;
+  }
+  n.R1 = r[0];
+  n.R2 = r[1];
+  return n;
+}
+
+void max_into(StepNeeds& acc, const StepNeeds& n) {
+  acc.Tt = std::max(acc.Tt, n.Tt);
+  acc.Bt = std::max(acc.Bt, n.Bt);
+  acc.X = std::max(acc.X, n.X);
+  acc.Y = std::max(acc.Y, n.Y);
+  acc.O = std::max(acc.O, n.O);
+  acc.R1 = std::max(acc.R1, n.R1);
+  acc.R2 = std::max(acc.R2, n.R2);
+}
+
+// Workspace plan: the per-step buffers must hold every step a context can take. The bond
+// dimensions reachable within max_steps steps (any axis sequence, starting from all 2) are
+// enumerated breadth-first; each D_b is 2, min(4, Dcut) or min(16, Dcut). Path of a step: FP64
+// for P < 256 or (in split modes) for steps <= fp64_steps, tensor cores otherwise with 3 planes
+// if the step may run the 6-pass GEMM.
+int planes_for_step(int precision, int step, int fp64_steps, int x6_steps, long long P) {
+  if (precision == HOTRG_FP64 || P < 256 || step <= fp64_steps) return 0;
+  if (precision == HOTRG_BF16X6 || step <= x6_steps) return 3;
+  return 2;
+}
+
+StepNeeds plan(int d, int Dcut, int precision, int fp64_steps, int x6_steps, int max_steps,
+               long long* Pmax_out) {
+  // breadth-first: minimal number of steps after which each bond-dimension state is reached
+  std::vector<std::vector<int>> states{std::vector<int>(d, 2)};
+  std::vector<int> depth{0};
+  for (size_t i = 0; i < states.size(); ++i) {
+    if (depth[i] >= max_steps) continue;
+    for (int a = 0; a < d; ++a) {
+      std::vector<int> nd(states[i]);
+      for (int b = 0; b < d; ++b)
+        if (b != a) nd[b] = std::min(nd[b] * nd[b], Dcut);
+      if (std::find(states.begin(), states.end(), nd) == states.end()) {
+        states.push_back(nd);
+        depth.push_back(depth[i] + 1);
+      }
+    }
+  }
+  StepNeeds acc{0, 0, 0, 0, 0, 0, 0};
+  long long Pmax = 1;
+  for (size_t i = 0; i < states.size(); ++i) {
+    long long P = 1;
+    for (int b = 0; b < d; ++b) P *= states[i][b];
+    Pmax = std::max(Pmax, P);
+    const int first = depth[i] + 1;  // earliest step number taken from this state
+    if (first > max_steps) continue;
+    for (int a = 0; a < d; ++a)
+      for (int step : {first, fp64_steps + 1, x6_steps + 1, max_steps})
+        if (step >= first && step <= max_steps)
+          max_into(acc, needs_for(d, states[i].data(), a, Dcut,
+                                  planes_for_step(precision, step, fp64_steps, x6_steps, P)));
+  }
+  *Pmax_out = Pmax;
+  return acc;
+}
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t bytes) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += (size_t)round_up((long long)bytes, kAlign);
+    return p;
+  }
+};
+
+// Lay out every buffer; with base == nullptr only the total size is computed.
+size_t carve(hotrg_ctx* c, char* base) {
+  long long Pmax = 1;
+  StepNeeds n = plan(c->d, c->Dcut, c->precision, c->fp64_steps, c->x6_steps, c->max_steps, &Pmax);
+  c->Pmax = Pmax;
+  const long long P2 = Pmax * Pmax;
+  const int nr_max = kMaxGram;
+  Carver k{base};
+  c->T = k.take<double>(sizeof(double) * P2 * c->batch);
+  c->Tnext = k.take<double>(sizeof(double) * P2);
+  c->dbeta = k.take<double>(sizeof(double) * c->batch);
+  c->dh = k.take<double>(sizeof(double) * c->batch);
+  c->L = k.take<double>(sizeof(double) * c->batch);
+  c->lnc_log = k.take<double>(sizeof(double) * c->batch * (c->max_steps + 1));
+  c->spec_stride = (long long)c->max_steps * c->d * kSpecCap;
+  c->spec_log = k.take<double>(sizeof(double) * c->batch * c->spec_stride);
+  c->out3 = k.take<double>(sizeof(double) * 3 * c->batch);
+  c->cval = k.take<double>(sizeof(double) * c->batch);
+  c->status = k.take<int>(sizeof(int) * 64);
+  c->norm_partial = k.take<double>(sizeof(double) * 1024);
+  c->gpartial = k.take<double>(sizeof(double) * gram_nsplit() * 4096);
+  c->Q1 = k.take<double>(sizeof(double) * nr_max * nr_max);
+  c->Q2 = k.take<double>(sizeof(double) * nr_max * nr_max);
+  c->G = k.take<double>(sizeof(double) * kMaxD * kMaxGram * kMaxGram);
+  c->U = k.take<double>(sizeof(double) * kMaxD * kMaxBond * kMaxGram);
+  c->ework = k.take<double>(sizeof(double) * (2 * kMaxGram * kMaxGram + 4 * kMaxGram));
+  c->sz_Tt = n.Tt; c->Tt = k.take<char>(n.Tt);
+  c->sz_Bt = n.Bt; c->Bt = k.take<char>(n.Bt);
+  c->sz_X = n.X;   c->X1 = k.take<char>(n.X); c->X2 = k.take<char>(n.X);
+  c->sz_Y = n.Y;   c->Y = k.take<char>(n.Y);
+  c->sz_O = n.O;   c->O = k.take<char>(n.O);
+  c->sz_R1 = n.R1; c->R1 = k.take<char>(n.R1 ? n.R1 : 256);
+  c->sz_R2 = n.R2; c->R2 = k.take<char>(n.R2 ? n.R2 : 256);
+  return k.off;
+}
+
+int cuda_err(hotrg_ctx* c) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (c && !c->sticky) c->sticky = HOTRG_EDEVICE;
+    return HOTRG_EDEVICE;
+  }
+  return HOTRG_OK;
+}
+
+int status_to_code(int bits) {
+  if (bits & ST_TIMEOUT) return HOTRG_ETIMEOUT;
+  if (bits & ST_NOCONV) return HOTRG_ENOCONV;
+  if (bits & ST_NUMERIC) return HOTRG_ENUMERIC;
+  if (bits) return HOTRG_EDEVICE;
+  return HOTRG_OK;
+}
+
+// Synchronise and fold the device status word into the sticky error.
+int sync_check(hotrg_ctx* c) {
+  if (c->sticky) return c->sticky;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return c->sticky = HOTRG_EDEVICE;
+  }
+  int bits = 0;
+  if (cudaMemcpy(&bits, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
+  const int code = status_to_code(bits);
+  if (code) c->sticky = code;
+  return code;
+}
+
+// ----------------------------------------------------------------- epilogue axis bookkeeping
+struct Ax {
+  int dim;
+  long long stride;
+  int kind;  // 0 = m (site-1 primed / a1), 1 = j (c3 isometry index), 2 = n (site-2 primed)
+  int slot;
+};
+
+// Contract (m_b, n_b) with U_b into k'_b; output dense row-major unless out_strides given.
+template <class Tin, class Tout>
+void contract_axes(std::vector<Ax>& axes, const Tin* in, Tout* out, int b, int chi_b, const double* Ub,
+                   const long long* final_out_stride, long long out_base, cudaStream_t s) {
+  int im = -1, in_ = -1;
+  for (int i = 0; i < (int)axes.size(); ++i) {
+    if (axes[i].kind == 0 && axes[i].slot == b) im = i;
+    if (axes[i].kind == 2 && axes[i].slot == b) in_ = i;
+  }
+  std::vector<Ax> out_axes;
+  View v;
+  v.ndim = 0;
+  int kaxis = -1;
+  for (int i = 0; i < (int)axes.size(); ++i) {
+    if (i == im) continue;
+    Ax ax = axes[i];
+    if (i == in_) {
+      kaxis = v.ndim;
+      ax.dim = chi_b;
+      ax.stride = 0;
+    }
+    v.shape[v.ndim] = ax.dim;
+    v.in_stride[v.ndim] = ax.stride;
+    out_axes.push_back(ax);
+    ++v.ndim;
+  }
+  // output strides
+  long long st = 1;
+  for (int i = v.ndim - 1; i >= 0; --i) {
+    v.out_stride[i] = final_out_stride ? final_out_stride[i] : st;
+    st *= v.shape[i];
+  }
+  launch_pair_contract<Tin, Tout>(in, out, v, kaxis, axes[im].dim, axes[in_].dim, axes[im].stride,
+                                  axes[in_].stride, Ub, chi_b, 0, out_base, s);
+  // new axes describe the dense output (only meaningful when not final)
+  st = 1;
+  for (int i = v.ndim - 1; i >= 0; --i) {
+    out_axes[i].stride = st;
+    st *= out_axes[i].dim;
+  }
+  axes = out_axes;
+}
+
+// Strides of the final output (Tnext in the new geometry) for an axes list.
+void final_strides(const std::vector<Ax>& axes, int skip_m_slot, int kslot, const Geom& gn, int c3,
+                   long long* out) {
+  int v = 0;
+  for (const Ax& ax : axes) {
+    if (ax.kind == 0 && ax.slot == skip_m_slot) continue;  // contracted away
+    long long s = 0;
+    if (ax.kind == 0) s = gn.Sn[ax.slot] * gn.P;          // m_a -> u'_a
+    else if (ax.kind == 1) s = c3 >= 0 ? gn.Sn[c3] * gn.P : 0;  // j -> u'_c3
+    else s = gn.Sn[ax.slot];                                // n_b / k'_b -> p'_b
+    (void)kslot;
+    out[v++] = s;
+  }
+}
+
+template <class TC>
+struct Ops;  // operand element types of a path
+
+template <>
+struct Ops<double> {
+  using Op = double;
+};
+template <>
+struct Ops<float> {
+  using Op = __nv_bfloat16;
+};
+
+// planes: 0 = FP64 path (TC = double), 2 / 3 = tensor-core path (TC = float) with 3 / 6 passes.
+template <class TC>
+int squeeze(hotrg_ctx* c, const double* Tin, const Geom& g, const Geom& gn, int a, const int* chi,
+            const int* trans, int nt, int planes) {
+  using Op = typename Ops<TC>::Op;
+  constexpr bool mixed = std::is_same<TC, float>::value;
+  cudaStream_t s = c->stream;
+  const long long P = g.P;
+  const long long ldk = mixed ? round_up(P, 64) : P;
+  const int c3 = nt ? trans[nt - 1] : -1;
+  const int chi3 = c3 >= 0 ? chi[c3] : 1;
+  const double* U = c->U;
+  auto Ub = [&](int b) { return U + (long long)b * kMaxBond * kMaxGram; };
+  // bounds of this step's buffers against the plan
+  StepNeeds need = needs_for(c->d, g.D, a, c->Dcut, planes);
+  if (need.Tt > c->sz_Tt || need.Bt > c->sz_Bt || need.X > c->sz_X || need.Y > c->sz_Y ||
+      need.O > c->sz_O || need.R1 > c->sz_R1 || need.R2 > c->sz_R2)
+    return HOTRG_ENOMEM;
+  const int nparts = mixed ? planes : 1;
+  // B operand
+  PhaseScope* ops_scope = new PhaseScope(c, PH_OPERANDS);
+  TC* Tt = static_cast<TC*>(c->Tt);
+  launch_transpose<TC>(Tin, Tt, P, s);
+  Planes<Op> Bt;
+  Bt.nparts = nparts;
+  for (int k = 0; k < 3; ++k) Bt.p[k] = static_cast<Op*>(c->Bt) + (size_t)(k < nparts ? k : 0) * chi3 * P * ldk;
+  launch_build_bt<TC, Op>(Tt, Bt, ldk, g, c3, c3 >= 0 ? Ub(c3) : nullptr, chi3, s);
+  delete ops_scope;
+  Planes<Op> Y;
+  Y.nparts = nparts;
+  for (int k = 0; k < 3; ++k) Y.p[k] = static_cast<Op*>(c->Y) + (size_t)(k < nparts ? k : 0) * P * ldk;
+  TC* O = static_cast<TC*>(c->O);
+  const long long ldO = (long long)chi3 * P;
+  // chunks over the other transverse axes
+  const int no = nt > 0 ? nt - 1 : 0;
+  int kcnt[kMaxD] = {0, 0, 0, 0};
+  long long nchunks = 1;
+  for (int i = 0; i < no; ++i) nchunks *= chi[trans[i]];
+  int prev_k0 = -1;
+  for (long long ch = 0; ch < nchunks; ++ch) {
+    long long r = ch;
+    for (int i = no - 1; i >= 0; --i) {
+      kcnt[i] = (int)(r % chi[trans[i]]);
+      r /= chi[trans[i]];
+    }
+    // producer: mode products on the unprimed legs of the other transverse axes
+    ops_scope = new PhaseScope(c, PH_OPERANDS);
+    if (no == 0) {
+      launch_build_y<double, Op>(Tin, Y, ldk, g, a, s);
+    } else {
+      TC* X1 = static_cast<TC*>(c->X1);
+      TC* X2 = static_cast<TC*>(c->X2);
+      if (kcnt[0] != prev_k0) {
+        launch_mode_unprimed<double, TC>(Tin, X1, g, trans[0], Ub(trans[0]), kcnt[0], s);
+        prev_k0 = kcnt[0];
+      }
+      const TC* X = X1;
+      if (no >= 2) {
+        launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(trans[1]), kcnt[1], s);
+        X = X2;
+      }
+      launch_build_y<TC, Op>(X, Y, ldk, g, a, s);
+    }
+    delete ops_scope;
+    // the O(D^15) GEMM
+    {
+      PhaseScope gemm_scope(c, PH_GEMM);
+      if constexpr (mixed) {
+        const int npass = planes == 3 ? 6 : 3;
+        const int rc = launch_gemm_split(Y, ldk, Bt, ldk, reinterpret_cast<float*>(O), ldO, P, ldO, P,
+                                         npass, c->status, c->timeout_s, s);
+        if (rc) return rc;
+        if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * P * npass;
+      } else {
+        launch_gemm_f64(Y.p[0], ldk, Bt.p[0], ldk, O, ldO, P, ldO, P, s);
+        if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * P;
+      }
+      if (c->timing) {
+        c->t_gemm_flops += 2.0 * P * (double)ldO * P;
+        ++c->t_gemm_launches;
+      }
+    }
+    // epilogue: O axes [m_0..m_{d-1}, j, n_0..n_{d-1}]
+    PhaseScope epi_scope(c, PH_EPILOGUE);
+    std::vector<Ax> axes;
+    for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b] * ldO, 0, b});
+    axes.push_back({chi3, P, 1, -1});
+    for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
+    long long out_base = 0;
+    for (int i = 0; i < no; ++i) out_base += (long long)kcnt[i] * gn.Sn[trans[i]] * gn.P;
+    const TC* cur = O;
+    TC* bufs[2] = {static_cast<TC*>(c->R1), static_cast<TC*>(c->R2)};
+    for (int i = 0; i < no; ++i) {
+      contract_axes<TC, TC>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(trans[i]), nullptr, 0, s);
+      cur = bufs[i];
+    }
+    long long fs[kMaxAxes];
+    if (c3 >= 0) {
+      // final axes after contracting c3 (m_c3 removed, n_c3 -> k'_c3)
+      final_strides(axes, c3, c3, gn, c3, fs);
+      contract_axes<TC, double>(axes, cur, c->Tnext, c3, chi3, Ub(c3), fs, out_base, s);
+    } else {
+      // d = 1: plain copy O[m][n] -> Tnext[u'][p']
+      final_strides(axes, -2, -1, gn, -1, fs);
+      View v;
+      v.ndim = (int)axes.size();
+      for (int i = 0; i < v.ndim; ++i) {
+        v.shape[i] = axes[i].dim;
+        v.in_stride[i] = axes[i].stride;
+        v.out_stride[i] = fs[i];
+      }
+      launch_pair_contract<TC, double>(cur, c->Tnext, v, -1, 1, 1, 0, 0, nullptr, 1, 0, 0, s);
+    }
+  }
+  return HOTRG_OK;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+extern "C" {
+
+void hotrg_opts_default(hotrg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = HOTRG_FP64;
+  o->fp64_steps = 2;
+  o->x6_steps = 0;
+  o->batch = 1;
+  o->max_steps = 64;
+  o->wait_timeout_s = 4.0;
+}
+
+int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) {
+  if (!bytes || d < 1 || d > kMaxD || Dcut < 2 || Dcut > kMaxBond) return HOTRG_EINVAL;
+  hotrg_opts def;
+  hotrg_opts_default(&def);
+  if (!opt) opt = &def;
+  if (opt->batch < 1 || opt->max_steps < 1 || opt->max_steps > 64) return HOTRG_EINVAL;
+  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X6) return HOTRG_EINVAL;
+  hotrg_ctx c;
+  c.d = d;
+  c.Dcut = Dcut;
+  c.batch = opt->batch;
+  c.precision = opt->precision;
+  c.fp64_steps = opt->fp64_steps;
+  c.x6_steps = opt->x6_steps;
+  c.max_steps = opt->max_steps;
+  *bytes = carve(&c, nullptr);
+  return HOTRG_OK;
+}
+
+int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const hotrg_opts* opt) {
+  if (!out || !opt) return HOTRG_EINVAL;
+  *out = nullptr;
+  if (d < 1 || d > kMaxD || Dcut < 2 || Dcut > kMaxBond || opt->batch < 1) return HOTRG_EINVAL;
+  if (opt->max_steps < 1 || opt->max_steps > 64 || opt->fp64_steps < 0) return HOTRG_EINVAL;
+  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X6) return HOTRG_EINVAL;
+  std::vector<double> vb(opt->batch), vh(opt->batch);
+  for (int i = 0; i < opt->batch; ++i) {
+    vb[i] = opt->beta ? opt->beta[i] : beta;
+    vh[i] = opt->h ? opt->h[i] : h;
+    if (!(vb[i] > 0.0) || !std::isfinite(vb[i]) || !std::isfinite(vh[i])) return HOTRG_EINVAL;
+  }
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HOTRG_EDEVICE;
+  }
+  if (!(prop.major == 10 && prop.minor == 3)) return HOTRG_EDEVICE;
+  hotrg_ctx* c = new hotrg_ctx();
+  c->d = d;
+  c->Dcut = Dcut;
+  c->batch = opt->batch;
+  c->precision = opt->precision;
+  c->fp64_steps = opt->fp64_steps;
+  c->x6_steps = opt->x6_steps;
+  c->max_steps = opt->max_steps;
+  c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
+  c->stream = static_cast<cudaStream_t>(opt->stream);
+  c->beta = vb;
+  c->h = vh;
+  const size_t need = carve(c, nullptr);
+  if (!opt->workspace || opt->workspace_bytes < need ||
+      (reinterpret_cast<uintptr_t>(opt->workspace) % kAlign)) {
+    delete c;
+    return HOTRG_ENOMEM;
+  }
+  carve(c, static_cast<char*>(opt->workspace));
+  for (int b = 0; b < d; ++b) c->dims[b] = 2;
+  cudaStream_t s = c->stream;
+  cudaMemsetAsync(c->status, 0, sizeof(int) * 64, s);
+  cudaMemsetAsync(c->L, 0, sizeof(double) * c->batch, s);
+  cudaMemsetAsync(c->lnc_log, 0, sizeof(double) * c->batch * (c->max_steps + 1), s);
+  cudaMemsetAsync(c->spec_log, 0, sizeof(double) * c->batch * c->spec_stride, s);
+  cudaMemcpyAsync(c->dbeta, vb.data(), sizeof(double) * c->batch, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(c->dh, vh.data(), sizeof(double) * c->batch, cudaMemcpyHostToDevice, s);
+  const long long P2 = c->Pmax * c->Pmax;
+  launch_init_tensor(c->T, P2, c->batch, d, c->dbeta, c->dh, s);
+  const long long n0 = 1LL << (2 * d);
+  Geom g = make_geom(d, c->dims);
+  for (int i = 0; i < c->batch; ++i) {
+    double* Ti = c->T + i * P2;
+    launch_norm_log(Ti, n0, c->norm_partial, c->cval + i, c->lnc_log + (long long)i * (c->max_steps + 1),
+                    c->L + i, 0, c->status, s);
+    launch_scale(Ti, Ti, n0, c->cval + i, s);
+    launch_trace_x(Ti, g, d - 1, c->L + i, 0, c->out3 + 3 * i, c->status, s);
+  }
+  if (cuda_err(c)) {
+    delete c;
+    return HOTRG_EDEVICE;
+  }
+  *out = c;
+  return HOTRG_OK;
+}
+
+int hotrg_step(hotrg_ctx* c, int axis) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (axis < -1 || axis >= c->d) return HOTRG_EINVAL;
+  if (c->steps >= c->max_steps) return HOTRG_ESTATE;
+  const int a = axis >= 0 ? axis : c->d - 1 - (c->steps % c->d);
+  const int step = c->steps + 1;
+  Geom g = make_geom(c->d, c->dims);
+  int chi[kMaxD], trans[kMaxD], nt = 0, nd[kMaxD];
+  for (int b = 0; b < c->d; ++b) {
+    nd[b] = c->dims[b];
+    chi[b] = c->dims[b];
+    if (b != a) {
+      const long long sq = (long long)c->dims[b] * c->dims[b];
+      chi[b] = (int)(sq < c->Dcut ? sq : c->Dcut);
+      nd[b] = chi[b];
+      trans[nt++] = b;
+    }
+  }
+  Geom gn = make_geom(c->d, nd);
+  const int planes = planes_for_step(c->precision, step, c->fp64_steps, c->x6_steps, g.P);
+  cudaStream_t s = c->stream;
+  const long long P2max = c->Pmax * c->Pmax;
+  PhaseScope step_scope(c, PH_STEP);
+  for (int i = 0; i < c->batch; ++i) {
+    const double* Ti = c->T + i * P2max;
+    // 1. isometries
+    PhaseScope* iso_scope = new PhaseScope(c, PH_ISO);
+    for (int t = 0; t < nt; ++t) {
+      const int b = trans[t];
+      const int n = g.D[b] * g.D[b];
+      double* Gb = c->G + (long long)b * kMaxGram * kMaxGram;
+      double* Ub = c->U + (long long)b * kMaxBond * kMaxGram;
+      launch_half_gram(Ti, g, b, c->d + a, c->gpartial, c->Q1, s);
+      launch_half_gram(Ti, g, b, a, c->gpartial, c->Q2, s);
+      launch_gram_combine(c->Q1, c->Q2, g.D[b], g.D[a], Gb, s);
+      double* ev = c->spec_log + i * c->spec_stride + ((long long)(step - 1) * c->d + b) * kSpecCap;
+      launch_eig(Gb, n, chi[b], ev, Ub, c->ework, c->status, s);
+    }
+    delete iso_scope;
+    // 2-3. squeeze into Tnext
+    const int rc = planes ? squeeze<float>(c, Ti, g, gn, a, chi, trans, nt, planes)
+                          : squeeze<double>(c, Ti, g, gn, a, chi, trans, nt, 0);
+    if (rc) return c->sticky = rc;
+    // 4. normalise, accumulate, measure
+    PhaseScope norm_scope(c, PH_NORM);
+    double* Tw = c->T + i * P2max;
+    launch_norm_log(c->Tnext, gn.P * gn.P, c->norm_partial, c->cval + i,
+                    c->lnc_log + (long long)i * (c->max_steps + 1), c->L + i, step, c->status, s);
+    launch_scale(c->Tnext, Tw, gn.P * gn.P, c->cval + i, s);
+    launch_trace_x(Tw, gn, a, c->L + i, step, c->out3 + 3 * i, c->status, s);
+  }
+  if (cuda_err(c)) return HOTRG_EDEVICE;
+  for (int b = 0; b < c->d; ++b) c->hist_dims[step - 1][b] = c->dims[b];
+  c->hist_axis[step - 1] = a;
+  for (int b = 0; b < c->d; ++b) c->dims[b] = nd[b];
+  c->steps = step;
+  c->last_axis = a;
+  if (c->timing) {
+    double f = 2.0 * (double)g.P * (double)g.P * (double)g.P * c->batch;
+    for (int t = 0; t < nt; ++t) f *= chi[trans[t]];
+    c->t_step_flops += f;
+    ++c->t_steps;
+  }
+  return HOTRG_OK;
+}
+
+int hotrg_free_energy(hotrg_ctx* c, double* lnz, double* f) {
+  if (!c) return HOTRG_EINVAL;
+  const int rc = sync_check(c);
+  if (rc) return rc;
+  std::vector<double> o3(3 * c->batch);
+  if (cudaMemcpy(o3.data(), c->out3, sizeof(double) * 3 * c->batch, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
+  for (int i = 0; i < c->batch; ++i) {
+    if (!(o3[3 * i] > 0.0)) return HOTRG_ENUMERIC;  // the flow state itself stays valid
+    if (lnz) lnz[i] = o3[3 * i + 1];
+    if (f) f[i] = -o3[3 * i + 1] / c->beta[i];
+  }
+  return HOTRG_OK;
+}
+
+int hotrg_observables(hotrg_ctx* c, int instance, hotrg_obs* out) {
+  if (!c || !out || instance < 0 || instance >= c->batch) return HOTRG_EINVAL;
+  const int rc = sync_check(c);
+  if (rc) return rc;
+  double o3[3], lc = 0.0;
+  if (cudaMemcpy(o3, c->out3 + 3 * instance, sizeof(o3), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&lc, c->lnc_log + (long long)instance * (c->max_steps + 1) + c->steps, sizeof(double),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
+  out->steps = c->steps;
+  out->last_axis = c->last_axis;
+  out->lnz_per_site = o3[1];
+  out->last_ln_c = lc;
+  out->x_indicator = c->steps ? o3[2] : 1.0;
+  return HOTRG_OK;
+}
+
+int hotrg_spectra(hotrg_ctx* c, int step, int axis, int instance, double* buf, int cap, int* n_out) {
+  if (!c || !n_out || step < 1 || step > c->steps || axis < 0 || axis >= c->d || instance < 0 ||
+      instance >= c->batch || cap < 0 || (cap > 0 && !buf))
+    return HOTRG_EINVAL;
+  const int rc = sync_check(c);
+  if (rc) return rc;
+  const int n = (axis == c->hist_axis[step - 1]) ? 0 : c->hist_dims[step - 1][axis] * c->hist_dims[step - 1][axis];
+  std::vector<double> tmp(kSpecCap);
+  const double* src = c->spec_log + instance * c->spec_stride + ((long long)(step - 1) * c->d + axis) * kSpecCap;
+  if (n > 0 && cudaMemcpy(tmp.data(), src, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
+  *n_out = n;
+  for (int i = 0; i < n && i < cap; ++i) buf[i] = tmp[i];
+  return HOTRG_OK;
+}
+
+int hotrg_ln_norms(hotrg_ctx* c, int instance, double* buf, int cap, int* n_out) {
+  if (!c || !n_out || instance < 0 || instance >= c->batch || cap < 0 || (cap > 0 && !buf))
+    return HOTRG_EINVAL;
+  const int rc = sync_check(c);
+  if (rc) return rc;
+  const int n = c->steps + 1;
+  std::vector<double> tmp(n);
+  if (cudaMemcpy(tmp.data(), c->lnc_log + (long long)instance * (c->max_steps + 1), sizeof(double) * n,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
+  *n_out = n;
+  for (int i = 0; i < n && i < cap; ++i) buf[i] = tmp[i];
+  return HOTRG_OK;
+}
+
+int hotrg_get_tensor(hotrg_ctx* c, int instance, int* dims, double* host, size_t cap) {
+  if (!c || instance < 0 || instance >= c->batch) return HOTRG_EINVAL;
+  if (dims)
+    for (int b = 0; b < c->d; ++b) dims[b] = c->dims[b];
+  if (!host) return HOTRG_OK;
+  Geom g = make_geom(c->d, c->dims);
+  if (cap < (size_t)(g.P * g.P)) return HOTRG_EINVAL;
+  const int rc = sync_check(c);
+  if (rc) return rc;
+  if (cudaMemcpy(host, c->T + instance * c->Pmax * c->Pmax, sizeof(double) * g.P * g.P,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
+  return HOTRG_OK;
+}
+
+int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* host) {
+  if (!c || !dims || !host || instance < 0 || instance >= c->batch) return HOTRG_EINVAL;
+  if (c->sticky) return c->sticky;
+  for (int b = 0; b < c->d; ++b)
+    if (dims[b] < 1 || dims[b] > c->Dcut) return HOTRG_EINVAL;
+  // all instances share the bond dimensions
+  if (c->batch > 1)
+    for (int b = 0; b < c->d; ++b)
+      if (dims[b] != c->dims[b]) return HOTRG_EINVAL;
+  Geom g = make_geom(c->d, dims);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemcpy(c->T + instance * c->Pmax * c->Pmax, host, sizeof(double) * g.P * g.P,
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
+  for (int b = 0; b < c->d; ++b) c->dims[b] = dims[b];
+  return HOTRG_OK;
+}
+
+// ---- checkpoint format: header, then per instance T (P^2), L, lnc_log, spec_log, out3
+struct StateHeader {
+  char magic[8];
+  int version, d, Dcut, batch, precision, max_steps, steps, last_axis;
+  int dims[kMaxD];
+  long long P;
+  int hist_dims[64][kMaxD];
+  int hist_axis[64];
+};
+
+int hotrg_state_size(hotrg_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return HOTRG_EINVAL;
+  Geom g = make_geom(c->d, c->dims);
+  const size_t per = sizeof(double) * ((size_t)g.P * g.P + 1 + (c->max_steps + 1) + c->spec_stride + 3);
+  *bytes = sizeof(StateHeader) + per * c->batch;
+  return HOTRG_OK;
+}
+
+int hotrg_state_save(hotrg_ctx* c, void* host, size_t cap) {
+  size_t need = 0;
+  if (hotrg_state_size(c, &need) || !host || cap < need) return HOTRG_EINVAL;
+  const int rc = sync_check(c);
+  if (rc) return rc;
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "HOTRGST", 8);
+  h.version = 1;
+  h.d = c->d; h.Dcut = c->Dcut; h.batch = c->batch; h.precision = c->precision;
+  h.max_steps = c->max_steps; h.steps = c->steps; h.last_axis = c->last_axis;
+  for (int b = 0; b < kMaxD; ++b) h.dims[b] = c->dims[b];
+  std::memcpy(h.hist_dims, c->hist_dims, sizeof(h.hist_dims));
+  std::memcpy(h.hist_axis, c->hist_axis, sizeof(h.hist_axis));
+  Geom g = make_geom(c->d, c->dims);
+  h.P = g.P;
+  char* p = static_cast<char*>(host);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  for (int i = 0; i < c->batch; ++i) {
+    bool ok = cudaMemcpy(p, c->T + i * c->Pmax * c->Pmax, sizeof(double) * g.P * g.P, cudaMemcpyDeviceToHost) == cudaSuccess;
+    p += sizeof(double) * g.P * g.P;
+    ok = ok && cudaMemcpy(p, c->L + i, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess;
+    p += sizeof(double);
+    ok = ok && cudaMemcpy(p, c->lnc_log + (long long)i * (c->max_steps + 1), sizeof(double) * (c->max_steps + 1),
+                          cudaMemcpyDeviceToHost) == cudaSuccess;
+    p += sizeof(double) * (c->max_steps + 1);
+    ok = ok && cudaMemcpy(p, c->spec_log + i * c->spec_stride, sizeof(double) * c->spec_stride,
+                          cudaMemcpyDeviceToHost) == cudaSuccess;
+    p += sizeof(double) * c->spec_stride;
+    ok = ok && cudaMemcpy(p, c->out3 + 3 * i, sizeof(double) * 3, cudaMemcpyDeviceToHost) == cudaSuccess;
+    p += sizeof(double) * 3;
+    if (!ok) return c->sticky = HOTRG_EDEVICE;
+  }
+  return HOTRG_OK;
+}
+
+int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
+  if (!c || !host || size < sizeof(StateHeader)) return HOTRG_EINVAL;
+  StateHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (std::memcmp(h.magic, "HOTRGST", 8) || h.version != 1 || h.d != c->d || h.Dcut != c->Dcut ||
+      h.batch != c->batch || h.precision != c->precision || h.max_steps != c->max_steps)
+    return HOTRG_EINVAL;
+  Geom g = make_geom(h.d, h.dims);
+  if (g.P != h.P || g.P > c->Pmax) return HOTRG_EINVAL;
+  const size_t per = sizeof(double) * ((size_t)g.P * g.P + 1 + (c->max_steps + 1) + c->spec_stride + 3);
+  if (size < sizeof(StateHeader) + per * c->batch) return HOTRG_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return c->sticky = HOTRG_EDEVICE;
+  const char* p = static_cast<const char*>(host) + sizeof(h);
+  for (int i = 0; i < c->batch; ++i) {
+    bool ok = cudaMemcpy(c->T + i * c->Pmax * c->Pmax, p, sizeof(double) * g.P * g.P, cudaMemcpyHostToDevice) == cudaSuccess;
+    p += sizeof(double) * g.P * g.P;
+    ok = ok && cudaMemcpy(c->L + i, p, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+    p += sizeof(double);
+    ok = ok && cudaMemcpy(c->lnc_log + (long long)i * (c->max_steps + 1), p, sizeof(double) * (c->max_steps + 1),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+    p += sizeof(double) * (c->max_steps + 1);
+    ok = ok && cudaMemcpy(c->spec_log + i * c->spec_stride, p, sizeof(double) * c->spec_stride,
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+    p += sizeof(double) * c->spec_stride;
+    ok = ok && cudaMemcpy(c->out3 + 3 * i, p, sizeof(double) * 3, cudaMemcpyHostToDevice) == cudaSuccess;
+    p += sizeof(double) * 3;
+    if (!ok) return c->sticky = HOTRG_EDEVICE;
+  }
+  for (int b = 0; b < kMaxD; ++b) c->dims[b] = h.dims[b];
+  std::memcpy(c->hist_dims, h.hist_dims, sizeof(h.hist_dims));
+  std::memcpy(c->hist_axis, h.hist_axis, sizeof(h.hist_axis));
+  c->steps = h.steps;
+  c->last_axis = h.last_axis;
+  return HOTRG_OK;
+}
+
+int hotrg_timing_start(hotrg_ctx* c) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->sticky) return c->sticky;
+  for (auto& e : c->evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  c->evs.clear();
+  c->timing = true;
+  c->launch0 = launches_total();
+  c->t_gemm_launches = c->t_steps = 0;
+  c->t_gemm_flops = c->t_gemm_tflops = c->t_step_flops = 0;
+  return HOTRG_OK;
+}
+
+int hotrg_timing_stop(hotrg_ctx* c, hotrg_timing* out) {
+  if (!c || !out) return HOTRG_EINVAL;
+  const int rc = sync_check(c);
+  c->timing = false;
+  if (rc) return rc;
+  double ms[PH_COUNT] = {0, 0, 0, 0, 0, 0};
+  for (auto& e : c->evs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ms[e.phase] += t;
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  c->evs.clear();
+  std::memset(out, 0, sizeof(*out));
+  out->ms_step = ms[PH_STEP];
+  out->ms_isometry = ms[PH_ISO];
+  out->ms_operands = ms[PH_OPERANDS];
+  out->ms_gemm = ms[PH_GEMM];
+  out->ms_epilogue = ms[PH_EPILOGUE];
+  out->ms_norm = ms[PH_NORM];
+  out->steps = c->t_steps;
+  out->gemm_launches = c->t_gemm_launches;
+  out->kernel_launches = launches_total() - c->launch0;
+  out->gemm_flops = c->t_gemm_flops;
+  out->gemm_tensor_flops = c->t_gemm_tflops;
+  out->step_flops = c->t_step_flops;
+  cudaGetLastError();
+  return HOTRG_OK;
+}
+
+void hotrg_destroy(hotrg_ctx* c) {
+  if (!c) return;
+  for (auto& e : c->evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  delete c;
+}
+
+const char* hotrg_strerror(int code) {
+  switch (code) {
+    case HOTRG_OK: return "ok";
+    case HOTRG_EINVAL: return "invalid argument";
+    case HOTRG_ENOMEM: return "workspace too small or misaligned";
+    case HOTRG_ENUMERIC: return "numerical failure (NaN/Inf, zero norm or non-positive trace)";
+    case HOTRG_ENOCONV: return "eigensolver did not converge";
+    case HOTRG_ETIMEOUT: return "a bounded device-side wait gave up";
+    case HOTRG_EDEVICE: return "CUDA device error or no sm_103 device";
+    case HOTRG_ESTATE: return "call not valid in the current state";
+    case HOTRG_ENOTSUP: return "not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+// ---- kernel-level GEMM entry point
+size_t hotrg_gemm_scratch_bytes(long long M, long long N, long long K) {
+  if (M <= 0 || N <= 0 || K <= 0) return 0;
+  const long long ld = round_up(K, 64);
+  return (size_t)kAlign + 3 * (size_t)round_up(M * ld * 2, kAlign) + 3 * (size_t)round_up(N * ld * 2, kAlign);
+}
+
+int hotrg_gemm_split(const float* A, long long lda, const float* Bt, long long ldb, float* C, long long ldc,
+                     long long M, long long N, long long K, int npass, void* scratch, size_t scratch_bytes,
+                     void* stream) {
+  if (!A || !Bt || !C || !scratch || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
+  if (npass != 1 && npass != 3 && npass != 6) return HOTRG_EINVAL;
+  if (scratch_bytes < hotrg_gemm_scratch_bytes(M, N, K) || (reinterpret_cast<uintptr_t>(scratch) % kAlign))
+    return HOTRG_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long ld = round_up(K, 64);
+  char* p = static_cast<char*>(scratch);
+  int* status = reinterpret_cast<int*>(p);
+  p += kAlign;
+  const int nparts = npass == 1 ? 1 : (npass == 3 ? 2 : 3);
+  Planes<__nv_bfloat16> Ap, Bp;
+  Ap.nparts = Bp.nparts = nparts;
+  for (int k = 0; k < 3; ++k) {
+    Ap.p[k] = reinterpret_cast<__nv_bfloat16*>(p);
+    p += round_up(M * ld * 2, kAlign);
+  }
+  for (int k = 0; k < 3; ++k) {
+    Bp.p[k] = reinterpret_cast<__nv_bfloat16*>(p);
+    p += round_up(N * ld * 2, kAlign);
+  }
+  cudaMemsetAsync(status, 0, sizeof(int), s);
+  launch_split_rows(A, lda, M, K, Ap, ld, s);
+  launch_split_rows(Bt, ldb, N, K, Bp, ld, s);
+  const int rc = launch_gemm_split(Ap, ld, Bp, ld, C, ldc, M, N, K, npass, status, 4.0, s);
+  if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
+}
+
+int hotrg_gemm_status(const void* scratch, void* stream) {
+  if (!scratch) return HOTRG_EINVAL;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return HOTRG_EDEVICE;
+  int bits = 0;
+  if (cudaMemcpy(&bits, scratch, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HOTRG_EDEVICE;
+  return status_to_code(bits);
+}
+
+}  // extern "C"

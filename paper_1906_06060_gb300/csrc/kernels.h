@@ -1,0 +1,80 @@
+// Host-side launchers of the libhotrg kernels. All launch on the given stream and return
+// immediately; errors surface through cudaGetLastError() and the device status word.
+#pragma once
+#include "common.cuh"
+
+namespace hotrg {
+
+// Number of kernels the launchers below have enqueued in this process (diagnostics: lets a
+// caller count the library's launches inside a timed region).
+void count_launches(int n);
+long long launches_total();
+
+// ---- kernels_tensor.cu --------------------------------------------------------------------
+// T^(0) (Sec. 2) for `batch` instances: T + i*stride gets beta[i], h[i] (device arrays).
+void launch_init_tensor(double* T, long long inst_stride, int batch, int d, const double* beta,
+                        const double* h, cudaStream_t s);
+// c = ||x||_F (deterministic), lnc_log[step] = ln c, L += 2^-step ln c, status on bad norm.
+void launch_norm_log(const double* x, long long n, double* partial, double* c_out,
+                     double* lnc_log, double* L, int step, int* status, cudaStream_t s);
+// dst = src / *c
+void launch_scale(const double* src, double* dst, long long n, const double* c, cudaStream_t s);
+// Tr T (Eq. (tTr)) and ln Z/N = L + 2^-step ln Tr; X^(n) along `axis` (Eq. (x)).
+void launch_trace_x(const double* T, Geom g, int axis, const double* L, int step, double* out3,
+                    int* status, cudaStream_t s);
+// out[..u_b=j..] = sum_i U[kk][i][j] in[..u_b=i..] on unprimed leg b (U: [chi][Db][Db] fp64).
+template <class Tin, class Tout>
+void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double* U, int kk,
+                          cudaStream_t s);
+// Tt[p][u] = T[u][p] (P x P), converted to Tout.
+template <class Tout>
+void launch_transpose(const double* T, Tout* Tt, long long P, cudaStream_t s);
+// B operand, K-major: Bt[(j*P + n)][k] = sum_x U3[j][k_c3][x] Tt[n][k | c3 := x], j < chi3.
+// c3 < 0: Bt = Tt. Mixed: 2 or 3 bf16 planes; FP64: one double plane.
+template <class Tin, class Tout>
+void launch_build_bt(const Tin* Tt, const Planes<Tout>& out, long long ld, Geom g, int c3,
+                     const double* U3, int chi3, cudaStream_t s);
+// A operand, K-major: Y[m][k] = X[u = (k_b, m_a)][p = (m_b, k_a)] for a step along `a`.
+template <class Tin, class Tout>
+void launch_build_y(const Tin* X, const Planes<Tout>& out, long long ld, Geom g, int a,
+                    cudaStream_t s);
+// Generic pair contraction / strided copy (see View): out[o] = sum_{i,j} U[k'][i][j] in[...].
+template <class Tin, class Tout>
+void launch_pair_contract(const Tin* in, Tout* out, const View& v, int kaxis, int Di, int Dj,
+                          long long si, long long sj, const double* U, int chi, long long in_base,
+                          long long out_base, cudaStream_t s);
+
+// ---- gram.cu -------------------------------------------------------------------------------
+// Q[(i,al)][(i~,al~)] = sum over all other legs of T[..i..al..] T[..i~..al~..]; legs l1, l2 are
+// positions 0..2d-1 in the natural layout. partial: nsplit * nr^2 doubles scratch.
+int gram_nsplit();
+void launch_half_gram(const double* T, Geom g, int l1, int l2, double* partial, double* Q,
+                      cudaStream_t s);
+// G[(b1 b2)][(b1~ b2~)] = sum_{al,al~} Q1[(b1,al)][(b1~,al~)] Q2[(b2,al)][(b2~,al~)]
+void launch_gram_combine(const double* Q1, const double* Q2, int Db, int Da, double* G,
+                         cudaStream_t s);
+
+// ---- eig.cu --------------------------------------------------------------------------------
+// Symmetric eigendecomposition of G (n x n, n <= 256) by cyclic Jacobi; eigenvalues sorted
+// descending into evals[0..n), the leading chi eigenvectors, sign-fixed, into U[k][0..n).
+// work: 2*n*n + 4*n doubles. Sets ST_NOCONV on the sweep limit.
+void launch_eig(const double* G, int n, int chi, double* evals, double* U, double* work,
+                int* status, cudaStream_t s);
+
+// ---- gemm_simt.cu --------------------------------------------------------------------------
+// C[m][n] = sum_k A[m][k] Bt[n][k] in FP64 (CUDA cores).
+void launch_gemm_f64(const double* A, long long lda, const double* Bt, long long ldb, double* C,
+                     long long ldc, long long M, long long N, long long K, cudaStream_t s);
+
+// ---- gemm_tc.cu ----------------------------------------------------------------------------
+// C[m][n] = sum over passes p of sum_k A_{a(p)}[m][k] Bt_{b(p)}[n][k], bf16 operand planes on
+// tcgen05, FP32 accumulation in TMEM. npass = 1: (hi,hi); 3: + (hi,lo), (lo,hi) with 2 planes;
+// 6: (hi,hi), (hi,mid), (mid,hi), (hi,lo), (mid,mid), (lo,hi) with 3 planes (hi, mid, lo).
+// Returns 0 or a hotrg_status (tensor-map encode failure, bad alignment or sizes).
+int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
+                      long long ldb, float* C, long long ldc, long long M, long long N, long long K,
+                      int npass, int* status, double timeout_s, cudaStream_t s);
+void launch_split_rows(const float* X, long long ldx, long long rows, long long cols,
+                       const Planes<__nv_bfloat16>& out, long long ld, cudaStream_t s);
+
+}  // namespace hotrg

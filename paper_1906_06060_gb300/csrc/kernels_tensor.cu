@@ -1,0 +1,387 @@
+// Element-wise, reduction and re-layout kernels of one HOTRG step (arXiv:1906.06060, Sec. 2).
+// The squeeze GEMM itself lives in gemm_tc.cu (tensor cores) and gemm_simt.cu (FP64).
+#include <atomic>
+#include <type_traits>
+
+#include "kernels.h"
+
+namespace hotrg {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+template <class Tout>
+using AccT = typename std::conditional<std::is_same<Tout, double>::value, double, float>::type;
+
+
+inline int grid_for(long long n, int block, int cap = 152 * 16) {
+  long long g = (n + block - 1) / block;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+constexpr int kNormBlocks = 1024;
+
+// ---------------------------------------------------------------------------- T^(0)
+// T[idx] = sum_s V_s prod_{legs} W[s, leg]; W[s,0] = sqrt(cosh b), W[s,1] = s sqrt(sinh b),
+// V_s = e^{b h s}; bit l of idx (from the most significant) is the index of leg l.
+__global__ void k_init_tensor(double* T, long long inst_stride, int d, const double* beta,
+                              const double* hfield) {
+  const int nlegs = 2 * d;
+  const int total = 1 << nlegs;
+  const int inst = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const double b = beta[inst], h = hfield[inst];
+  const double wc = sqrt(cosh(b)), ws = sqrt(sinh(b));
+  double acc = 0.0;
+  for (int si = 0; si < 2; ++si) {
+    const double s = si ? -1.0 : 1.0;
+    double v = exp(s * b * h);
+    for (int l = 0; l < nlegs; ++l) {
+      const int bit = (idx >> (nlegs - 1 - l)) & 1;
+      v *= bit ? s * ws : wc;
+    }
+    acc += v;
+  }
+  T[inst * inst_stride + idx] = acc;
+}
+
+// ---------------------------------------------------------------------------- norms
+template <int BS>
+__device__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = BS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_sumsq_partial(const double* __restrict__ x, long long n,
+                                                       double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)kNormBlocks * 256) {
+    const double v = x[i];
+    s = fma(v, v, s);
+  }
+  const double t = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(256) k_norm_finish(const double* __restrict__ partial, double* c_out,
+                                                     double* lnc_log, double* L, int step, int* status) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kNormBlocks; i += 256) s += partial[i];
+  const double t = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) {
+    const double c = sqrt(t);
+    if (!(c > 0.0) || !isfinite(c)) atomic_status(status, ST_NUMERIC);
+    const double lc = log(c);
+    *c_out = c;
+    lnc_log[step] = lc;
+    *L += ldexp(lc, -step);
+  }
+}
+
+__global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst, long long n,
+                        const double* __restrict__ c) {
+  const double cv = *c;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i] / cv;
+}
+
+// ---------------------------------------------------------------------------- trace, X^(n)
+// out3[0] = Tr T, out3[1] = L + 2^-step ln Tr T, out3[2] = X^(n) along axis.
+__global__ void __launch_bounds__(256) k_trace_x(const double* __restrict__ T, Geom g, int axis,
+                                                 const double* L, int step, double* out3, int* status) {
+  __shared__ double sh[256];
+  __shared__ double A[kMaxBond * kMaxBond];
+  const long long P = g.P;
+  double s = 0.0;
+  for (long long u = threadIdx.x; u < P; u += 256) s += T[u * P + u];
+  const double tr = block_sum<256>(s, sh);
+  // A_{ij} = sum over the other slots (equal on both halves) with slot `axis` = i / j.
+  const int Da = g.D[axis];
+  const long long Sa = g.Sn[axis];
+  const long long nrest = P / Da;
+  for (int e = threadIdx.x; e < Da * Da; e += 256) {
+    const int i = e / Da, j = e % Da;
+    double acc = 0.0;
+    for (long long r = 0; r < nrest; ++r) {
+      // r enumerates the other slots: split r around slot `axis`
+      const long long hi = r / Sa, lo = r % Sa;
+      const long long base = hi * Sa * Da + lo;
+      acc += T[(base + i * Sa) * P + base + j * Sa];
+    }
+    A[e] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double trA = 0.0, trA2 = 0.0;
+    for (int i = 0; i < Da; ++i) trA += A[i * Da + i];
+    for (int i = 0; i < Da; ++i)
+      for (int j = 0; j < Da; ++j) trA2 += A[i * Da + j] * A[j * Da + i];
+    (void)status;  // a non-positive trace is reported by the free-energy query, not here
+    out3[0] = tr;
+    out3[1] = tr > 0.0 ? *L + ldexp(log(tr), -step) : nan("");
+    out3[2] = trA * trA / trA2;
+  }
+}
+
+// ---------------------------------------------------------------------------- mode product
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(256) k_mode_unprimed(const Tin* __restrict__ in, Tout* __restrict__ out,
+                                                       long long total, long long stride_b, int Db,
+                                                       const double* __restrict__ U, int kk) {
+  using Acc = AccT<Tout>;
+  __shared__ Acc W[kMaxGram];
+  for (int t = threadIdx.x; t < Db * Db; t += blockDim.x) W[t] = (Acc)U[(long long)kk * Db * Db + t];
+  __syncthreads();
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)((idx / stride_b) % Db);
+    const long long base = idx - (long long)j * stride_b;
+    Acc acc = 0;
+    for (int i = 0; i < Db; ++i) acc += W[i * Db + j] * (Acc)in[base + i * stride_b];
+    out[idx] = (Tout)acc;
+  }
+}
+
+// ---------------------------------------------------------------------------- transpose
+template <class Tout>
+__global__ void __launch_bounds__(256) k_transpose(const double* __restrict__ T, Tout* __restrict__ Tt,
+                                                   long long P) {
+  __shared__ double tile[32][33];
+  const long long r0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const long long r = r0 + k, c = c0 + threadIdx.x;
+    if (r < P && c < P) tile[k][threadIdx.x] = T[r * P + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const long long r = c0 + k, c = r0 + threadIdx.x;  // Tt[r][c] = T[c][r]
+    if (r < P && c < P) Tt[r * P + c] = (Tout)tile[threadIdx.x][k];
+  }
+}
+
+// ---------------------------------------------------------------------------- B operand
+// Bt[(j*P + n)][k] = sum_x U3[j][k_c3][x] Tt[n][k | c3 := x]
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(256) k_build_bt(const Tin* __restrict__ Tt, Planes<Tout> out,
+                                                  long long ld, long long P,
+                                                  long long Sc, int Dc, const double* __restrict__ U3,
+                                                  int chi3) {
+  using Acc = AccT<Tout>;
+  extern __shared__ unsigned char smraw[];
+  Acc* W = reinterpret_cast<Acc*>(smraw);  // [chi3][Dc][Dc]
+  const int nW = chi3 * Dc * Dc;
+  for (int t = threadIdx.x; t < nW; t += blockDim.x) W[t] = U3 ? (Acc)U3[t] : (Acc)1;
+  __syncthreads();
+  const long long total = (long long)chi3 * P * P;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long k = idx % P;
+    const long long row = idx / P;  // j*P + n
+    const long long n = row % P;
+    const int j = (int)(row / P);
+    Acc acc;
+    if (Sc > 0) {
+      const int kc = (int)((k / Sc) % Dc);
+      const long long base = n * P + k - (long long)kc * Sc;
+      const Acc* w = W + ((long long)j * Dc + kc) * Dc;
+      acc = 0;
+      for (int x = 0; x < Dc; ++x) acc += w[x] * (Acc)Tt[base + x * Sc];
+    } else {
+      acc = (Acc)Tt[n * P + k];
+    }
+    store_planes(out, row * ld + k, acc);
+  }
+}
+
+// ---------------------------------------------------------------------------- A operand
+// Y[m][k] = X[R(k) + C(m)], R(k) = sum_{b!=a} k_b Sn_b P + k_a Sn_a, C(m) = sum_{b!=a} m_b Sn_b + m_a Sn_a P.
+// Tiles of 32 x 32; when a is the fastest slot the source is contiguous along k (no transpose),
+// otherwise along m (transpose through shared memory).
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(256) k_build_y(const Tin* __restrict__ X, Planes<Tout> out, long long ld,
+                                                 Geom g, int a) {
+  using Acc = AccT<Tout>;
+  __shared__ Acc tile[32][33];
+  __shared__ long long Rk[32], Cm[32];
+  const long long P = g.P;
+  const long long m0 = (long long)blockIdx.y * 32, k0 = (long long)blockIdx.x * 32;
+  if (threadIdx.y == 0) {
+    const long long k = k0 + threadIdx.x, m = m0 + threadIdx.x;
+    long long rk = 0, cm = 0;
+    for (int b = 0; b < g.d; ++b) {
+      const long long kb = (k / g.Sn[b]) % g.D[b];
+      const long long mb = (m / g.Sn[b]) % g.D[b];
+      if (b == a) { rk += kb * g.Sn[b]; cm += mb * g.Sn[b] * P; }
+      else        { rk += kb * g.Sn[b] * P; cm += mb * g.Sn[b]; }
+    }
+    Rk[threadIdx.x] = rk;
+    Cm[threadIdx.x] = cm;
+  }
+  __syncthreads();
+  const bool a_fast = (a == g.d - 1);
+  if (a_fast) {
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      const long long m = m0 + r, k = k0 + threadIdx.x;
+      if (m < P && k < P) store_planes(out, m * ld + k, (Acc)X[Rk[threadIdx.x] + Cm[r]]);
+    }
+  } else {
+    for (int r = threadIdx.y; r < 32; r += 8) {  // r indexes k, threadIdx.x indexes m
+      const long long k = k0 + r, m = m0 + threadIdx.x;
+      if (m < P && k < P) tile[r][threadIdx.x] = (Acc)X[Rk[r] + Cm[threadIdx.x]];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {  // r indexes m, threadIdx.x indexes k
+      const long long m = m0 + r, k = k0 + threadIdx.x;
+      if (m < P && k < P) store_planes(out, m * ld + k, tile[threadIdx.x][r]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- pair contraction
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(256) k_pair_contract(const Tin* __restrict__ in, Tout* __restrict__ out,
+                                                       View v, long long total, int kaxis, int Di, int Dj,
+                                                       long long si, long long sj,
+                                                       const double* __restrict__ U, int chi,
+                                                       long long in_base, long long out_base) {
+  using Acc = AccT<Tout>;
+  extern __shared__ unsigned char smraw[];
+  Acc* W = reinterpret_cast<Acc*>(smraw);  // [chi][Di][Dj]
+  const int nW = chi * Di * Dj;
+  for (int t = threadIdx.x; t < nW; t += blockDim.x) W[t] = U ? (Acc)U[t] : (Acc)1;
+  __syncthreads();
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long rem = idx, ioff = in_base, ooff = out_base;
+    int kp = 0;
+    for (int ax = v.ndim - 1; ax >= 0; --ax) {
+      const long long c = rem % v.shape[ax];
+      rem /= v.shape[ax];
+      ioff += c * v.in_stride[ax];
+      ooff += c * v.out_stride[ax];
+      if (ax == kaxis) kp = (int)c;
+    }
+    const Acc* w = W + (long long)kp * Di * Dj;
+    Acc acc = 0;
+    for (int i = 0; i < Di; ++i) {
+      const Tin* src = in + ioff + i * si;
+      for (int j = 0; j < Dj; ++j) acc += w[i * Dj + j] * (Acc)src[j * sj];
+    }
+    out[ooff] = (Tout)acc;
+  }
+}
+
+}  // namespace
+
+// ============================================================================ launchers
+void launch_init_tensor(double* T, long long inst_stride, int batch, int d, const double* beta,
+                        const double* h, cudaStream_t s) {
+  const int total = 1 << (2 * d);
+  dim3 grid((total + 255) / 256, batch);
+  k_init_tensor<<<grid, 256, 0, s>>>(T, inst_stride, d, beta, h);
+  count_launches(1);
+}
+
+void launch_norm_log(const double* x, long long n, double* partial, double* c_out, double* lnc_log,
+                     double* L, int step, int* status, cudaStream_t s) {
+  k_sumsq_partial<<<kNormBlocks, 256, 0, s>>>(x, n, partial);
+  count_launches(1);
+  k_norm_finish<<<1, 256, 0, s>>>(partial, c_out, lnc_log, L, step, status);
+  count_launches(1);
+}
+
+void launch_scale(const double* src, double* dst, long long n, const double* c, cudaStream_t s) {
+  k_scale<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n, c);
+  count_launches(1);
+}
+
+void launch_trace_x(const double* T, Geom g, int axis, const double* L, int step, double* out3,
+                    int* status, cudaStream_t s) {
+  k_trace_x<<<1, 256, 0, s>>>(T, g, axis, L, step, out3, status);
+  count_launches(1);
+}
+
+template <class Tin, class Tout>
+void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double* U, int kk,
+                          cudaStream_t s) {
+  const long long total = g.P * g.P;
+  k_mode_unprimed<Tin, Tout><<<grid_for(total, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
+                                                                   g.D[b], U, kk);
+  count_launches(1);
+}
+
+template <class Tout>
+void launch_transpose(const double* T, Tout* Tt, long long P, cudaStream_t s) {
+  dim3 grid((unsigned)((P + 31) / 32), (unsigned)((P + 31) / 32));
+  k_transpose<Tout><<<grid, dim3(32, 8), 0, s>>>(T, Tt, P);
+  count_launches(1);
+}
+
+template <class Tin, class Tout>
+void launch_build_bt(const Tin* Tt, const Planes<Tout>& out, long long ld, Geom g, int c3,
+                     const double* U3, int chi3, cudaStream_t s) {
+  using Acc = AccT<Tout>;
+  const long long Sc = c3 >= 0 ? g.Sn[c3] : 0;
+  const int Dc = c3 >= 0 ? g.D[c3] : 1;
+  const int nchi = c3 >= 0 ? chi3 : 1;
+  const size_t smem = sizeof(Acc) * (size_t)nchi * Dc * Dc;
+  const long long total = (long long)nchi * g.P * g.P;
+  k_build_bt<Tin, Tout><<<grid_for(total, 256), 256, smem, s>>>(Tt, out, ld, g.P, Sc, Dc,
+                                                                 c3 >= 0 ? U3 : nullptr, nchi);
+  count_launches(1);
+}
+
+template <class Tin, class Tout>
+void launch_build_y(const Tin* X, const Planes<Tout>& out, long long ld, Geom g, int a,
+                    cudaStream_t s) {
+  dim3 grid((unsigned)((g.P + 31) / 32), (unsigned)((g.P + 31) / 32));
+  k_build_y<Tin, Tout><<<grid, dim3(32, 8), 0, s>>>(X, out, ld, g, a);
+  count_launches(1);
+}
+
+template <class Tin, class Tout>
+void launch_pair_contract(const Tin* in, Tout* out, const View& v, int kaxis, int Di, int Dj,
+                          long long si, long long sj, const double* U, int chi, long long in_base,
+                          long long out_base, cudaStream_t s) {
+  using Acc = AccT<Tout>;
+  long long total = 1;
+  for (int i = 0; i < v.ndim; ++i) total *= v.shape[i];
+  const int nchi = U ? chi : 1;
+  const size_t smem = sizeof(Acc) * (size_t)nchi * Di * Dj;
+  k_pair_contract<Tin, Tout><<<grid_for(total, 256), 256, smem, s>>>(in, out, v, total, kaxis, Di, Dj,
+                                                                      si, sj, U, nchi, in_base, out_base);
+  count_launches(1);
+}
+
+// explicit instantiations: FP64 path (double everywhere) and BF16X3 path (float intermediates)
+template void launch_mode_unprimed<double, double>(const double*, double*, Geom, int, const double*, int, cudaStream_t);
+template void launch_mode_unprimed<double, float>(const double*, float*, Geom, int, const double*, int, cudaStream_t);
+template void launch_mode_unprimed<float, float>(const float*, float*, Geom, int, const double*, int, cudaStream_t);
+template void launch_transpose<double>(const double*, double*, long long, cudaStream_t);
+template void launch_transpose<float>(const double*, float*, long long, cudaStream_t);
+template void launch_build_bt<double, double>(const double*, const Planes<double>&, long long, Geom, int, const double*, int, cudaStream_t);
+template void launch_build_bt<float, __nv_bfloat16>(const float*, const Planes<__nv_bfloat16>&, long long, Geom, int, const double*, int, cudaStream_t);
+template void launch_build_y<double, double>(const double*, const Planes<double>&, long long, Geom, int, cudaStream_t);
+template void launch_build_y<float, __nv_bfloat16>(const float*, const Planes<__nv_bfloat16>&, long long, Geom, int, cudaStream_t);
+template void launch_build_y<double, __nv_bfloat16>(const double*, const Planes<__nv_bfloat16>&, long long, Geom, int, cudaStream_t);
+template void launch_pair_contract<double, double>(const double*, double*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
+template void launch_pair_contract<float, float>(const float*, float*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
+template void launch_pair_contract<float, double>(const float*, double*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
+
+}  // namespace hotrg

@@ -1,0 +1,97 @@
+"""The C-ABI library builds, loads and exports every symbol include/hotrg.h declares (no GPU:
+only host-side entry points are called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1906_06060_gb300 import build
+    from paper_1906_06060_gb300 import _lib
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hotrg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hotrg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1906_06060_gb300 import _lib
+    assert set(declared_functions()) <= set(_lib._SIGS)
+
+
+def test_opts_defaults(lib):
+    from paper_1906_06060_gb300 import _lib
+    o = _lib.Opts()
+    lib.hotrg_opts_default(ctypes.byref(o))
+    assert (o.precision, o.fp64_steps, o.batch, o.max_steps) == (0, 2, 1, 64)
+    assert o.wait_timeout_s == 4.0
+
+
+def test_workspace_size_and_argument_checks(lib):
+    from paper_1906_06060_gb300 import _lib
+    n = ctypes.c_size_t()
+    assert lib.hotrg_workspace_size(4, 4, None, ctypes.byref(n)) == 0
+    small = n.value
+    assert lib.hotrg_workspace_size(4, 10, None, ctypes.byref(n)) == 0
+    big = n.value
+    # T and the squeeze scratch grow like Dcut^8: Dcut=10 needs several GB, Dcut=4 far less
+    assert big > 1e9 > small > 1e6
+    for bad in [(0, 4), (5, 4), (4, 1), (4, 17)]:
+        assert lib.hotrg_workspace_size(bad[0], bad[1], None, ctypes.byref(n)) == _lib.HOTRG_EINVAL
+    assert lib.hotrg_workspace_size(4, 4, None, None) == _lib.HOTRG_EINVAL
+    o = _lib.Opts()
+    lib.hotrg_opts_default(ctypes.byref(o))
+    o.batch = 0
+    assert lib.hotrg_workspace_size(4, 4, ctypes.byref(o), ctypes.byref(n)) == _lib.HOTRG_EINVAL
+    o.batch = 8
+    assert lib.hotrg_workspace_size(4, 4, ctypes.byref(o), ctypes.byref(n)) == 0
+    assert n.value > small  # tensors are per instance
+    o.batch = 1
+    o.precision = 7
+    assert lib.hotrg_workspace_size(4, 4, ctypes.byref(o), ctypes.byref(n)) == _lib.HOTRG_EINVAL
+
+
+def test_init_rejects_bad_arguments_before_touching_a_device(lib):
+    from paper_1906_06060_gb300 import _lib
+    o = _lib.Opts()
+    lib.hotrg_opts_default(ctypes.byref(o))
+    ctx = ctypes.c_void_p()
+    for d, beta, h, D in [(0, 0.1, 0, 4), (4, -0.1, 0, 4), (4, float("nan"), 0, 4), (4, 0.1, float("inf"), 4),
+                          (4, 0.1, 0, 1)]:
+        assert lib.hotrg_init(ctypes.byref(ctx), d, beta, h, D, ctypes.byref(o)) == _lib.HOTRG_EINVAL
+    assert lib.hotrg_init(ctypes.byref(ctx), 4, 0.1, 0.0, 4, None) == _lib.HOTRG_EINVAL
+
+
+def test_strerror_and_null_context(lib):
+    from paper_1906_06060_gb300 import _lib
+    for code in range(0, -9, -1):
+        assert lib.hotrg_strerror(code)
+    assert lib.hotrg_step(None, 0) == _lib.HOTRG_EINVAL
+    lib.hotrg_destroy(None)
+    assert lib.hotrg_gemm_scratch_bytes(0, 1, 1) == 0
+    assert lib.hotrg_gemm_scratch_bytes(128, 256, 64) > 2 * (128 + 256) * 64 * 2
+
+
+def test_product_path_fails_loudly_without_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("has a GPU")
+    from paper_1906_06060_gb300 import HOTRG
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        HOTRG(4, 0.1497, 0.0, 4)

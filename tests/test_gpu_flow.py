@@ -1,0 +1,263 @@
+"""Parity of the CUDA HOTRG flow (through the C ABI) against the FP64 CPU oracle.
+
+Element by element where the result is unique (a single step on generic random tensors: the
+isometries are fixed up to the sign convention both sides apply), and on gauge-invariant
+results (ln Z/N per step, ln c_n, Gram spectra) for the Ising flows. Expected values come from
+oracle/ directly or from tests/golden/*.json (written by tests/golden/make_golden.py).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import exact as E
+from oracle import hotrg_ref as R
+from tests.inputs import random_site_tensor
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+# FP64 path: agreement up to reassociation of sums (relative to the largest entry / value)
+TOL_FP64 = 1e-12
+# BF16X3 path: the squeeze products carry O(2^-16) relative error before FP32 accumulation
+TOL_MIXED_TENSOR = 2e-4
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name + ".json")) as fh:
+        return json.load(fh)
+
+
+def flow(d, beta, h, Dcut, **kw):
+    from paper_1906_06060_gb300 import HOTRG
+    return HOTRG(d, beta, h, Dcut, **kw)
+
+
+# ------------------------------------------------------------------------- initial tensor
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("beta,h", [(0.1497, 0.0), (0.44, 0.3), (1.0, -1e-6)])
+def test_initial_tensor_and_norm(d, beta, h):
+    with flow(d, beta, h, 4) as f:
+        T = f.get_tensor()
+        ref = R.initial_tensor(d, beta, h)
+        c0 = R.frobenius(ref)
+        np.testing.assert_allclose(T, ref / c0, rtol=0, atol=1e-15)
+        assert abs(f.ln_norms()[0] - math.log(c0)) < 1e-14
+        lnz, _ = f.free_energy()
+        assert abs(lnz[0] - (math.log(c0) + math.log(R.trace(ref / c0)))) < 1e-14
+
+
+# ------------------------------------------------------------------------- one step, element-wise
+STEP_CASES = [
+    (2, (3, 2), 1, 4), (2, (5, 4), 0, 6), (3, (2, 3, 2), 0, 3), (3, (3, 3, 2), 2, 5),
+    (4, (2, 2, 2, 2), 3, 4), (4, (2, 3, 2, 2), 1, 4), (4, (3, 2, 2, 3), 0, 9), (4, (3, 3, 3, 3), 2, 5),
+    (4, (4, 3, 2, 3), 3, 7),
+]
+
+
+def _eigvec_tolerance(info, Dcut):
+    """FP64 tolerance for entries of the coarse-grained tensor, relative to its largest entry.
+    Eigenvectors computed in FP64 carry an error ~ eps * lambda_1 / gap (first-order
+    perturbation theory), so the tolerance scales with the smallest gap among the kept
+    eigenvalues and at the cut."""
+    worst = 1.0
+    for iso in info.isometries.values():
+        lam = iso.eigenvalues
+        k = min(iso.chi + 1, lam.size)
+        gaps = -np.diff(lam[:k]) / lam[0]
+        if gaps.size:
+            worst = min(worst, float(gaps.min()))
+    return max(TOL_FP64, 2e-16 / max(worst, 1e-300))
+
+
+@pytest.mark.parametrize("d,dims,a,Dcut", STEP_CASES)
+def test_single_step_fp64_elementwise(d, dims, a, Dcut):
+    T = random_site_tensor(dims, seed=sum(dims) * 10 + a)
+    ref, info = R.coarse_grain(T, a, Dcut)
+    c = R.frobenius(ref)
+    with flow(d, 0.3, 0.0, Dcut) as f:
+        f.set_tensor(T)
+        f.step(a)
+        got = f.get_tensor()
+        assert got.shape == ref.shape
+        tol = _eigvec_tolerance(info, Dcut)
+        np.testing.assert_allclose(got, ref / c, rtol=0, atol=tol * np.abs(ref / c).max())
+        assert abs(f.ln_norms()[1] - math.log(c)) < 1e-12
+        for b, iso in info.isometries.items():
+            lam = f.spectra(1, b)
+            np.testing.assert_allclose(lam, iso.eigenvalues, rtol=0, atol=1e-12 * iso.eigenvalues[0])
+
+
+@pytest.mark.parametrize("d,dims,a,Dcut", [(4, (4, 4, 4, 4), 3, 8), (4, (4, 4, 4, 4), 0, 5),
+                                           (2, (16, 16), 1, 16), (3, (8, 8, 5), 2, 8), (4, (5, 4, 4, 4), 1, 6)])
+def test_single_step_bf16x3_elementwise(d, dims, a, Dcut):
+    """Tensor-core path (P >= 256, including P not a multiple of 64 and ragged tiles)."""
+    T = random_site_tensor(dims, seed=sum(dims) + a)
+    ref, _ = R.coarse_grain(T, a, Dcut)
+    ref /= R.frobenius(ref)
+    with flow(d, 0.3, 0.0, Dcut, precision="bf16x3", fp64_steps=0) as f:
+        f.set_tensor(T)
+        f.step(a)
+        got = f.get_tensor()
+        np.testing.assert_allclose(got, ref, rtol=0, atol=TOL_MIXED_TENSOR * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------------- exact pins through the GPU
+@pytest.mark.parametrize("beta,h", [(0.1497, 0.0), (0.3, 0.01)])
+def test_gpu_4d_lossless_steps_match_enumeration(beta, h):
+    with flow(4, beta, h, 16, max_steps=2) as f:
+        f.step()
+        lnz1 = f.free_energy()[0][0]
+        f.step()
+        lnz2 = f.free_energy()[0][0]
+    assert abs(2 * lnz1 - E.lnz_bruteforce(beta, h, (1, 1, 1, 2))) < 1e-12
+    assert abs(4 * lnz2 - E.lnz_bruteforce(beta, h, (1, 1, 2, 2))) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3", "bf16x6"])
+def test_gpu_2d_4x4_matches_enumeration(precision):
+    beta, h = 0.4407, 0.05
+    with flow(2, beta, h, 16, precision=precision, fp64_steps=0) as f:
+        for _ in range(4):
+            f.step()
+        lnz = f.free_energy()[0][0]
+    tol = {"fp64": 1e-12, "bf16x3": 1e-6, "bf16x6": 1e-9}[precision]
+    assert abs(16 * lnz - E.lnz_bruteforce(beta, h, (4, 4))) < tol * 16
+
+
+# ------------------------------------------------------------------------- Ising flows vs golden
+def _compare_flow(f, g, upto, tol_lnz, tol_spec, precision_note=""):
+    lnc = f.ln_norms()
+    assert abs(lnc[0] - g["ln_c0"]) < 1e-13
+    for st in g["steps"][:upto]:
+        n = st["step"]
+        assert abs(lnc[n] - st["ln_c"]) < tol_lnz * max(1.0, abs(st["ln_c"])), (n, precision_note)
+        for b, spec in st["spectra"].items():
+            lam = f.spectra(n, int(b))
+            lam = lam[: len(spec)] / lam[0]
+            keep = np.array(spec) > 1e-10
+            np.testing.assert_allclose(lam[keep], np.array(spec)[keep], rtol=tol_spec, atol=tol_spec * 1e-3)
+
+
+def test_fp64_flow_dcut5_16_steps_matches_oracle():
+    g = golden("flow_d4_b0.1497_h0_D5_n16")
+    with flow(4, 0.1497, 0.0, 5) as f:
+        for st in g["steps"]:
+            f.step()
+            lnz = f.free_energy()[0][0]
+            assert abs(lnz - st["lnz"]) < TOL_FP64 * abs(st["lnz"]), st["step"]
+            assert abs(f.observables()["x_indicator"] - st["x"]) < 1e-9
+        _compare_flow(f, g, 16, 1e-12, 1e-9)
+
+
+def test_fp64_flow_dcut4_until_cut_ambiguity():
+    """Dcut = 4 splits an exactly degenerate multiplet at step 3 (gap ~1e-16): the kept subspace
+    is not unique from there on, so only the steps before the split are compared."""
+    g = golden("flow_d4_b0.1497_h0_D4_n16")
+    upto = g["first_ambiguous_step"] - 1
+    assert upto == 2
+    with flow(4, 0.1497, 0.0, 4) as f:
+        for _ in range(16):
+            f.step()
+        _compare_flow(f, g, upto, 1e-12, 1e-9)
+        lnz = f.free_energy()[0][0]
+        # past the split both sides still land on a valid truncation of the same flow
+        assert abs(lnz - g["lnz_final"]) < 1e-3
+
+
+def test_fp64_flow_with_field():
+    g = golden("flow_d4_b0.1497_h1e-6_D4_n8")
+    with flow(4, 0.1497, 1e-6, 4) as f:
+        for _ in range(2):
+            f.step()
+        _compare_flow(f, g, 2, 1e-12, 1e-9)
+
+
+def test_fp64_2d_flow_40_steps_matches_oracle_and_onsager():
+    g = golden("flow_d2_b0.3_h0_D8_n40")
+    with flow(2, 0.3, 0.0, 8) as f:
+        for _ in range(40):
+            f.step()
+        lnz = f.free_energy()[0][0]
+        _compare_flow(f, g, 40, 1e-11, 1e-8)
+    assert abs(lnz - g["lnz_final"]) < 1e-12 * abs(lnz)
+    assert abs(lnz - E.lnz_onsager(0.3)) < 1e-6
+
+
+@pytest.mark.parametrize("precision,x6_steps,bound", [("bf16x6", 0, 2e-7), ("bf16x3", 8, 2e-7),
+                                                     ("bf16x3", 0, 3e-7)])
+def test_split_flow_dcut5_relative_free_energy(precision, x6_steps, bound):
+    """Split-precision paths: |delta f / f| against the FP64 oracle after every step.
+
+    The bound is set by the tensor cores' FP32 accumulation, which rounds toward zero: each
+    k-block's partial sum (restarted every 64 K, folded with round-to-nearest) keeps a bias
+    of about 2^-24 relative, which the flow turns into ~1e-7 in ln Z/N."""
+    g = golden("flow_d4_b0.1497_h0_D5_n16")
+    worst = 0.0
+    with flow(4, 0.1497, 0.0, 5, precision=precision, fp64_steps=2, x6_steps=x6_steps) as f:
+        for st in g["steps"]:
+            f.step()
+            lnz = f.free_energy()[0][0]
+            worst = max(worst, abs(lnz - st["lnz"]) / abs(st["lnz"]))
+    assert worst < bound, worst
+
+
+# ------------------------------------------------------------------------- batching, state, errors
+def test_batched_instances_match_separate_runs():
+    betas = [0.14, 0.1497, 0.16]
+    hs = [0.0, 1e-5, -1e-5]
+    with flow(4, betas, hs, 4) as fb:
+        for _ in range(6):
+            fb.step()
+        lnz_b = fb.free_energy()[0]
+    for i, (b, h) in enumerate(zip(betas, hs)):
+        with flow(4, b, h, 4) as f:
+            for _ in range(6):
+                f.step()
+            assert f.free_energy()[0][0] == lnz_b[i]  # same kernels, same order: bitwise
+
+
+def test_checkpoint_roundtrip_is_bitwise():
+    with flow(4, 0.1497, 0.0, 5) as f:
+        for _ in range(5):
+            f.step()
+        blob = f.state_save()
+        for _ in range(3):
+            f.step()
+        a = f.free_energy()[0][0]
+        f.state_load(blob)
+        assert f.observables()["steps"] == 5
+        for _ in range(3):
+            f.step()
+        b = f.free_energy()[0][0]
+    assert a == b
+
+
+def test_fp64_path_is_deterministic():
+    out = []
+    for _ in range(2):
+        with flow(4, 0.1497, 0.0, 5) as f:
+            for _ in range(6):
+                f.step()
+            out.append(f.get_tensor())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_error_codes():
+    from paper_1906_06060_gb300 import HotrgError
+    from paper_1906_06060_gb300 import _lib
+    with flow(4, 0.1497, 0.0, 4, max_steps=2) as f:
+        with pytest.raises(HotrgError) as e:
+            f.step(4)
+        assert e.value.code == _lib.HOTRG_EINVAL
+        f.step()
+        f.step()
+        with pytest.raises(HotrgError) as e:
+            f.step()
+        assert e.value.code == _lib.HOTRG_ESTATE
+        # the context stays usable after argument errors
+        assert f.observables()["steps"] == 2
+    with pytest.raises(HotrgError):
+        flow(4, -0.1, 0.0, 4)
