@@ -183,6 +183,24 @@ int hotrg_gemm_split(const float *A, long long lda, const float *Bt, long long l
                      long long ldc, long long M, long long N, long long K, int npass,
                      void *scratch, size_t scratch_bytes, void *stream);
 
+/* The same GEMM for callers that cannot allocate device memory (the paper has no counterpart:
+ * this is a service of the library). hotrg_gemm_split needs a scratch buffer from its caller;
+ * some callers have none to give, e.g. a process whose device memory is already reserved in
+ * full by another framework's pool, or a latency-critical loop that must not call cudaMalloc
+ * (it may synchronise the device). This variant allocates nothing: the bf16 planes and the
+ * status word live in a fixed device array inside the library (about 12 MiB, held on every GPU
+ * where this entry point is used until the process exits).
+ *   Limit: (M + N) * round_up(K, 64) <= HOTRG_GEMM_NOALLOC_MAX_ELEMS, else HOTRG_EINVAL.
+ *   Set-up: the first call on a device (made while it is current) looks up the array's device
+ *   address; make that first call before any stream capture.
+ *   Sharing: every call uses the same array. Calls whose GPU work overlaps (other streams or
+ *   host threads) race on it. The call synchronises `stream` and returns the GEMM's status
+ *   (0, HOTRG_ETIMEOUT if a pipeline wait gave up, HOTRG_EDEVICE). Other errors: EINVAL. */
+#define HOTRG_GEMM_NOALLOC_MAX_ELEMS 2097152LL
+int hotrg_gemm_split_noalloc(const float *A, long long lda, const float *Bt, long long ldb, float *C,
+                             long long ldc, long long M, long long N, long long K, int npass,
+                             void *stream);
+
 /* Status of the last hotrg_gemm_split call that used `scratch` (0 = ok, HOTRG_ETIMEOUT if a
  * pipeline wait of the GEMM kernel gave up). The word lives in the first bytes of scratch and
  * is cleared by each GEMM call. Synchronises `stream`. */

@@ -54,6 +54,8 @@ _SIGS = {
     "hotrg_gemm_split": (c_int, [c_void_p, c_longlong, c_void_p, c_longlong, c_void_p, c_longlong,
                                   c_longlong, c_longlong, c_longlong, c_int, c_void_p, c_size_t, c_void_p]),
     "hotrg_gemm_status": (c_int, [c_void_p, c_void_p]),
+    "hotrg_gemm_split_noalloc": (c_int, [c_void_p, c_longlong, c_void_p, c_longlong, c_void_p, c_longlong,
+                                         c_longlong, c_longlong, c_longlong, c_int, c_void_p]),
 }
 
 _lib = None
