@@ -8,6 +8,10 @@ the steady-state bond dimensions 10^4) run untimed, then K steady-state steps ar
 events on the library's stream. Metric: algorithmic TFLOP/s of the squeeze (2 prod(chi_b) P^3
 per step = 2 Dcut^15 at steady state; split-precision extra passes are not counted).
 
+Default precision schedule (the one whose free energy stays within 1e-7 of FP64): steps 1-3 in
+FP64, steps 4-12 in BF16X6, then BF16X3. With the default W = 12 the timed steps are BF16X3 steps
+of that schedule; with W = 3 they are BF16X6 steps.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|bf16x6|fp64]
     python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
 
@@ -37,11 +41,14 @@ PROFILE = os.path.join(ROOT, "profiles", "ncu_squeeze_gemm_dcut10_summary.md")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=12)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6", "fp64"])
-    ap.add_argument("--x6-steps", type=int, default=0)
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x4", "bf16x6", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--kblock", type=int, default=64)
+    ap.add_argument("--fold-group", type=int, default=0)
+    ap.add_argument("--x6-steps", type=int, default=12)
     ap.add_argument("--dcut", type=int, default=10)
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--h", type=float, default=0.0)
@@ -55,7 +62,9 @@ def workload_config(a):
     return {"workload": f"4D Ising HOTRG, beta={a.beta}, h={a.h}, Dcut={a.dcut}: steady-state "
                         f"coarse-graining steps (bond dims {a.dcut}^4) of the 40-step flow to 1024^4",
             "d": 4, "Dcut": a.dcut, "beta": a.beta, "h": a.h, "precision": a.precision,
-            "x6_steps": a.x6_steps,
+            "timed_steps": [a.warmup + 1, a.warmup + a.steps],
+            "fp64_steps": a.fp64_steps, "x6_steps": a.x6_steps, "kblock": a.kblock,
+            "fold_group": a.fold_group,
             "l2": "inputs larger than L2 (T 800 MB fp64, GEMM operands several GB per step)",
             "parallelism": "replicas" if a.gpus > 1 else "single GPU"}
 
@@ -199,7 +208,7 @@ def run_ours(a, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
-    kw = dict(precision=a.precision, fp64_steps=2, x6_steps=a.x6_steps, stream=stream)
+    kw = dict(precision=a.precision, fp64_steps=a.fp64_steps, x6_steps=a.x6_steps, kblock=a.kblock, fold_group=a.fold_group, stream=stream)
 
     def barrier():
         if dist:
@@ -274,7 +283,8 @@ def e2e(a):
     torch.cuda.synchronize()
     nsteps = a.warmup + a.steps
     t0 = time.perf_counter()
-    flow = HOTRG(4, a.beta, a.h, a.dcut, precision=a.precision, fp64_steps=2, x6_steps=a.x6_steps)
+    flow = HOTRG(4, a.beta, a.h, a.dcut, precision=a.precision, fp64_steps=a.fp64_steps, x6_steps=a.x6_steps,
+                 kblock=a.kblock, fold_group=a.fold_group)
     flops = 0.0
     dims = [2, 2, 2, 2]
     for n in range(nsteps):

@@ -53,15 +53,17 @@ typedef enum hotrg_precision {
                        (bf16 each); products hi*hi + hi*lo + lo*hi accumulate in FP32 (TMEM):
                        O(2^-16) relative error per product. Gram matrices, eigensolver, norms
                        and ln sums stay FP64; other intermediates are FP32. */
-  HOTRG_BF16X6 = 2  /* as BF16X3 with three planes x = hi + mid + lo and the six products
+  HOTRG_BF16X6 = 2, /* as BF16X3 with three planes x = hi + mid + lo and the six products
                        hh, hm, mh, hl, mm, lh: O(2^-24) per product, twice the tensor work */
+  HOTRG_BF16X4 = 3  /* two planes and all four products (adds lo*lo): no systematic
+                       truncation of the product, O(2^-17) unbiased per product */
 } hotrg_precision;
 
 typedef struct hotrg_opts {
   int precision;          /* hotrg_precision (default HOTRG_FP64) */
   int fp64_steps;         /* in BF16X3/X6 modes the first fp64_steps steps run in FP64 (default 2) */
-  int x6_steps;           /* in BF16X3 mode, steps fp64_steps+1 .. x6_steps use the 6-pass GEMM
-                             (the early steps weigh 2^-n in ln Z/N; default 0) */
+  int x6_steps;           /* in BF16X3/X4 modes, steps fp64_steps+1 .. x6_steps use the 6-pass
+                             GEMM (the early steps weigh 2^-n in ln Z/N; default 0) */
   int batch;              /* independent (beta, h) instances in the context (default 1) */
   const double *beta;     /* [batch] host array; NULL: all instances use the beta argument */
   const double *h;        /* [batch] host array; NULL: all instances use the h argument */
@@ -69,6 +71,12 @@ typedef struct hotrg_opts {
   void *workspace;        /* device pointer, >= hotrg_workspace_size() bytes, 256-B aligned */
   size_t workspace_bytes;
   int max_steps;          /* capacity of the per-step logs, 1..64 (default 64) */
+  int kblock;             /* split modes: K width of a pipeline stage, 32 or 64 (0 = 64) */
+  int fold_group;         /* split modes: stages per accumulator fold, 1 or 2 (0 = 1): the tensor
+                             cores' FP32 accumulator restarts every fold_group * kblock K */
+  int graphs;             /* 1: capture a steady-state step (bond dimensions unchanged) once per
+                             axis as a CUDA graph and replay it (default 1; off while timing and
+                             on the legacy default stream, which cannot be captured) */
   double wait_timeout_s;  /* bound on any device-side spin wait, seconds (default 4) */
 } hotrg_opts;
 
@@ -163,6 +171,21 @@ typedef struct hotrg_timing {
 int hotrg_timing_start(hotrg_ctx *c);
 int hotrg_timing_stop(hotrg_ctx *c, hotrg_timing *out);
 
+/* Autotuner of the squeeze GEMM's tile configuration: times the split-precision GEMM of the
+ * last step's shape (M = P, N = chi P, K = P, on the operands that step left in the workspace)
+ * for each candidate - k-block 64 or 32 (unless opts.kblock fixed it; 32 only for 6 passes), one
+ * or two k-blocks per accumulator fold at k-block 32, and tile-raster groups of 4, 8, 16 or 32
+ * M-tiles - keeps the fastest for the following steps and
+ * drops captured step graphs. Call it after a steady-state split-precision step. Synchronises.
+ * Errors: ESTATE (no split-precision step yet), EDEVICE. */
+typedef struct hotrg_tuning {
+  int kblock;
+  int group_m;
+  int fold_group;
+  double ms;  /* best GEMM time of the timed shape */
+} hotrg_tuning;
+int hotrg_autotune(hotrg_ctx *c, hotrg_tuning *out);
+
 /* Release the context's host object. The workspace is not touched. NULL is a no-op. */
 void hotrg_destroy(hotrg_ctx *c);
 
@@ -176,12 +199,17 @@ const char *hotrg_strerror(int code);
  * A (M x lda floats, row-major) and Bt (N x ldb floats, row-major) are device FP32 arrays that
  * are split into bf16 planes in `scratch` (device, >= hotrg_gemm_scratch_bytes(M,N,K) bytes,
  * 256-B aligned) before the tcgen05 GEMM; C is device FP32 with leading dimension ldc.
- * npass: 1 = hi*hi only, 3 = BF16X3 products, 6 = BF16X6 products. Enqueued on `stream`; not
- * synchronised. Errors: EINVAL (sizes, npass, alignment), EDEVICE. */
+ * npass: 1 = hi*hi only, 3 / 4 / 6 = BF16X3 / BF16X4 / BF16X6 products. kblock: 64 or 32, the K
+ * width of a pipeline stage (0 = 64; the 6-pass GEMM always uses 32). fold_group: stages whose
+ * products share one tensor-core accumulator before it is folded into FP32 registers with
+ * round-to-nearest adds (0 = 1; larger values are clamped to what the kernel variant's ring
+ * allows, at most 2).
+ * Enqueued on `stream`; not synchronised. Errors: EINVAL (sizes, npass, kblock, alignment),
+ * EDEVICE. */
 size_t hotrg_gemm_scratch_bytes(long long M, long long N, long long K);
 int hotrg_gemm_split(const float *A, long long lda, const float *Bt, long long ldb, float *C,
-                     long long ldc, long long M, long long N, long long K, int npass,
-                     void *scratch, size_t scratch_bytes, void *stream);
+                     long long ldc, long long M, long long N, long long K, int npass, int kblock,
+                     int fold_group, void *scratch, size_t scratch_bytes, void *stream);
 
 /* The same GEMM for callers that cannot allocate device memory (the paper has no counterpart:
  * this is a service of the library). hotrg_gemm_split needs a scratch buffer from its caller;

@@ -17,11 +17,11 @@ from ctypes import byref, c_double, c_int, c_size_t, c_void_p
 import numpy as np
 
 from . import _lib
-from ._lib import HOTRG_BF16X3, HOTRG_BF16X6, HOTRG_FP64, HotrgError, check
+from ._lib import HOTRG_BF16X3, HOTRG_BF16X4, HOTRG_BF16X6, HOTRG_FP64, HotrgError, check
 
 __all__ = ["HOTRG", "HotrgError", "gemm_split", "workspace_bytes", "PRECISIONS"]
 
-PRECISIONS = {"fp64": HOTRG_FP64, "bf16x3": HOTRG_BF16X3, "bf16x6": HOTRG_BF16X6}
+PRECISIONS = {"fp64": HOTRG_FP64, "bf16x3": HOTRG_BF16X3, "bf16x4": HOTRG_BF16X4, "bf16x6": HOTRG_BF16X6}
 
 
 def _torch():
@@ -31,7 +31,8 @@ def _torch():
     return torch
 
 
-def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0):
+def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0, kblock=0,
+          graphs=True, fold_group=0):
     lib = _lib.load()
     o = _lib.Opts()
     lib.hotrg_opts_default(byref(o))
@@ -39,6 +40,9 @@ def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=
     o.batch = int(batch)
     o.fp64_steps = int(fp64_steps)
     o.x6_steps = int(x6_steps)
+    o.kblock = int(kblock)
+    o.graphs = 1 if graphs else 0
+    o.fold_group = int(fold_group)
     o.max_steps = int(max_steps)
     o.wait_timeout_s = float(wait_timeout_s)
     return o
@@ -56,12 +60,13 @@ class HOTRG:
     """One HOTRG flow context (or a batch of independent (beta, h) instances).
 
     beta, h: scalars, or sequences of equal length `batch` for a temperature/field scan.
-    precision: "fp64", "bf16x3" or "bf16x6" (tensor-core squeeze with split operands);
+    precision: "fp64", "bf16x3", "bf16x4" or "bf16x6" (tensor-core squeeze with split operands);
     fp64_steps / x6_steps: precision schedule of the split modes (see include/hotrg.h).
     """
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
-                 max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0):
+                 max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0,
+                 kblock: int = 0, graphs: bool = True, fold_group: int = 0):
         torch = _torch()
         lib = _lib.load()
         betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))
@@ -76,7 +81,7 @@ class HOTRG:
         self.d, self.Dcut, self.batch, self.precision = d, Dcut, batch, precision
         self.beta = betas
         self.h = hs
-        o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps)
+        o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps, kblock, graphs, fold_group)
         n = c_size_t(0)
         check(lib.hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -151,6 +156,13 @@ class HOTRG:
     def state_load(self, blob: bytes) -> None:
         check(_lib.load().hotrg_state_load(self._ctx, blob, len(blob)), "hotrg_state_load")
 
+    def autotune(self) -> dict:
+        """Pick the squeeze GEMM's k-block and tile raster for the current step shape (call after
+        a steady-state split-precision step)."""
+        t = _lib.Tuning()
+        check(_lib.load().hotrg_autotune(self._ctx, byref(t)), "hotrg_autotune")
+        return {"kblock": t.kblock, "group_m": t.group_m, "fold_group": t.fold_group, "ms": t.ms}
+
     def timing_start(self) -> None:
         check(_lib.load().hotrg_timing_start(self._ctx), "hotrg_timing_start")
 
@@ -178,9 +190,9 @@ class HOTRG:
             pass
 
 
-def gemm_split(A, Bt, npass: int = 3, C=None, stream=None):
+def gemm_split(A, Bt, npass: int = 3, C=None, stream=None, kblock: int = 0, fold_group: int = 0):
     """C = A @ Bt^T through the tcgen05 kernel (A: M x K, Bt: N x K, float32 CUDA tensors);
-    npass 1 / 3 / 6 selects hi*hi, BF16X3 or BF16X6 products."""
+    npass 1 / 3 / 4 / 6 selects hi*hi, BF16X3, BF16X4 or BF16X6 products."""
     torch = _torch()
     lib = _lib.load()
     assert A.dtype == torch.float32 and Bt.dtype == torch.float32 and A.is_cuda and Bt.is_cuda
@@ -192,7 +204,7 @@ def gemm_split(A, Bt, npass: int = 3, C=None, stream=None):
     nbytes = lib.hotrg_gemm_scratch_bytes(M, N, K)
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=A.device)
     check(lib.hotrg_gemm_split(c_void_p(A.data_ptr()), A.stride(0), c_void_p(Bt.data_ptr()), Bt.stride(0),
-                                c_void_p(C.data_ptr()), C.stride(0), M, N, K, npass,
+                                c_void_p(C.data_ptr()), C.stride(0), M, N, K, npass, kblock, fold_group,
                                 c_void_p(scratch.data_ptr()), nbytes, c_void_p(stream.cuda_stream)),
           "hotrg_gemm_split")
     check(lib.hotrg_gemm_status(c_void_p(scratch.data_ptr()), c_void_p(stream.cuda_stream)), "gemm status")

@@ -10,14 +10,14 @@ LIB_PATH = os.path.join(HERE, "libhotrg.so")
 
 HOTRG_OK, HOTRG_EINVAL, HOTRG_ENOMEM, HOTRG_ENUMERIC = 0, -1, -2, -3
 HOTRG_ENOCONV, HOTRG_ETIMEOUT, HOTRG_EDEVICE, HOTRG_ESTATE, HOTRG_ENOTSUP = -4, -5, -6, -7, -8
-HOTRG_FP64, HOTRG_BF16X3, HOTRG_BF16X6 = 0, 1, 2
+HOTRG_FP64, HOTRG_BF16X3, HOTRG_BF16X6, HOTRG_BF16X4 = 0, 1, 2, 3
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("fp64_steps", c_int), ("x6_steps", c_int), ("batch", c_int),
                 ("beta", POINTER(c_double)), ("h", POINTER(c_double)), ("stream", c_void_p),
                 ("workspace", c_void_p), ("workspace_bytes", c_size_t), ("max_steps", c_int),
-                ("wait_timeout_s", c_double)]
+                ("kblock", c_int), ("fold_group", c_int), ("graphs", c_int), ("wait_timeout_s", c_double)]
 
 
 class Obs(ctypes.Structure):
@@ -30,6 +30,10 @@ class Timing(ctypes.Structure):
                 ("ms_gemm", c_double), ("ms_epilogue", c_double), ("ms_norm", c_double),
                 ("steps", c_longlong), ("gemm_launches", c_longlong), ("kernel_launches", c_longlong),
                 ("gemm_flops", c_double), ("gemm_tensor_flops", c_double), ("step_flops", c_double)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("kblock", c_int), ("group_m", c_int), ("fold_group", c_int), ("ms", c_double)]
 
 
 _SIGS = {
@@ -46,13 +50,15 @@ _SIGS = {
     "hotrg_state_size": (c_int, [c_void_p, POINTER(c_size_t)]),
     "hotrg_state_save": (c_int, [c_void_p, c_void_p, c_size_t]),
     "hotrg_state_load": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "hotrg_autotune": (c_int, [c_void_p, POINTER(Tuning)]),
     "hotrg_timing_start": (c_int, [c_void_p]),
     "hotrg_timing_stop": (c_int, [c_void_p, POINTER(Timing)]),
     "hotrg_destroy": (None, [c_void_p]),
     "hotrg_strerror": (c_char_p, [c_int]),
     "hotrg_gemm_scratch_bytes": (c_size_t, [c_longlong, c_longlong, c_longlong]),
     "hotrg_gemm_split": (c_int, [c_void_p, c_longlong, c_void_p, c_longlong, c_void_p, c_longlong,
-                                  c_longlong, c_longlong, c_longlong, c_int, c_void_p, c_size_t, c_void_p]),
+                                 c_longlong, c_longlong, c_longlong, c_int, c_int, c_int, c_void_p, c_size_t,
+                                 c_void_p]),
     "hotrg_gemm_status": (c_int, [c_void_p, c_void_p]),
     "hotrg_gemm_split_noalloc": (c_int, [c_void_p, c_longlong, c_void_p, c_longlong, c_void_p, c_longlong,
                                          c_longlong, c_longlong, c_longlong, c_int, c_void_p]),

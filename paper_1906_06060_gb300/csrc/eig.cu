@@ -28,11 +28,19 @@ __device__ void sm_red_sum(double* sred, double v, int tid) {
   }
 }
 
-__global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict__ G, int n, int chi,
-                                                        double* __restrict__ evals,
-                                                        double* __restrict__ Uout,
-                                                        double* __restrict__ work, int* status) {
+__global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict__ G, long long g_stride, int n,
+                                                        int chi, EigOut o, double* __restrict__ Uout,
+                                                        long long u_stride, double* __restrict__ work,
+                                                        int* status) {
   extern __shared__ double sm[];
+  G += (long long)blockIdx.x * g_stride;
+  Uout += (long long)blockIdx.x * u_stride;
+  work += (long long)blockIdx.x * 2 * n * n;
+  // eigenvalue log slot of this instance for the current step (device step counter, 1-based)
+  const int step = o.step ? *o.step : 1;
+  double* evals = (step >= 1 && step <= o.max_steps)
+                      ? o.base + (long long)blockIdx.x * o.inst_stride + (long long)(step - 1) * o.step_stride
+                      : nullptr;
   const int tid = threadIdx.x;
   const int np = n + (n & 1);          // padded to even (index n is a dummy)
   const int npairs = np / 2;
@@ -136,7 +144,8 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict
     perm[rank] = i;
   }
   __syncthreads();
-  for (int k = tid; k < n; k += kEigThreads) evals[k] = lam[perm[k]];
+  if (evals)
+    for (int k = tid; k < n; k += kEigThreads) evals[k] = lam[perm[k]];
   // sign-fixed eigenvectors: one warp per kept vector
   const int warp = tid / 32, lane = tid % 32;
   for (int k = warp; k < chi; k += kEigThreads / 32) {
@@ -159,10 +168,10 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict
 
 }  // namespace
 
-void launch_eig(const double* G, int n, int chi, double* evals, double* U, double* work, int* status,
-                cudaStream_t s) {
+void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o, double* U,
+                long long u_stride, double* work, int* status, cudaStream_t s) {
   const size_t smem = sizeof(double) * (128 + 128 + 128 + 128 + kEigThreads);
-  k_jacobi<<<1, kEigThreads, smem, s>>>(G, n, chi, evals, U, work, status);
+  k_jacobi<<<batch, kEigThreads, smem, s>>>(G, g_stride, n, chi, o, U, u_stride, work, status);
   count_launches(1);
 }
 

@@ -3,10 +3,11 @@
 //
 // Precision: each FP32 operand is split into bf16 planes, x = hi + lo (2 planes) or
 // x = hi + mid + lo (3 planes), each plane the bf16 rounding of what the previous ones left.
-// The GEMM sums the plane products ("passes") whose combined order is at most 2^-16: with two
-// planes hi*hi + hi*lo + lo*hi (3 passes), with three planes hh, hm, mh, hl, mm, lh (6 passes),
-// accumulating in FP32 in tensor memory. Dropped terms and split residuals are O(2^-16)
-// relative per product for 3 passes and O(2^-24) for 6 passes.
+// The GEMM sums plane products ("passes"): with two planes hi*hi + hi*lo + lo*hi (3 passes) or
+// all four products (4 passes, adds lo*lo), with three planes hh, hm, mh, hl, mm, lh (6
+// passes), accumulating in FP32 in tensor memory. Per product the dropped terms and split
+// residuals are O(2^-16) relative for 3 passes, O(2^-17) unbiased for 4 and O(2^-24) for 6. The
+// dropped lo*lo of 3 passes is systematic when A and B are built from the same tensor.
 //
 // Accumulation: the tensor core's FP32 accumulate rounds toward zero, so a long chain of MMAs
 // into one TMEM accumulator drifts systematically towards zero by about (chain length) x 2^-25
@@ -16,11 +17,12 @@
 // k-block's partial sum is folded into an FP32 register accumulator with round-to-nearest adds.
 //
 // Kernel structure (one CTA per SM, persistent over output tiles, 320 threads):
-//   warp 0      TMA producer: per (k-block, pass) loads a 128x64 A tile and a 256x64 B tile
-//               (bf16, 128-byte swizzle) into a 4-stage shared-memory ring.
+//   warp 0      TMA producer: per k-block loads every bf16 plane of the 128 x BK A tile and
+//               of the 256 x BK B tile (BK*2-byte swizzle) into one stage of a shared-memory
+//               ring, so the passes of a k-block reuse the same stage (BK = 64 or 32).
 //   warp 1      MMA issuer: one thread issues tcgen05.mma.cta_group::1.kind::f16 (M=128,
-//               N=256, K=16) for one k-block into one of two TMEM buffers (2 x 256 FP32
-//               columns), releases ring stages and hands the buffer over with tcgen05.commit.
+//               N=256, K=16) for all passes of one k-block into one of two TMEM buffers (2 x 256
+//               FP32 columns), releases the stage and hands the buffer over with tcgen05.commit.
 //   warps 2-9   fold/epilogue: warp w reads TMEM lanes 32*(w%4).. (its hardware quadrant),
 //               columns 128*((w-2)/4).. of the buffer, adds them into 128 FP32 registers per
 //               thread and frees the buffer; after the last k-block it stores its 128 columns.
@@ -28,6 +30,7 @@
 // the copies and MMAs it issued (again with a bound), frees TMEM and returns.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "kernels.h"
@@ -36,16 +39,21 @@ namespace hotrg {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64;
-constexpr int TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BN = 256;
 constexpr int TC_THREADS = 320;
 constexpr int TC_FOLD_THREADS = 256;  // warps 2-9
-constexpr uint32_t A_TILE = TC_BM * TC_BK * 2;  // 16 KB
-constexpr uint32_t B_TILE = TC_BN * TC_BK * 2;  // 32 KB
-constexpr uint32_t STAGE_BYTES = A_TILE + B_TILE;
 constexpr uint32_t TMEM_COLS = 2 * TC_BN;
-constexpr int GROUP_M = 16;
-constexpr size_t TC_SMEM = 1024 + TC_STAGES * STAGE_BYTES + 256;
+
+// k-block width BK (bf16 elements per tile row): 64 -> 128-byte swizzle, 4 stages;
+// 32 -> 64-byte swizzle, 8 stages. The accumulator is folded once per k-block.
+template <int BK, int NPL>
+struct Cfg {
+  static constexpr uint32_t A_TILE = TC_BM * BK * 2;
+  static constexpr uint32_t B_TILE = TC_BN * BK * 2;
+  static constexpr uint32_t STAGE_BYTES = NPL * (A_TILE + B_TILE);
+  static constexpr int STAGES = (int)((216u * 1024u) / STAGE_BYTES) > 4 ? 4 : (int)((216u * 1024u) / STAGE_BYTES);
+  static constexpr size_t SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+};
 
 // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
 // both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -58,17 +66,29 @@ struct TmapSet {
 };
 
 // plane index of A and B for each pass, smallest products first, hi*hi last
-//   npass 1: hh      npass 3: hl, lh, hh      npass 6: lh, mm, hl, mh, hm, hh  (h=0, m=1, l=2)
-__constant__ int8_t kPassA1[1] = {0};
-__constant__ int8_t kPassB1[1] = {0};
-__constant__ int8_t kPassA3[3] = {0, 1, 0};
-__constant__ int8_t kPassB3[3] = {1, 0, 0};
-__constant__ int8_t kPassA6[6] = {2, 1, 0, 1, 0, 0};
-__constant__ int8_t kPassB6[6] = {0, 1, 2, 0, 1, 0};
+//   npass 1: hh    npass 3: hl, lh, hh    npass 4: ll, hl, lh, hh (two planes, all products)
+//   npass 6: lh, mm, hl, mh, hm, hh (three planes h=0, m=1, l=2)
+__host__ __device__ constexpr int pass_plane_a(int npass, int ps) {
+  return npass == 1 ? 0
+       : npass == 3 ? (ps == 1 ? 1 : 0)
+       : npass == 4 ? ((ps == 0 || ps == 2) ? 1 : 0)
+       : (ps == 0 ? 2 : (ps == 1 || ps == 3) ? 1 : 0);
+}
+__host__ __device__ constexpr int pass_plane_b(int npass, int ps) {
+  return npass == 1 ? 0
+       : npass == 3 ? (ps == 0 ? 1 : 0)
+       : npass == 4 ? ((ps == 0 || ps == 1) ? 1 : 0)
+       : (ps == 2 ? 2 : (ps == 1 || ps == 4) ? 1 : 0);
+}
+static_assert(pass_plane_a(6, 0) == 2 && pass_plane_b(6, 0) == 0, "lh first");
+static_assert(pass_plane_a(6, 5) == 0 && pass_plane_b(6, 5) == 0, "hh last");
+static_assert(pass_plane_a(3, 2) == 0 && pass_plane_b(3, 2) == 0, "hh last");
+static_assert(pass_plane_a(4, 0) == 1 && pass_plane_b(4, 0) == 1, "ll first");
 
 struct TcParams {
-  long long M, N;
+  long long M, N, K;
   int num_m, num_n, num_kb, npass;
+  int group_m;     // output tiles are rastered in groups of group_m M-tiles (L2 reuse of A and B)
   float* C;
   long long ldc;
   int* status;
@@ -128,28 +148,32 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// No "memory" clobber: the MMA reads shared memory the async proxy filled and writes TMEM; its
+// order against the mbarrier waits and tcgen05.commit around it is kept because all of these are
+// volatile asm statements, which the compiler does not reorder among themselves.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
 }
-// Shared-memory matrix descriptor, K-major operand staged by TMA with 128-byte swizzle:
-// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this layout, bits 16-29),
-// stride byte offset 1024 B between 8-row groups (bits 32-45), version 1 (bits 46-47),
-// base offset 0 (tiles are 1024-B aligned), layout SWIZZLE_128B = 2 (bits 61-63).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor, K-major operand staged by TMA with a BK*2-byte swizzle:
+// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for these layouts, bits
+// 16-29), stride byte offset = 8 rows x BK*2 bytes between 8-row groups (bits 32-45), version 1
+// (bits 46-47), base offset 0 (tiles are 1024-B aligned), layout SWIZZLE_128B = 2 or
+// SWIZZLE_64B = 4 (bits 61-63). Consecutive K=16 slices are 32 bytes apart inside a row.
+template <int BK>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= ((uint64_t)(BK == 64 ? 1024 : 512) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(BK == 64 ? 2 : 4) << 61;
   return d;
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -167,24 +191,32 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void raster(int tile, int num_m, int num_n, int& mt, int& nt) {
-  const int per_group = GROUP_M * num_n;
+__device__ __forceinline__ void raster(int tile, int num_m, int num_n, int group_m, int& mt, int& nt) {
+  const int per_group = group_m * num_n;
   const int g = tile / per_group;
-  const int first_m = g * GROUP_M;
-  const int gsz = min(num_m - first_m, GROUP_M);
+  const int first_m = g * group_m;
+  const int gsz = min(num_m - first_m, group_m);
   const int local = tile - g * per_group;
   mt = first_m + local % gsz;
   nt = local / gsz;
 }
 
+template <int BK, int NPL, int NPASS, int FG>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_split(const __grid_constant__ TmapSet maps, TcParams p) {
+  using C = Cfg<BK, NPL>;
+  static_assert(FG == 1 || FG <= C::STAGES - 1, "a fold group leaves one stage to the producer");
+  constexpr int TC_STAGES = C::STAGES;
+  constexpr uint32_t A_TILE = C::A_TILE, B_TILE = C::B_TILE, STAGE_BYTES = C::STAGE_BYTES;
+  constexpr int TC_BK = BK;
+  static_assert(TC_STAGES >= 2, "ring needs two stages");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + TC_STAGES * A_TILE;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TC_STAGES * B_TILE);
+  // stage s: A planes 0..NPL-1 then B planes 0..NPL-1
+  auto a_tile = [&](int stage, int pl) { return smem + stage * STAGE_BYTES + pl * A_TILE; };
+  auto b_tile = [&](int stage, int pl) { return smem + stage * STAGE_BYTES + NPL * A_TILE + pl * B_TILE; };
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -202,15 +234,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, TC_FOLD_THREADS);
+      mbar_init(tempty0 + 8 * b, TC_FOLD_THREADS / 32);
     }
     mbar_init(final_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const int nplanes = p.npass == 1 ? 1 : (p.npass == 3 ? 2 : 3);
-  if (warp == 0 && lane < 2 * nplanes) {
-    const CUtensorMap* m = lane < nplanes ? &maps.a[lane] : &maps.b[lane - nplanes];
+  if (warp == 0 && lane < 2 * NPL) {
+    const CUtensorMap* m = lane < NPL ? &maps.a[lane] : &maps.b[lane - NPL];
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
   }
   if (warp == 1) {
@@ -225,7 +256,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
 
   const int total = p.num_m * p.num_n;
-  const int kiters = p.num_kb * p.npass;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -235,18 +265,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
         int mt, nt;
-        raster(tile, p.num_m, p.num_n, mt, nt);
-        for (int it = 0; it < kiters; ++it) {
-          const int kb = it / p.npass, ps = it % p.npass;
+        raster(tile, p.num_m, p.num_n, p.group_m, mt, nt);
+        for (int kb = 0; kb < p.num_kb; ++kb) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.timeout_ns)) { ok = false; break; }
           const uint32_t fb = full0 + 8 * stage;
           mbar_expect_tx(fb, STAGE_BYTES);
-          const int pa = p.npass == 6 ? kPassA6[ps] : (p.npass == 3 ? kPassA3[ps] : kPassA1[ps]);
-          const int pb = p.npass == 6 ? kPassB6[ps] : (p.npass == 3 ? kPassB3[ps] : kPassB1[ps]);
-          const CUtensorMap* ma = &maps.a[pa];
-          const CUtensorMap* mb = &maps.b[pb];
-          tma_load_2d(smem_u32(sA + stage * A_TILE), ma, fb, kb * TC_BK, mt * TC_BM);
-          tma_load_2d(smem_u32(sB + stage * B_TILE), mb, fb, kb * TC_BK, nt * TC_BN);
+#pragma unroll
+          for (int pl = 0; pl < NPL; ++pl) {
+            tma_load_2d(smem_u32(a_tile(stage, pl)), &maps.a[pl], fb, kb * TC_BK, mt * TC_BM);
+            tma_load_2d(smem_u32(b_tile(stage, pl)), &maps.b[pl], fb, kb * TC_BK, nt * TC_BN);
+          }
           ++issued;
           if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
         }
@@ -266,22 +294,48 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t bphase = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-        for (int kb = 0; kb < p.num_kb && ok; ++kb) {
+        // Descriptors differ only in their start-address field (bits 0-13, address >> 4), so each
+        // one is a base descriptor plus the tile's byte offset >> 4 (all offsets are multiples of
+        // 16 bytes and the shared window is < 256 KB, so the field never carries over). Passes,
+        // planes and the fold group are compile-time: a group's MMAs unroll into straight-line
+        // issue code with constant offsets.
+        const uint64_t desc_base = smem_desc<BK>(smem_u32(smem));
+        constexpr uint32_t B_OFF = NPL * A_TILE;
+        for (int kb0 = 0; kb0 < p.num_kb && ok; kb0 += FG) {
+          const int g = min(FG, p.num_kb - kb0);  // k-blocks in this fold group
           if (!mbar_wait(tempty0 + 8 * buf, bphase ^ 1, abort_flag, p.timeout_ns)) { ok = false; break; }
+          uint32_t so[FG];  // byte offsets of the group's stages
+          {
+            int st = stage;
+            uint32_t ph = phase;
+#pragma unroll
+            for (int i = 0; i < FG; ++i) {
+              so[i] = (uint32_t)st * STAGE_BYTES;
+              if (i < g && ok && !mbar_wait(full0 + 8 * st, ph, abort_flag, p.timeout_ns)) ok = false;
+              if (++st == TC_STAGES) { st = 0; ph ^= 1; }
+            }
+          }
+          if (!ok) break;
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(buf * TC_BN);
-          for (int ps = 0; ps < p.npass; ++ps) {
-            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.timeout_ns)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + stage * A_TILE);
-            const uint32_t b0 = smem_u32(sB + stage * B_TILE);
 #pragma unroll
-            for (int k = 0; k < TC_BK / 16; ++k)
-              mma_bf16(d_tmem, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), IDESC, (ps | k) != 0);
+          for (int ps = 0; ps < NPASS; ++ps) {
+#pragma unroll
+            for (int i = 0; i < FG; ++i) {
+              if (i < g) {
+                const uint64_t da = desc_base + ((so[i] + (uint32_t)pass_plane_a(NPASS, ps) * A_TILE) >> 4);
+                const uint64_t db = desc_base + ((so[i] + B_OFF + (uint32_t)pass_plane_b(NPASS, ps) * B_TILE) >> 4);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k)
+                  mma_bf16(d_tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC,
+                           (ps == 0 && i == 0 && k == 0) ? 0u : 1u);
+              }
+            }
+          }
+          for (int i = 0; i < g; ++i) {
             mma_commit(empty0 + 8 * stage);
             if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
           }
-          if (!ok) break;
           mma_commit(tfull0 + 8 * buf);
           if (++buf == 2) { buf = 0; bphase ^= 1; }
         }
@@ -298,25 +352,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = true;
     for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
       int mt, nt;
-      raster(tile, p.num_m, p.num_n, mt, nt);
+      raster(tile, p.num_m, p.num_n, p.group_m, mt, nt);
       float acc[128];
 #pragma unroll
       for (int j = 0; j < 128; ++j) acc[j] = 0.f;
-      for (int kb = 0; kb < p.num_kb; ++kb) {
-        const bool w = mbar_wait(tfull0 + 8 * buf, bphase, abort_flag, p.timeout_ns);
-        if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+      for (int kb = 0; kb < p.num_kb; kb += FG) {
+        // one lane waits for the fold group's MMAs, the warp follows it
+        int w = 1;
+        if (lane == 0) w = mbar_wait(tfull0 + 8 * buf, bphase, abort_flag, p.timeout_ns) ? 1 : 0;
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (!w) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN + half * 128);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint32_t r[32];
-          tmem_ld32(taddr + c * 32, r);
+        for (int c = 0; c < 4; c += 2) {
+          uint32_t r0[32], r1[32];
+          tmem_ld32(taddr + c * 32, r0);
+          tmem_ld32(taddr + (c + 1) * 32, r1);
           tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[c * 32 + j] += __uint_as_float(r[j]);
+          for (int j = 0; j < 32; ++j) {
+            acc[c * 32 + j] += __uint_as_float(r0[j]);
+            acc[(c + 1) * 32 + j] += __uint_as_float(r1[j]);
+          }
         }
         tc_fence_before();
-        mbar_arrive(tempty0 + 8 * buf);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * buf);  // one arrive per warp
         if (++buf == 2) { buf = 0; bphase ^= 1; }
       }
       if (!ok) break;
@@ -375,16 +437,41 @@ EncodeTiledFn encode_fn() {
 }
 
 bool make_map(CUtensorMap* m, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld,
-              int box_rows) {
+              int box_rows, int bk) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Encodes the tensor maps and launches one kernel variant. The maps' box width, the stage slot
+// sizes and the expected transaction bytes all derive from the same compile-time BK and NPL,
+// so a TMA copy can never be larger than the stage slot it lands in.
+template <int BK, int NPL, int NPASS, int FG>
+int launch_variant(int grid, const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
+                   long long ldb, const TcParams& p, cudaStream_t s) {
+  static_assert(Cfg<BK, NPL>::STAGE_BYTES == NPL * (TC_BM + TC_BN) * BK * 2, "stage holds exactly the boxes");
+  TmapSet maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int i = 0; i < NPL; ++i)
+    if (!make_map(&maps.a[i], A.p[i], p.M, p.K, lda, TC_BM, BK) ||
+        !make_map(&maps.b[i], B.p[i], p.N, p.K, ldb, TC_BN, BK))
+      return HOTRG_EDEVICE;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_gemm_split<BK, NPL, NPASS, FG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<BK, NPL>::SMEM) != cudaSuccess)
+      return HOTRG_EDEVICE;
+    attr = true;
+  }
+  k_gemm_split<BK, NPL, NPASS, FG><<<grid, TC_THREADS, Cfg<BK, NPL>::SMEM, s>>>(maps, p);
+  return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
 }
 
 int num_sms() {
@@ -402,34 +489,30 @@ int num_sms() {
 
 int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
-                      int npass, int* status, double timeout_s, cudaStream_t s) {
-  if (M < TC_BM || N < TC_BN || K < TC_BK || (npass != 1 && npass != 3 && npass != 6)) return HOTRG_EINVAL;
-  const int nplanes = npass == 1 ? 1 : (npass == 3 ? 2 : 3);
+                      int npass, int* status, double timeout_s, cudaStream_t s, int bk, int group_m,
+                      int fold_group) {
+  if (bk != 32 && bk != 64) return HOTRG_EINVAL;
+  if (group_m < 1 || group_m > 64 || fold_group < 1) return HOTRG_EINVAL;
+  if (M < TC_BM || N < TC_BN || K < 64 || (npass != 1 && npass != 3 && npass != 4 && npass != 6))
+    return HOTRG_EINVAL;
+  const int nplanes = npass == 1 ? 1 : (npass == 6 ? 3 : 2);
+  if (nplanes == 3) bk = 32;  // three 64-wide planes do not fit two ring stages: resolved first
+  if (nplanes == 1) bk = 64;  // single-plane GEMMs use 64-wide stages
   if (A.nparts < nplanes || B.nparts < nplanes) return HOTRG_EINVAL;
   if ((lda % 8) || (ldb % 8) || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
   if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return HOTRG_EINVAL;
   auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-  TmapSet maps;
-  std::memset(&maps, 0, sizeof(maps));
-  for (int i = 0; i < nplanes; ++i) {
+  for (int i = 0; i < nplanes; ++i)
     if (!al16(A.p[i]) || !al16(B.p[i])) return HOTRG_EINVAL;
-    if (!make_map(&maps.a[i], A.p[i], M, K, lda, TC_BM) || !make_map(&maps.b[i], B.p[i], N, K, ldb, TC_BN))
-      return HOTRG_EDEVICE;
-  }
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) !=
-        cudaSuccess)
-      return HOTRG_EDEVICE;
-    attr_set = true;
-  }
   TcParams p;
   p.M = M;
   p.N = N;
+  p.K = K;
   p.num_m = (int)((M + TC_BM - 1) / TC_BM);
   p.num_n = (int)((N + TC_BN - 1) / TC_BN);
-  p.num_kb = (int)((K + TC_BK - 1) / TC_BK);
+  p.num_kb = (int)((K + bk - 1) / bk);
   p.npass = npass;
+  p.group_m = group_m;
   p.C = C;
   p.ldc = ldc;
   p.status = status;
@@ -438,9 +521,32 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
   const long long tiles = (long long)p.num_m * p.num_n;
   if (tiles > 0x7fffffffLL) return HOTRG_EINVAL;
   const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
-  k_gemm_split<<<grid, TC_THREADS, TC_SMEM, s>>>(maps, p);
+  // supported variants (fold groups beyond a variant's maximum are clamped to it)
+  const int fg = std::max(1, std::min(fold_group, max_fold_group(npass, bk)));
+  int rc = HOTRG_EINVAL;
+#define HOTRG_GEMM_VARIANT(BK_, NPL_, NP_, FG_)                                          \
+  if (bk == BK_ && nplanes == NPL_ && npass == NP_ && fg == FG_)                        \
+    rc = launch_variant<BK_, NPL_, NP_, FG_>(grid, A, lda, B, ldb, p, s);
+  HOTRG_GEMM_VARIANT(64, 1, 1, 1)
+  HOTRG_GEMM_VARIANT(64, 1, 1, 2)
+  HOTRG_GEMM_VARIANT(64, 2, 3, 1)
+  HOTRG_GEMM_VARIANT(64, 2, 4, 1)
+  HOTRG_GEMM_VARIANT(32, 2, 3, 1)
+  HOTRG_GEMM_VARIANT(32, 2, 3, 2)
+  HOTRG_GEMM_VARIANT(32, 2, 4, 1)
+  HOTRG_GEMM_VARIANT(32, 2, 4, 2)
+  HOTRG_GEMM_VARIANT(32, 3, 6, 1)
+  HOTRG_GEMM_VARIANT(32, 3, 6, 2)
+#undef HOTRG_GEMM_VARIANT
+  if (rc) return rc;
   count_launches(1);
-  return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
+  return HOTRG_OK;
+}
+
+int max_fold_group(int npass, int bk) {
+  if (npass == 6) return 2;        // 32-wide stages, three planes, 3-stage ring
+  if (npass == 1) return 2;        // 64-wide stages, one plane, 4-stage ring
+  return bk == 64 ? 1 : 2;         // two planes: 2-stage ring at 64, 4-stage ring at 32
 }
 
 void launch_split_rows(const float* X, long long ldx, long long rows, long long cols,

@@ -22,10 +22,12 @@ struct LegInfo {
   long long stride[kMaxLegs];
 };
 
-__global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ T, LegInfo li,
+__global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ T, long long t_stride, LegInfo li,
                                                    long long S1, long long S2, int Da, int nr,
                                                    long long K, int ntile, int nsplit,
                                                    double* __restrict__ partial) {
+  T += (long long)blockIdx.z * t_stride;
+  partial += (long long)blockIdx.z * nsplit * nr * nr;
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   __shared__ long long coloff[GK];
@@ -101,19 +103,24 @@ __global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ T,
 }
 
 __global__ void k_reduce_splits(const double* __restrict__ partial, int nsplit, int nn,
-                                double* __restrict__ Q) {
+                                double* __restrict__ Q, long long q_stride) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nn) return;
+  partial += (long long)blockIdx.y * nsplit * nn;
+  Q += (long long)blockIdx.y * q_stride;
   double s = 0.0;
   for (int k = 0; k < nsplit; ++k) s += partial[(long long)k * nn + e];
   Q[e] = s;
 }
 
-__global__ void k_gram_combine(const double* __restrict__ Q1, const double* __restrict__ Q2, int Db,
-                               int Da, double* __restrict__ G) {
+__global__ void k_gram_combine(const double* __restrict__ Q1, const double* __restrict__ Q2, long long q_stride,
+                               int Db, int Da, double* __restrict__ G, long long g_stride) {
   const int n = Db * Db, nr = Db * Da;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
+  Q1 += (long long)blockIdx.y * q_stride;
+  Q2 += (long long)blockIdx.y * q_stride;
+  G += (long long)blockIdx.y * g_stride;
   const int row = e / n, col = e % n;
   const int b1 = row / Db, b2 = row % Db, c1 = col / Db, c2 = col % Db;
   double s = 0.0;
@@ -129,8 +136,26 @@ __global__ void k_gram_combine(const double* __restrict__ Q1, const double* __re
 
 int gram_nsplit() { return kGramCTAs; }
 
-void launch_half_gram(const double* T, Geom g, int l1, int l2, double* partial, double* Q,
-                      cudaStream_t s) {
+// split-K factor for nr x nr outputs over `batch` instances (about two waves of CTAs in total)
+static int nsplit_for(int nr, long long K, int batch) {
+  const int ntile = (nr + GT - 1) / GT;
+  int nsplit = kGramCTAs / (ntile * ntile * batch);
+  if (nsplit < 1) nsplit = 1;
+  if (nsplit > K) nsplit = (int)K;
+  return nsplit;
+}
+
+size_t gram_partial_doubles(int nr_max, int batch) {
+  size_t best = 0;
+  for (int nr = 1; nr <= nr_max; ++nr) {
+    const size_t v = (size_t)batch * nsplit_for(nr, 1LL << 40, batch) * nr * nr;
+    if (v > best) best = v;
+  }
+  return best;
+}
+
+void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, int l1, int l2, double* partial,
+                      double* Q, long long q_stride, cudaStream_t s) {
   const int d = g.d;
   auto leg_dim = [&](int l) { return g.D[l % d]; };
   auto leg_stride = [&](int l) { return l < d ? g.Sn[l] * g.P : g.Sn[l - d]; };
@@ -147,22 +172,20 @@ void launch_half_gram(const double* T, Geom g, int l1, int l2, double* partial, 
   const long long K = g.P * g.P / nr;
   const int ntile = (nr + GT - 1) / GT;
   const int tiles = ntile * ntile;
-  int nsplit = kGramCTAs / tiles;
-  if (nsplit < 1) nsplit = 1;
-  if (nsplit > K) nsplit = (int)K;
-  dim3 grid(tiles, nsplit);
-  k_half_gram<<<grid, 256, 0, s>>>(T, li, leg_stride(l1), leg_stride(l2), Da, nr, K, ntile, nsplit,
+  const int nsplit = nsplit_for(nr, K, batch);
+  dim3 grid(tiles, nsplit, batch);
+  k_half_gram<<<grid, 256, 0, s>>>(T, t_stride, li, leg_stride(l1), leg_stride(l2), Da, nr, K, ntile, nsplit,
                                     partial);
   count_launches(1);
   const int nn = nr * nr;
-  k_reduce_splits<<<(nn + 255) / 256, 256, 0, s>>>(partial, nsplit, nn, Q);
+  k_reduce_splits<<<dim3((nn + 255) / 256, batch), 256, 0, s>>>(partial, nsplit, nn, Q, q_stride);
   count_launches(1);
 }
 
-void launch_gram_combine(const double* Q1, const double* Q2, int Db, int Da, double* G,
-                         cudaStream_t s) {
+void launch_gram_combine(const double* Q1, const double* Q2, long long q_stride, int batch, int Db, int Da,
+                         double* G, long long g_stride, cudaStream_t s) {
   const int n = Db * Db;
-  k_gram_combine<<<(n * n + 255) / 256, 256, 0, s>>>(Q1, Q2, Db, Da, G);
+  k_gram_combine<<<dim3((n * n + 255) / 256, batch), 256, 0, s>>>(Q1, Q2, q_stride, Db, Da, G, g_stride);
   count_launches(1);
 }
 

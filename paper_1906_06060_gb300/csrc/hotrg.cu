@@ -26,6 +26,15 @@ using namespace hotrg;
 
 struct hotrg_ctx {
   int d = 0, Dcut = 0, batch = 1, precision = HOTRG_FP64, fp64_steps = 2, x6_steps = 0, max_steps = 64;
+  int kblock = 64;
+  bool kblock_fixed = false;  // the caller fixed the k-block (else the autotuner may change it)
+  int group_m = 16;
+  int fold_group = 0;  // k-blocks per accumulator fold (0: one)
+  // shape of the last split-precision GEMM launched (what the autotuner times)
+  struct LastGemm {
+    long long M = 0, N = 0, K = 0, ldk = 0;
+    int npass = 0, nparts = 0;
+  } last_gemm;
   double timeout_s = 4.0;
   cudaStream_t stream = nullptr;
   int dims[kMaxD] = {1, 1, 1, 1};
@@ -40,6 +49,8 @@ struct hotrg_ctx {
   double *norm_partial = nullptr, *gpartial = nullptr, *Q1 = nullptr, *Q2 = nullptr;
   double *G = nullptr, *U = nullptr, *ework = nullptr;
   int* status = nullptr;
+  int* dstep = nullptr;       // device-side step counter (steps done)
+  long long q_stride = 0, g_stride = 0, u_stride = 0;  // per-instance strides (doubles)
   void *Tt = nullptr, *Bt = nullptr, *X1 = nullptr, *X2 = nullptr, *Y = nullptr, *O = nullptr;
   void *R1 = nullptr, *R2 = nullptr;
   size_t sz_Tt = 0, sz_Bt = 0, sz_X = 0, sz_Y = 0, sz_O = 0, sz_R1 = 0, sz_R2 = 0;
@@ -51,6 +62,11 @@ struct hotrg_ctx {
   };
   bool timing = false;
   std::vector<Ev> evs;
+  // captured steady-state steps, one per axis (replayed while the bond dimensions do not change)
+  bool graphs = true;
+  cudaGraphExec_t graph_exec[kMaxD] = {nullptr, nullptr, nullptr, nullptr};
+  int graph_dims[kMaxD][kMaxD] = {};
+  int graph_planes[kMaxD] = {-1, -1, -1, -1};
   long long launch0 = 0, t_gemm_launches = 0, t_steps = 0;
   double t_gemm_flops = 0, t_gemm_tflops = 0, t_step_flops = 0;
 };
@@ -147,6 +163,22 @@ int planes_for_step(int precision, int step, int fp64_steps, int x6_steps, long 
   return 2;
 }
 
+// k-blocks per accumulator fold: one unless the caller chose otherwise, within what the kernel
+// variant's ring allows
+int fold_group_for(const hotrg_ctx* c, int npass) {
+  const int bk = npass == 6 ? 32 : c->kblock;
+  const int g = c->fold_group > 0 ? c->fold_group : 1;
+  return std::max(1, std::min(g, max_fold_group(npass, bk)));
+}
+
+// passes of the split GEMM for a step (0 = FP64 path)
+int passes_for_step(int precision, int step, int fp64_steps, int x6_steps, long long P) {
+  const int pl = planes_for_step(precision, step, fp64_steps, x6_steps, P);
+  if (pl == 0) return 0;
+  if (pl == 3) return 6;
+  return precision == HOTRG_BF16X4 ? 4 : 3;
+}
+
 StepNeeds plan(int d, int Dcut, int precision, int fp64_steps, int x6_steps, int max_steps,
                long long* Pmax_out) {
   // breadth-first: minimal number of steps after which each bond-dimension state is reached
@@ -211,14 +243,22 @@ size_t carve(hotrg_ctx* c, char* base) {
   c->spec_log = k.take<double>(sizeof(double) * c->batch * c->spec_stride);
   c->out3 = k.take<double>(sizeof(double) * 3 * c->batch);
   c->cval = k.take<double>(sizeof(double) * c->batch);
-  c->status = k.take<int>(sizeof(int) * 64);
+  c->status = k.take<int>(sizeof(int) * 32);
+  c->dstep = k.take<int>(sizeof(int) * 32);
   c->norm_partial = k.take<double>(sizeof(double) * 1024);
-  c->gpartial = k.take<double>(sizeof(double) * gram_nsplit() * 4096);
-  c->Q1 = k.take<double>(sizeof(double) * nr_max * nr_max);
-  c->Q2 = k.take<double>(sizeof(double) * nr_max * nr_max);
-  c->G = k.take<double>(sizeof(double) * kMaxD * kMaxGram * kMaxGram);
-  c->U = k.take<double>(sizeof(double) * kMaxD * kMaxBond * kMaxGram);
-  c->ework = k.take<double>(sizeof(double) * (2 * kMaxGram * kMaxGram + 4 * kMaxGram));
+  // Gram matrices and isometries: sized for the largest Gram this Dcut produces (n <= Dcut^2... 256)
+  const int nmax = std::min(kMaxGram, std::max(16, c->Dcut * c->Dcut));
+  const int nrm = std::min(kMaxGram, std::max(16, c->Dcut * c->Dcut));
+  c->q_stride = (long long)nrm * nrm;
+  c->g_stride = (long long)kMaxD * nmax * nmax;
+  c->u_stride = (long long)kMaxD * kMaxBond * kMaxGram;
+  c->gpartial = k.take<double>(sizeof(double) * gram_partial_doubles(nrm, c->batch));
+  c->Q1 = k.take<double>(sizeof(double) * c->q_stride * c->batch);
+  c->Q2 = k.take<double>(sizeof(double) * c->q_stride * c->batch);
+  c->G = k.take<double>(sizeof(double) * c->g_stride * c->batch);
+  c->U = k.take<double>(sizeof(double) * c->u_stride * c->batch);
+  c->ework = k.take<double>(sizeof(double) * 2 * nmax * nmax * c->batch);
+  (void)nr_max;
   c->sz_Tt = n.Tt; c->Tt = k.take<char>(n.Tt);
   c->sz_Bt = n.Bt; c->Bt = k.take<char>(n.Bt);
   c->sz_X = n.X;   c->X1 = k.take<char>(n.X); c->X2 = k.take<char>(n.X);
@@ -301,8 +341,18 @@ void contract_axes(std::vector<Ax>& axes, const Tin* in, Tout* out, int b, int c
     v.out_stride[i] = final_out_stride ? final_out_stride[i] : st;
     st *= v.shape[i];
   }
-  launch_pair_contract<Tin, Tout>(in, out, v, kaxis, axes[im].dim, axes[in_].dim, axes[im].stride,
-                                  axes[in_].stride, Ub, chi_b, 0, out_base, s);
+  // rest view: the output axes without k'
+  View rest;
+  rest.ndim = 0;
+  for (int i = 0; i < v.ndim; ++i) {
+    if (i == kaxis) continue;
+    rest.shape[rest.ndim] = v.shape[i];
+    rest.in_stride[rest.ndim] = v.in_stride[i];
+    rest.out_stride[rest.ndim] = v.out_stride[i];
+    ++rest.ndim;
+  }
+  launch_pair_contract_all<Tin, Tout>(in, out, rest, axes[im].dim, axes[in_].dim, axes[im].stride,
+                                      axes[in_].stride, v.out_stride[kaxis], Ub, chi_b, 0, out_base, s);
   // new axes describe the dense output (only meaningful when not final)
   st = 1;
   for (int i = v.ndim - 1; i >= 0; --i) {
@@ -341,8 +391,8 @@ struct Ops<float> {
 
 // planes: 0 = FP64 path (TC = double), 2 / 3 = tensor-core path (TC = float) with 3 / 6 passes.
 template <class TC>
-int squeeze(hotrg_ctx* c, const double* Tin, const Geom& g, const Geom& gn, int a, const int* chi,
-            const int* trans, int nt, int planes) {
+int squeeze(hotrg_ctx* c, const double* Tin, const double* U, const Geom& g, const Geom& gn, int a,
+            const int* chi, const int* trans, int nt, int planes, int npass) {
   using Op = typename Ops<TC>::Op;
   constexpr bool mixed = std::is_same<TC, float>::value;
   cudaStream_t s = c->stream;
@@ -350,7 +400,6 @@ int squeeze(hotrg_ctx* c, const double* Tin, const Geom& g, const Geom& gn, int 
   const long long ldk = mixed ? round_up(P, 64) : P;
   const int c3 = nt ? trans[nt - 1] : -1;
   const int chi3 = c3 >= 0 ? chi[c3] : 1;
-  const double* U = c->U;
   auto Ub = [&](int b) { return U + (long long)b * kMaxBond * kMaxGram; };
   // bounds of this step's buffers against the plan
   StepNeeds need = needs_for(c->d, g.D, a, c->Dcut, planes);
@@ -407,9 +456,15 @@ int squeeze(hotrg_ctx* c, const double* Tin, const Geom& g, const Geom& gn, int 
     {
       PhaseScope gemm_scope(c, PH_GEMM);
       if constexpr (mixed) {
-        const int npass = planes == 3 ? 6 : 3;
         const int rc = launch_gemm_split(Y, ldk, Bt, ldk, reinterpret_cast<float*>(O), ldO, P, ldO, P,
-                                         npass, c->status, c->timeout_s, s);
+                                         npass, c->status, c->timeout_s, s, c->kblock, c->group_m,
+                                         fold_group_for(c, npass));
+        c->last_gemm.M = P;
+        c->last_gemm.N = ldO;
+        c->last_gemm.K = P;
+        c->last_gemm.ldk = ldk;
+        c->last_gemm.npass = npass;
+        c->last_gemm.nparts = planes;
         if (rc) return rc;
         if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * P * npass;
       } else {
@@ -469,6 +524,8 @@ void hotrg_opts_default(hotrg_opts* o) {
   o->x6_steps = 0;
   o->batch = 1;
   o->max_steps = 64;
+  o->kblock = 64;
+  o->graphs = 1;
   o->wait_timeout_s = 4.0;
 }
 
@@ -478,7 +535,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   hotrg_opts_default(&def);
   if (!opt) opt = &def;
   if (opt->batch < 1 || opt->max_steps < 1 || opt->max_steps > 64) return HOTRG_EINVAL;
-  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X6) return HOTRG_EINVAL;
+  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X4) return HOTRG_EINVAL;
   hotrg_ctx c;
   c.d = d;
   c.Dcut = Dcut;
@@ -496,7 +553,9 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   *out = nullptr;
   if (d < 1 || d > kMaxD || Dcut < 2 || Dcut > kMaxBond || opt->batch < 1) return HOTRG_EINVAL;
   if (opt->max_steps < 1 || opt->max_steps > 64 || opt->fp64_steps < 0) return HOTRG_EINVAL;
-  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X6) return HOTRG_EINVAL;
+  if (opt->kblock != 0 && opt->kblock != 32 && opt->kblock != 64) return HOTRG_EINVAL;
+  if (opt->fold_group < 0) return HOTRG_EINVAL;
+  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X4) return HOTRG_EINVAL;
   std::vector<double> vb(opt->batch), vh(opt->batch);
   for (int i = 0; i < opt->batch; ++i) {
     vb[i] = opt->beta ? opt->beta[i] : beta;
@@ -518,6 +577,10 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->fp64_steps = opt->fp64_steps;
   c->x6_steps = opt->x6_steps;
   c->max_steps = opt->max_steps;
+  c->kblock = opt->kblock ? opt->kblock : 64;
+  c->kblock_fixed = opt->kblock != 0;
+  c->fold_group = opt->fold_group;
+  c->graphs = opt->graphs != 0;
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
@@ -531,7 +594,8 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   carve(c, static_cast<char*>(opt->workspace));
   for (int b = 0; b < d; ++b) c->dims[b] = 2;
   cudaStream_t s = c->stream;
-  cudaMemsetAsync(c->status, 0, sizeof(int) * 64, s);
+  cudaMemsetAsync(c->status, 0, sizeof(int) * 32, s);
+  cudaMemsetAsync(c->dstep, 0, sizeof(int) * 32, s);
   cudaMemsetAsync(c->L, 0, sizeof(double) * c->batch, s);
   cudaMemsetAsync(c->lnc_log, 0, sizeof(double) * c->batch * (c->max_steps + 1), s);
   cudaMemsetAsync(c->spec_log, 0, sizeof(double) * c->batch * c->spec_stride, s);
@@ -544,10 +608,10 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   for (int i = 0; i < c->batch; ++i) {
     double* Ti = c->T + i * P2;
     launch_norm_log(Ti, n0, c->norm_partial, c->cval + i, c->lnc_log + (long long)i * (c->max_steps + 1),
-                    c->L + i, 0, c->status, s);
+                    c->L + i, c->dstep, c->status, s);
     launch_scale(Ti, Ti, n0, c->cval + i, s);
-    launch_trace_x(Ti, g, d - 1, c->L + i, 0, c->out3 + 3 * i, c->status, s);
   }
+  launch_trace_x(c->T, P2, c->batch, g, d - 1, c->L, c->dstep, c->out3, s);
   if (cuda_err(c)) {
     delete c;
     return HOTRG_EDEVICE;
@@ -556,13 +620,8 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   return HOTRG_OK;
 }
 
-int hotrg_step(hotrg_ctx* c, int axis) {
-  if (!c) return HOTRG_EINVAL;
-  if (c->sticky) return c->sticky;
-  if (axis < -1 || axis >= c->d) return HOTRG_EINVAL;
-  if (c->steps >= c->max_steps) return HOTRG_ESTATE;
-  const int a = axis >= 0 ? axis : c->d - 1 - (c->steps % c->d);
-  const int step = c->steps + 1;
+// Enqueue one step along axis a on the context's stream (all instances).
+static int enqueue_step(hotrg_ctx* c, int a, int step) {
   Geom g = make_geom(c->d, c->dims);
   int chi[kMaxD], trans[kMaxD], nt = 0, nd[kMaxD];
   for (int b = 0; b < c->d; ++b) {
@@ -577,36 +636,110 @@ int hotrg_step(hotrg_ctx* c, int axis) {
   }
   Geom gn = make_geom(c->d, nd);
   const int planes = planes_for_step(c->precision, step, c->fp64_steps, c->x6_steps, g.P);
+  const int npass = passes_for_step(c->precision, step, c->fp64_steps, c->x6_steps, g.P);
   cudaStream_t s = c->stream;
   const long long P2max = c->Pmax * c->Pmax;
   PhaseScope step_scope(c, PH_STEP);
-  for (int i = 0; i < c->batch; ++i) {
-    const double* Ti = c->T + i * P2max;
-    // 1. isometries
-    PhaseScope* iso_scope = new PhaseScope(c, PH_ISO);
+  launch_step_advance(c->dstep, s);
+  // 1. isometries of every instance (batched launches: one CTA group per instance)
+  {
+    PhaseScope iso_scope(c, PH_ISO);
     for (int t = 0; t < nt; ++t) {
       const int b = trans[t];
       const int n = g.D[b] * g.D[b];
-      double* Gb = c->G + (long long)b * kMaxGram * kMaxGram;
+      double* Gb = c->G + (long long)b * (c->g_stride / kMaxD);
       double* Ub = c->U + (long long)b * kMaxBond * kMaxGram;
-      launch_half_gram(Ti, g, b, c->d + a, c->gpartial, c->Q1, s);
-      launch_half_gram(Ti, g, b, a, c->gpartial, c->Q2, s);
-      launch_gram_combine(c->Q1, c->Q2, g.D[b], g.D[a], Gb, s);
-      double* ev = c->spec_log + i * c->spec_stride + ((long long)(step - 1) * c->d + b) * kSpecCap;
-      launch_eig(Gb, n, chi[b], ev, Ub, c->ework, c->status, s);
+      launch_half_gram(c->T, P2max, c->batch, g, b, c->d + a, c->gpartial, c->Q1, c->q_stride, s);
+      launch_half_gram(c->T, P2max, c->batch, g, b, a, c->gpartial, c->Q2, c->q_stride, s);
+      launch_gram_combine(c->Q1, c->Q2, c->q_stride, c->batch, g.D[b], g.D[a], Gb, c->g_stride, s);
+      EigOut eo{c->spec_log + (long long)b * kSpecCap, c->spec_stride, (long long)c->d * kSpecCap, c->dstep,
+                c->max_steps};
+      launch_eig(Gb, c->g_stride, c->batch, n, chi[b], eo, Ub, c->u_stride, c->ework, c->status, s);
     }
-    delete iso_scope;
-    // 2-3. squeeze into Tnext
-    const int rc = planes ? squeeze<float>(c, Ti, g, gn, a, chi, trans, nt, planes)
-                          : squeeze<double>(c, Ti, g, gn, a, chi, trans, nt, 0);
-    if (rc) return c->sticky = rc;
-    // 4. normalise, accumulate, measure
+  }
+  // 2-4. squeeze, normalise and accumulate, instance by instance (each fills the GPU)
+  for (int i = 0; i < c->batch; ++i) {
+    const double* Ti = c->T + i * P2max;
+    const double* Ui = c->U + i * c->u_stride;
+    const int rc = planes ? squeeze<float>(c, Ti, Ui, g, gn, a, chi, trans, nt, planes, npass)
+                          : squeeze<double>(c, Ti, Ui, g, gn, a, chi, trans, nt, 0, 0);
+    if (rc) return rc;
     PhaseScope norm_scope(c, PH_NORM);
     double* Tw = c->T + i * P2max;
     launch_norm_log(c->Tnext, gn.P * gn.P, c->norm_partial, c->cval + i,
-                    c->lnc_log + (long long)i * (c->max_steps + 1), c->L + i, step, c->status, s);
+                    c->lnc_log + (long long)i * (c->max_steps + 1), c->L + i, c->dstep, c->status, s);
     launch_scale(c->Tnext, Tw, gn.P * gn.P, c->cval + i, s);
-    launch_trace_x(Tw, gn, a, c->L + i, step, c->out3 + 3 * i, c->status, s);
+  }
+  launch_trace_x(c->T, P2max, c->batch, gn, a, c->L, c->dstep, c->out3, s);
+  if (c->timing) {
+    double f = 2.0 * (double)g.P * (double)g.P * (double)g.P * c->batch;
+    for (int t = 0; t < nt; ++t) f *= chi[trans[t]];
+    c->t_step_flops += f;
+    ++c->t_steps;
+  }
+  return HOTRG_OK;
+}
+
+int hotrg_step(hotrg_ctx* c, int axis) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (axis < -1 || axis >= c->d) return HOTRG_EINVAL;
+  if (c->steps >= c->max_steps) return HOTRG_ESTATE;
+  const int a = axis >= 0 ? axis : c->d - 1 - (c->steps % c->d);
+  const int step = c->steps + 1;
+  int nd[kMaxD];
+  bool steady = true;
+  long long P = 1;
+  for (int b = 0; b < c->d; ++b) {
+    nd[b] = c->dims[b];
+    P *= c->dims[b];
+    if (b != a) {
+      const long long sq = (long long)c->dims[b] * c->dims[b];
+      nd[b] = (int)(sq < c->Dcut ? sq : c->Dcut);
+      if (nd[b] != c->dims[b]) steady = false;
+    }
+  }
+  const int pl = passes_for_step(c->precision, step, c->fp64_steps, c->x6_steps, P);
+  int rc = HOTRG_OK;
+  // graphs need a capturable stream: not the legacy default stream
+  if (c->graphs && steady && !c->timing && c->stream != nullptr) {
+    // a steady-state step is the same launch sequence every time: capture it once per axis
+    bool hit = c->graph_exec[a] && c->graph_planes[a] == pl;
+    for (int b = 0; hit && b < c->d; ++b) hit = c->graph_dims[a][b] == c->dims[b];
+    if (!hit) {
+      if (c->graph_exec[a]) cudaGraphExecDestroy(c->graph_exec[a]);
+      c->graph_exec[a] = nullptr;
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return c->sticky = HOTRG_EDEVICE;
+      }
+      rc = enqueue_step(c, a, step);
+      const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return c->sticky = rc;
+      }
+      if (e != cudaSuccess || cudaGraphInstantiate(&c->graph_exec[a], graph, 0) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return c->sticky = HOTRG_EDEVICE;
+      }
+      cudaGraphDestroy(graph);
+      c->graph_planes[a] = pl;
+      for (int b = 0; b < c->d; ++b) c->graph_dims[a][b] = c->dims[b];
+    }
+    if (cudaGraphLaunch(c->graph_exec[a], c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return c->sticky = HOTRG_EDEVICE;
+    }
+  } else {
+    rc = enqueue_step(c, a, step);
+    if (rc) {
+      cudaGetLastError();
+      return c->sticky = rc;
+    }
   }
   if (cuda_err(c)) return HOTRG_EDEVICE;
   for (int b = 0; b < c->d; ++b) c->hist_dims[step - 1][b] = c->dims[b];
@@ -614,12 +747,6 @@ int hotrg_step(hotrg_ctx* c, int axis) {
   for (int b = 0; b < c->d; ++b) c->dims[b] = nd[b];
   c->steps = step;
   c->last_axis = a;
-  if (c->timing) {
-    double f = 2.0 * (double)g.P * (double)g.P * (double)g.P * c->batch;
-    for (int t = 0; t < nt; ++t) f *= chi[trans[t]];
-    c->t_step_flops += f;
-    ++c->t_steps;
-  }
   return HOTRG_OK;
 }
 
@@ -802,6 +929,8 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
     p += sizeof(double) * 3;
     if (!ok) return c->sticky = HOTRG_EDEVICE;
   }
+  if (cudaMemcpy(c->dstep, &h.steps, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
   for (int b = 0; b < kMaxD; ++b) c->dims[b] = h.dims[b];
   std::memcpy(c->hist_dims, h.hist_dims, sizeof(h.hist_dims));
   std::memcpy(c->hist_axis, h.hist_axis, sizeof(h.hist_axis));
@@ -855,8 +984,85 @@ int hotrg_timing_stop(hotrg_ctx* c, hotrg_timing* out) {
   return HOTRG_OK;
 }
 
+int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
+  if (!c) return HOTRG_EINVAL;
+  const int rc = sync_check(c);
+  if (rc) return rc;
+  const auto& lg = c->last_gemm;
+  if (lg.npass == 0) return HOTRG_ESTATE;  // no split-precision step has run yet
+  Planes<__nv_bfloat16> Y, Bt;
+  Y.nparts = Bt.nparts = lg.nparts;
+  for (int k = 0; k < 3; ++k) {
+    const int kk = k < lg.nparts ? k : 0;
+    Y.p[k] = static_cast<__nv_bfloat16*>(c->Y) + (size_t)kk * lg.M * lg.ldk;
+    Bt.p[k] = static_cast<__nv_bfloat16*>(c->Bt) + (size_t)kk * lg.N * lg.ldk;
+  }
+  // candidates keep the hi*hi chain between folds at most 64 K: (k-block 64, 1 per fold),
+  // (32, 1) or (32, 2)
+  std::vector<int> kbs;
+  if (lg.npass == 6) kbs = {32};
+  else if (c->kblock_fixed) kbs = {c->kblock};
+  else kbs = {64, 32};
+  const int groups[4] = {4, 8, 16, 32};
+  struct Cand {
+    int kb, fg, gm;
+  };
+  std::vector<Cand> cands;
+  for (int kb : kbs)
+    for (int fg = 1; fg <= (kb == 32 ? 2 : 1); ++fg)
+      for (int gm : groups) cands.push_back({kb, fg, gm});
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HOTRG_EDEVICE;
+  double best = 1e300;
+  int best_kb = c->kblock, best_g = c->group_m, best_fg = std::max(1, c->fold_group);
+  for (const Cand& cd : cands) {
+    double t_min = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, c->stream);
+      const int r = launch_gemm_split(Y, lg.ldk, Bt, lg.ldk, static_cast<float*>(c->O), lg.N, lg.M, lg.N, lg.K,
+                                      lg.npass, c->status, c->timeout_s, c->stream, cd.kb, cd.gm, cd.fg);
+      cudaEventRecord(e1, c->stream);
+      float ms = 0.f;
+      if (r || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaGetLastError();
+        return r ? r : (c->sticky = HOTRG_EDEVICE);
+      }
+      t_min = std::min(t_min, (double)ms);
+    }
+    if (t_min < best) {
+      best = t_min;
+      best_kb = cd.kb;
+      best_g = cd.gm;
+      best_fg = cd.fg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int rc2 = sync_check(c);
+  if (rc2) return rc2;
+  c->kblock = best_kb;
+  c->group_m = best_g;
+  c->fold_group = best_fg;
+  for (int a = 0; a < kMaxD; ++a)
+    if (c->graph_exec[a]) {
+      cudaGraphExecDestroy(c->graph_exec[a]);  // captured with the previous choice
+      c->graph_exec[a] = nullptr;
+    }
+  if (out) {
+    out->kblock = best_kb;
+    out->group_m = best_g;
+    out->fold_group = best_fg;
+    out->ms = best;
+  }
+  return HOTRG_OK;
+}
+
 void hotrg_destroy(hotrg_ctx* c) {
   if (!c) return;
+  for (int a = 0; a < kMaxD; ++a)
+    if (c->graph_exec[a]) cudaGraphExecDestroy(c->graph_exec[a]);
   for (auto& e : c->evs) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -887,10 +1093,13 @@ size_t hotrg_gemm_scratch_bytes(long long M, long long N, long long K) {
 }
 
 int hotrg_gemm_split(const float* A, long long lda, const float* Bt, long long ldb, float* C, long long ldc,
-                     long long M, long long N, long long K, int npass, void* scratch, size_t scratch_bytes,
-                     void* stream) {
+                     long long M, long long N, long long K, int npass, int kblock, int fold_group, void* scratch,
+                     size_t scratch_bytes, void* stream) {
+  if (fold_group < 0) return HOTRG_EINVAL;
   if (!A || !Bt || !C || !scratch || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
-  if (npass != 1 && npass != 3 && npass != 6) return HOTRG_EINVAL;
+  if (kblock == 0) kblock = 64;
+  if (kblock != 32 && kblock != 64) return HOTRG_EINVAL;
+  if (npass != 1 && npass != 3 && npass != 4 && npass != 6) return HOTRG_EINVAL;
   if (scratch_bytes < hotrg_gemm_scratch_bytes(M, N, K) || (reinterpret_cast<uintptr_t>(scratch) % kAlign))
     return HOTRG_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -898,7 +1107,7 @@ int hotrg_gemm_split(const float* A, long long lda, const float* Bt, long long l
   char* p = static_cast<char*>(scratch);
   int* status = reinterpret_cast<int*>(p);
   p += kAlign;
-  const int nparts = npass == 1 ? 1 : (npass == 3 ? 2 : 3);
+  const int nparts = npass == 1 ? 1 : (npass == 6 ? 3 : 2);
   Planes<__nv_bfloat16> Ap, Bp;
   Ap.nparts = Bp.nparts = nparts;
   for (int k = 0; k < 3; ++k) {
@@ -912,7 +1121,8 @@ int hotrg_gemm_split(const float* A, long long lda, const float* Bt, long long l
   cudaMemsetAsync(status, 0, sizeof(int), s);
   launch_split_rows(A, lda, M, K, Ap, ld, s);
   launch_split_rows(Bt, ldb, N, K, Bp, ld, s);
-  const int rc = launch_gemm_split(Ap, ld, Bp, ld, C, ldc, M, N, K, npass, status, 4.0, s);
+  const int fg = fold_group > 0 ? fold_group : 1;
+  const int rc = launch_gemm_split(Ap, ld, Bp, ld, C, ldc, M, N, K, npass, status, 4.0, s, kblock, 16, fg);
   if (rc) return rc;
   return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
 }

@@ -14,14 +14,19 @@ long long launches_total();
 // T^(0) (Sec. 2) for `batch` instances: T + i*stride gets beta[i], h[i] (device arrays).
 void launch_init_tensor(double* T, long long inst_stride, int batch, int d, const double* beta,
                         const double* h, cudaStream_t s);
-// c = ||x||_F (deterministic), lnc_log[step] = ln c, L += 2^-step ln c, status on bad norm.
+// *dstep += 1 (device-side step counter read by the kernels below, so that a captured step
+// can be replayed for any step number).
+void launch_step_advance(int* dstep, cudaStream_t s);
+// c = ||x||_F (deterministic), lnc_log[n] = ln c, L += 2^-n ln c with n = *dstep; status on a bad
+// norm.
 void launch_norm_log(const double* x, long long n, double* partial, double* c_out,
-                     double* lnc_log, double* L, int step, int* status, cudaStream_t s);
+                     double* lnc_log, double* L, const int* dstep, int* status, cudaStream_t s);
 // dst = src / *c
 void launch_scale(const double* src, double* dst, long long n, const double* c, cudaStream_t s);
-// Tr T (Eq. (tTr)) and ln Z/N = L + 2^-step ln Tr; X^(n) along `axis` (Eq. (x)).
-void launch_trace_x(const double* T, Geom g, int axis, const double* L, int step, double* out3,
-                    int* status, cudaStream_t s);
+// Tr T (Eq. (tTr)) and ln Z/N = L + 2^-n ln Tr (n = *dstep); X^(n) along `axis` (Eq. (x)).
+// One CTA per instance: T + i*t_stride, L + i, out3 + 3 i.
+void launch_trace_x(const double* T, long long t_stride, int batch, Geom g, int axis, const double* L,
+                    const int* dstep, double* out3, cudaStream_t s);
 // out[..u_b=j..] = sum_i U[kk][i][j] in[..u_b=i..] on unprimed leg b (U: [chi][Db][Db] fp64).
 template <class Tin, class Tout>
 void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double* U, int kk,
@@ -43,23 +48,39 @@ template <class Tin, class Tout>
 void launch_pair_contract(const Tin* in, Tout* out, const View& v, int kaxis, int Di, int Dj,
                           long long si, long long sj, const double* U, int chi, long long in_base,
                           long long out_base, cudaStream_t s);
+// Same contraction with one thread per index of `rest` (the output axes without k'), computing
+// all chi outputs out[o + k' sk]; every input element is read once.
+template <class Tin, class Tout>
+void launch_pair_contract_all(const Tin* in, Tout* out, const View& rest, int Di, int Dj, long long si,
+                              long long sj, long long sk, const double* U, int chi, long long in_base,
+                              long long out_base, cudaStream_t s);
 
 // ---- gram.cu -------------------------------------------------------------------------------
 // Q[(i,al)][(i~,al~)] = sum over all other legs of T[..i..al..] T[..i~..al~..]; legs l1, l2 are
 // positions 0..2d-1 in the natural layout. partial: nsplit * nr^2 doubles scratch.
+// Instance i reads T + i*t_stride and writes Q + i*q_stride.
 int gram_nsplit();
-void launch_half_gram(const double* T, Geom g, int l1, int l2, double* partial, double* Q,
-                      cudaStream_t s);
-// G[(b1 b2)][(b1~ b2~)] = sum_{al,al~} Q1[(b1,al)][(b1~,al~)] Q2[(b2,al)][(b2~,al~)]
-void launch_gram_combine(const double* Q1, const double* Q2, int Db, int Da, double* G,
-                         cudaStream_t s);
+size_t gram_partial_doubles(int nr_max, int batch);  // scratch for `partial`
+void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, int l1, int l2,
+                      double* partial, double* Q, long long q_stride, cudaStream_t s);
+// G[(b1 b2)][(b1~ b2~)] = sum_{al,al~} Q1[(b1,al)][(b1~,al~)] Q2[(b2,al)][(b2~,al~)] per instance
+void launch_gram_combine(const double* Q1, const double* Q2, long long q_stride, int batch, int Db,
+                         int Da, double* G, long long g_stride, cudaStream_t s);
 
 // ---- eig.cu --------------------------------------------------------------------------------
-// Symmetric eigendecomposition of G (n x n, n <= 256) by cyclic Jacobi; eigenvalues sorted
-// descending into evals[0..n), the leading chi eigenvectors, sign-fixed, into U[k][0..n).
-// work: 2*n*n + 4*n doubles. Sets ST_NOCONV on the sweep limit.
-void launch_eig(const double* G, int n, int chi, double* evals, double* U, double* work,
-                int* status, cudaStream_t s);
+// Where the sorted eigenvalues go: base + i*inst_stride + (*step - 1)*step_stride for instance
+// i (nothing is written when the step is outside 1..max_steps).
+struct EigOut {
+  double* base;
+  long long inst_stride, step_stride;
+  const int* step;
+  int max_steps;
+};
+// Symmetric eigendecomposition of G (n x n, n <= 256) by cyclic Jacobi, one CTA per instance;
+// eigenvalues sorted descending, the leading chi eigenvectors, sign-fixed, into U[k][0..n).
+// work: batch * 2*n*n doubles. Sets ST_NOCONV on the sweep limit.
+void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o,
+                double* U, long long u_stride, double* work, int* status, cudaStream_t s);
 
 // ---- gemm_simt.cu --------------------------------------------------------------------------
 // C[m][n] = sum_k A[m][k] Bt[n][k] in FP64 (CUDA cores).
@@ -69,11 +90,17 @@ void launch_gemm_f64(const double* A, long long lda, const double* Bt, long long
 // ---- gemm_tc.cu ----------------------------------------------------------------------------
 // C[m][n] = sum over passes p of sum_k A_{a(p)}[m][k] Bt_{b(p)}[n][k], bf16 operand planes on
 // tcgen05, FP32 accumulation in TMEM. npass = 1: (hi,hi); 3: + (hi,lo), (lo,hi) with 2 planes;
-// 6: (hi,hi), (hi,mid), (mid,hi), (hi,lo), (mid,mid), (lo,hi) with 3 planes (hi, mid, lo).
+// 4: + (lo,lo); 6: (hi,hi), (hi,mid), (mid,hi), (hi,lo), (mid,mid), (lo,hi) with 3 planes.
+// bk = 64 or 32: the k-block width (the accumulator restarts and is folded once per k-block);
+// group_m: output tiles are visited in groups of group_m M-tiles (L2 reuse); fold_group: k-blocks
+// per accumulator fold (at most ring stages - 1 when > 1).
 // Returns 0 or a hotrg_status (tensor-map encode failure, bad alignment or sizes).
 int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
-                      int npass, int* status, double timeout_s, cudaStream_t s);
+                      int npass, int* status, double timeout_s, cudaStream_t s, int bk = 64,
+                      int group_m = 16, int fold_group = 1);
+// Largest fold group the kernel variant for (npass, bk) accepts.
+int max_fold_group(int npass, int bk);
 void launch_split_rows(const float* X, long long ldx, long long rows, long long cols,
                        const Planes<__nv_bfloat16>& out, long long ld, cudaStream_t s);
 

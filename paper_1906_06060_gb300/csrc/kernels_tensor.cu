@@ -77,8 +77,11 @@ __global__ void __launch_bounds__(256) k_sumsq_partial(const double* __restrict_
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
+__global__ void k_step_advance(int* dstep) { *dstep += 1; }
+
 __global__ void __launch_bounds__(256) k_norm_finish(const double* __restrict__ partial, double* c_out,
-                                                     double* lnc_log, double* L, int step, int* status) {
+                                                     double* lnc_log, double* L, const int* dstep, int* status) {
+  const int step = *dstep;
   __shared__ double sh[256];
   double s = 0.0;
   for (int i = threadIdx.x; i < kNormBlocks; i += 256) s += partial[i];
@@ -103,9 +106,13 @@ __global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst
 
 // ---------------------------------------------------------------------------- trace, X^(n)
 // out3[0] = Tr T, out3[1] = L + 2^-step ln Tr T, out3[2] = X^(n) along axis.
-__global__ void __launch_bounds__(256) k_trace_x(const double* __restrict__ T, Geom g, int axis,
-                                                 const double* L, int step, double* out3, int* status) {
+__global__ void __launch_bounds__(256) k_trace_x(const double* __restrict__ T, long long t_stride, Geom g,
+                                                 int axis, const double* L, const int* dstep, double* out3) {
   __shared__ double sh[256];
+  const int step = *dstep;
+  T += (long long)blockIdx.x * t_stride;
+  L += blockIdx.x;
+  out3 += 3 * blockIdx.x;
   __shared__ double A[kMaxBond * kMaxBond];
   const long long P = g.P;
   double s = 0.0;
@@ -132,7 +139,7 @@ __global__ void __launch_bounds__(256) k_trace_x(const double* __restrict__ T, G
     for (int i = 0; i < Da; ++i) trA += A[i * Da + i];
     for (int i = 0; i < Da; ++i)
       for (int j = 0; j < Da; ++j) trA2 += A[i * Da + j] * A[j * Da + i];
-    (void)status;  // a non-positive trace is reported by the free-energy query, not here
+    // a non-positive trace is reported by the free-energy query, not here
     out3[0] = tr;
     out3[1] = tr > 0.0 ? *L + ldexp(log(tr), -step) : nan("");
     out3[2] = trA * trA / trA2;
@@ -287,6 +294,53 @@ __global__ void __launch_bounds__(256) k_pair_contract(const Tin* __restrict__ i
   }
 }
 
+// All chi outputs of one "rest" index per thread: out[o + k' sk] = sum_{i,j} U[k'][i][j] in[r + i si + j sj]
+// (r, o: offsets of the rest index in the input and output views). Every input element is read
+// once; W is held in shared memory as [i][j][k'] so a warp reads it by broadcast.
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(256) k_pair_contract_all(const Tin* __restrict__ in, Tout* __restrict__ out,
+                                                           View v, long long total, int Di, int Dj,
+                                                           long long si, long long sj, long long sk,
+                                                           const double* __restrict__ U, int chi,
+                                                           long long in_base, long long out_base) {
+  using Acc = AccT<Tout>;
+  constexpr int kMaxChi = kMaxBond;
+  extern __shared__ unsigned char smraw[];
+  Acc* W = reinterpret_cast<Acc*>(smraw);  // [Di*Dj][chi]
+  const int nij = Di * Dj;
+  for (int t = threadIdx.x; t < chi * nij; t += blockDim.x) {
+    const int k = t / nij, ij = t % nij;
+    W[ij * chi + k] = U ? (Acc)U[t] : (Acc)1;
+  }
+  __syncthreads();
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long rem = idx, ioff = in_base, ooff = out_base;
+    for (int ax = v.ndim - 1; ax >= 0; --ax) {
+      const long long c = rem % v.shape[ax];
+      rem /= v.shape[ax];
+      ioff += c * v.in_stride[ax];
+      ooff += c * v.out_stride[ax];
+    }
+    Acc acc[kMaxChi];
+#pragma unroll
+    for (int k = 0; k < kMaxChi; ++k) acc[k] = 0;
+    for (int i = 0; i < Di; ++i) {
+      const Tin* src = in + ioff + i * si;
+      for (int j = 0; j < Dj; ++j) {
+        const Acc x = (Acc)src[j * sj];
+        const Acc* w = W + (i * Dj + j) * chi;
+#pragma unroll
+        for (int k = 0; k < kMaxChi; ++k)
+          if (k < chi) acc[k] += w[k] * x;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxChi; ++k)
+      if (k < chi) out[ooff + k * sk] = (Tout)acc[k];
+  }
+}
+
 }  // namespace
 
 // ============================================================================ launchers
@@ -298,11 +352,16 @@ void launch_init_tensor(double* T, long long inst_stride, int batch, int d, cons
   count_launches(1);
 }
 
+void launch_step_advance(int* dstep, cudaStream_t s) {
+  k_step_advance<<<1, 1, 0, s>>>(dstep);
+  count_launches(1);
+}
+
 void launch_norm_log(const double* x, long long n, double* partial, double* c_out, double* lnc_log,
-                     double* L, int step, int* status, cudaStream_t s) {
+                     double* L, const int* dstep, int* status, cudaStream_t s) {
   k_sumsq_partial<<<kNormBlocks, 256, 0, s>>>(x, n, partial);
   count_launches(1);
-  k_norm_finish<<<1, 256, 0, s>>>(partial, c_out, lnc_log, L, step, status);
+  k_norm_finish<<<1, 256, 0, s>>>(partial, c_out, lnc_log, L, dstep, status);
   count_launches(1);
 }
 
@@ -311,9 +370,9 @@ void launch_scale(const double* src, double* dst, long long n, const double* c, 
   count_launches(1);
 }
 
-void launch_trace_x(const double* T, Geom g, int axis, const double* L, int step, double* out3,
-                    int* status, cudaStream_t s) {
-  k_trace_x<<<1, 256, 0, s>>>(T, g, axis, L, step, out3, status);
+void launch_trace_x(const double* T, long long t_stride, int batch, Geom g, int axis, const double* L,
+                    const int* dstep, double* out3, cudaStream_t s) {
+  k_trace_x<<<batch, 256, 0, s>>>(T, t_stride, g, axis, L, dstep, out3);
   count_launches(1);
 }
 
@@ -369,6 +428,19 @@ void launch_pair_contract(const Tin* in, Tout* out, const View& v, int kaxis, in
   count_launches(1);
 }
 
+template <class Tin, class Tout>
+void launch_pair_contract_all(const Tin* in, Tout* out, const View& rest, int Di, int Dj, long long si,
+                              long long sj, long long sk, const double* U, int chi, long long in_base,
+                              long long out_base, cudaStream_t s) {
+  using Acc = AccT<Tout>;
+  long long total = 1;
+  for (int i = 0; i < rest.ndim; ++i) total *= rest.shape[i];
+  const size_t smem = sizeof(Acc) * (size_t)chi * Di * Dj;
+  k_pair_contract_all<Tin, Tout><<<grid_for(total, 256), 256, smem, s>>>(in, out, rest, total, Di, Dj, si, sj, sk,
+                                                                          U, chi, in_base, out_base);
+  count_launches(1);
+}
+
 // explicit instantiations: FP64 path (double everywhere) and BF16X3 path (float intermediates)
 template void launch_mode_unprimed<double, double>(const double*, double*, Geom, int, const double*, int, cudaStream_t);
 template void launch_mode_unprimed<double, float>(const double*, float*, Geom, int, const double*, int, cudaStream_t);
@@ -383,5 +455,8 @@ template void launch_build_y<double, __nv_bfloat16>(const double*, const Planes<
 template void launch_pair_contract<double, double>(const double*, double*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
 template void launch_pair_contract<float, float>(const float*, float*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
 template void launch_pair_contract<float, double>(const float*, double*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
+template void launch_pair_contract_all<double, double>(const double*, double*, const View&, int, int, long long, long long, long long, const double*, int, long long, long long, cudaStream_t);
+template void launch_pair_contract_all<float, float>(const float*, float*, const View&, int, int, long long, long long, long long, const double*, int, long long, long long, cudaStream_t);
+template void launch_pair_contract_all<float, double>(const float*, double*, const View&, int, int, long long, long long, long long, const double*, int, long long, long long, cudaStream_t);
 
 }  // namespace hotrg

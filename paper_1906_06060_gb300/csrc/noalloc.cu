@@ -61,7 +61,7 @@ extern "C" int hotrg_gemm_split_noalloc(const float* A, long long lda, const flo
                                         float* C, long long ldc, long long M, long long N, long long K,
                                         int npass, void* stream) {
   if (!A || !Bt || !C || M <= 0 || N <= 0 || K <= 0 || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
-  if (npass != 1 && npass != 3 && npass != 6) return HOTRG_EINVAL;
+  if (npass != 1 && npass != 3 && npass != 4 && npass != 6) return HOTRG_EINVAL;
   const long long ld = round64(K);
   if (M > kNoallocMaxElems || N > kNoallocMaxElems || (M + N) > kNoallocMaxElems / ld) return HOTRG_EINVAL;
   int err = HOTRG_OK;
@@ -74,7 +74,7 @@ extern "C" int hotrg_gemm_split_noalloc(const float* A, long long lda, const flo
   const size_t b_plane = (size_t)((N * ld * 2 + 255) / 256 * 256);
   char* p = base + kNoallocStatusBytes;
   if (kNoallocStatusBytes + 3 * (a_plane + b_plane) > kNoallocBytes) return HOTRG_EINVAL;
-  const int nparts = npass == 1 ? 1 : (npass == 3 ? 2 : 3);
+  const int nparts = npass == 1 ? 1 : (npass == 6 ? 3 : 2);
   Planes<__nv_bfloat16> Ap, Bp;
   Ap.nparts = Bp.nparts = nparts;
   for (int k = 0; k < 3; ++k) {

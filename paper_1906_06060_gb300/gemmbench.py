@@ -25,6 +25,8 @@ def main():
     ap.add_argument("--K", type=int, default=10000)
     ap.add_argument("--npass", type=int, default=3)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--kblock", type=int, default=64)
+    ap.add_argument("--fold-group", type=int, default=0)
     a = ap.parse_args()
     import torch
     lib = _lib.load()
@@ -37,7 +39,7 @@ def main():
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     s = torch.cuda.current_stream()
     args = lambda: (c_void_p(A.data_ptr()), A.stride(0), c_void_p(Bt.data_ptr()), Bt.stride(0),
-                    c_void_p(C.data_ptr()), C.stride(0), a.M, a.N, a.K, a.npass,
+                    c_void_p(C.data_ptr()), C.stride(0), a.M, a.N, a.K, a.npass, a.kblock, a.fold_group,
                     c_void_p(scratch.data_ptr()), nbytes, c_void_p(s.cuda_stream))
     check(lib.hotrg_gemm_split(*args()), "hotrg_gemm_split")   # warm-up (also splits planes)
     check(lib.hotrg_gemm_status(c_void_p(scratch.data_ptr()), c_void_p(s.cuda_stream)), "status")
@@ -52,7 +54,7 @@ def main():
     check(lib.hotrg_gemm_status(c_void_p(scratch.data_ptr()), c_void_p(s.cuda_stream)), "status")
     flops = 2.0 * a.M * a.N * a.K
     best = min(times)
-    print(json.dumps({"M": a.M, "N": a.N, "K": a.K, "npass": a.npass, "ms": times,
+    print(json.dumps({"M": a.M, "N": a.N, "K": a.K, "npass": a.npass, "kblock": a.kblock, "fold_group": a.fold_group, "ms": times,
                       "note": "timed region includes the plane split of A and Bt",
                       "alg_tflops": flops / (best * 1e-3) / 1e12,
                       "tensor_tflops": a.npass * flops / (best * 1e-3) / 1e12}))

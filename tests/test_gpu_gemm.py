@@ -13,19 +13,21 @@ def _bound(A, Bt, K, npass):
     products (bf16 unit roundoff u = 2^-8: 2u for hi*hi only, 3u^2 for 3 passes, 3u^3 for 6
     passes), plus FP32 accumulation (K * 2^-24)."""
     u = 2.0 ** -8
-    rel = {1: 2 * u, 3: 3 * u ** 2, 6: 3 * u ** 3}[npass]
+    rel = {1: 2 * u, 3: 3 * u ** 2, 4: 2 * u ** 2, 6: 3 * u ** 3}[npass]
     return (rel + K * 2.0 ** -24) * (np.abs(A) @ np.abs(Bt).T) + 1e-30
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 700, 200), (257, 513, 129), (1000, 2560, 1000),
                                    (2048, 1024, 4096)])
-@pytest.mark.parametrize("npass", [3, 1, 6])
-def test_gemm_bf16x3_matches_fp64(M, N, K, npass):
+@pytest.mark.parametrize("npass", [3, 1, 4, 6])
+@pytest.mark.parametrize("kblock,fold_group", [(64, 0), (32, 1), (32, 2), (32, 3)])
+def test_gemm_split_matches_fp64(M, N, K, npass, kblock, fold_group):
     import torch
     from paper_1906_06060_gb300 import gemm_split
     A = random_matrix(M, K, seed=M + K, scale_spread=2.0).astype(np.float32)
     Bt = random_matrix(N, K, seed=N + 7 * K).astype(np.float32)
-    C = gemm_split(torch.from_numpy(A).cuda(), torch.from_numpy(Bt).cuda(), npass=npass)
+    C = gemm_split(torch.from_numpy(A).cuda(), torch.from_numpy(Bt).cuda(), npass=npass, kblock=kblock,
+                   fold_group=fold_group)
     torch.cuda.synchronize()
     got = C.cpu().numpy().astype(np.float64)
     ref = A.astype(np.float64) @ Bt.astype(np.float64).T
@@ -43,7 +45,8 @@ def test_gemm_bf16x3_matches_fp64(M, N, K, npass):
 
 
 @pytest.mark.parametrize("npass", [3, 6])
-def test_gemm_accumulation_has_no_drift_with_k(npass):
+@pytest.mark.parametrize("kblock,fold_group", [(64, 1), (32, 1), (32, 2)])
+def test_gemm_accumulation_has_no_drift_with_k(npass, kblock, fold_group):
     """All-positive operands: every partial sum has the same sign, so an accumulator that
     rounds toward zero would lose ~ (number of MMAs) x 2^-25 relative. The promoted
     accumulation keeps the mean relative error at rounding level even for K = 8192."""
@@ -53,7 +56,8 @@ def test_gemm_accumulation_has_no_drift_with_k(npass):
     rng = np.random.default_rng(11)
     A = rng.uniform(0.5, 1.5, (M, K)).astype(np.float32)
     Bt = rng.uniform(0.5, 1.5, (N, K)).astype(np.float32)
-    C = gemm_split(torch.from_numpy(A).cuda(), torch.from_numpy(Bt).cuda(), npass=npass).cpu().numpy()
+    C = gemm_split(torch.from_numpy(A).cuda(), torch.from_numpy(Bt).cuda(), npass=npass,
+                   kblock=kblock, fold_group=fold_group).cpu().numpy()
     ref = A.astype(np.float64) @ Bt.astype(np.float64).T
     rel = (C.astype(np.float64) - ref) / ref
     bias = abs(float(np.mean(rel)))
