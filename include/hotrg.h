@@ -74,6 +74,8 @@ typedef struct hotrg_opts {
   int kblock;             /* split modes: K width of a pipeline stage, 32 or 64 (0 = 64) */
   int fold_group;         /* split modes: stages per accumulator fold, 1 or 2 (0 = 1): the tensor
                              cores' FP32 accumulator restarts every fold_group * kblock K */
+  int derivatives;        /* 1: also propagate d/d beta and d/d h of the flow with the isometries
+                             held fixed (forward-mode tangents, 4 extra squeezes per step) */
   int graphs;             /* 1: capture a steady-state step (bond dimensions unchanged) once per
                              axis as a CUDA graph and replay it (default 1; off while timing and
                              on the legacy default stream, which cannot be captured) */
@@ -86,6 +88,13 @@ typedef struct hotrg_obs {
   double lnz_per_site;    /* ln Z_N / N estimate after the last step, N = 2^steps */
   double last_ln_c;       /* ln c_n of the last step */
   double x_indicator;     /* X^(n) of Eq. (x) along the last axis (1 for steps == 0) */
+  /* with opts.derivatives (NaN otherwise), derivatives of the ln Z_N / N estimate with the
+   * isometries of every step held fixed, and what they give (H = -sum s s' - h sum s):
+   *   d(lnZ/N)/d beta = -<H>/N = d <s s'> + h <s>,   d(lnZ/N)/d h = beta <s>   */
+  double dlnz_dbeta;
+  double dlnz_dh;
+  double internal_energy; /* <H>/N = -d(lnZ/N)/d beta */
+  double magnetization;   /* <s> = (1/beta) d(lnZ/N)/d h */
 } hotrg_obs;
 
 typedef struct hotrg_ctx hotrg_ctx;
@@ -139,7 +148,8 @@ int hotrg_get_tensor(hotrg_ctx *c, int instance, int *dims, double *host, size_t
 
 /* Replace the tensor of `instance` by a host array in natural layout with bond dimensions
  * dims[0..d) (each 1..Dcut). Used to coarse-grain arbitrary tensors. It does not normalise and
- * does not touch the ln Z accumulator. Errors: EINVAL. */
+ * does not touch the ln Z accumulator; with opts.derivatives it zeroes the instance's tangents
+ * (the supplied tensor does not depend on beta or h). Errors: EINVAL. */
 int hotrg_set_tensor(hotrg_ctx *c, int instance, const int *dims, const double *host);
 
 /* Checkpoint: size of, save to and restore from a host buffer holding the full flow state

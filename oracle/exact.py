@@ -46,6 +46,49 @@ def lnz_bruteforce(beta: float, h: float, L: tuple[int, ...]) -> float:
     return float(m + math.log(np.sum(np.exp(expo - m))))
 
 
+def moments_bruteforce(beta: float, h: float, L: tuple[int, ...]) -> tuple[float, float]:
+    """(<sum over bonds s_i s_j> / N, <sum over sites s_i> / N) on the same periodic lattice as
+    lnz_bruteforce, by enumeration. With H = -sum_bonds s s' - h sum s these give
+    d(ln Z/N)/d beta = e_bond + h m and d(ln Z/N)/d h = beta m."""
+    L = tuple(int(x) for x in L)
+    N = int(np.prod(L))
+    if N > 20:
+        raise ValueError("enumeration limited to 20 spins")
+    sites = list(itertools.product(*[range(n) for n in L]))
+    index = {s: i for i, s in enumerate(sites)}
+    bonds = []
+    for s in sites:
+        for a, La in enumerate(L):
+            t = list(s)
+            t[a] = (t[a] + 1) % La
+            bonds.append((index[s], index[tuple(t)]))
+    cfg = ((np.arange(2 ** N)[:, None] >> np.arange(N)[None, :]) & 1).astype(np.int8)
+    spins = 1 - 2 * cfg.astype(np.float64)
+    i, j = np.array(bonds).T
+    e_bond = np.sum(spins[:, i] * spins[:, j], axis=1)
+    e_field = np.sum(spins, axis=1)
+    expo = beta * e_bond + beta * h * e_field
+    w = np.exp(expo - expo.max())
+    z = w.sum()
+    return float(np.dot(w, e_bond) / z / N), float(np.dot(w, e_field) / z / N)
+
+
+def dlnz_1d(beta: float, h: float, N: int) -> tuple[float, float]:
+    """(d/d beta, d/d h) of lnz_1d(beta, h, N) / N, differentiating the transfer-matrix
+    eigenvalues: with q = (lam-/lam+)^N, d(ln Z)/N = (dlam+/lam+ + q dlam-/lam-) / (1 + q)."""
+    eb = math.exp(beta)
+    sh, ch = math.sinh(beta * h), math.cosh(beta * h)
+    r = math.sqrt(eb * eb * sh * sh + 1.0 / (eb * eb))
+    lp, lm = eb * ch + r, eb * ch - r
+    # r^2 = e^{2b} sinh^2(bh) + e^{-2b}
+    dr_db = (eb * eb * sh * sh + eb * eb * sh * ch * h - 1.0 / (eb * eb)) / r
+    dr_dh = eb * eb * sh * ch * beta / r
+    dlp_db, dlm_db = eb * ch + eb * sh * h + dr_db, eb * ch + eb * sh * h - dr_db
+    dlp_dh, dlm_dh = eb * sh * beta + dr_dh, eb * sh * beta - dr_dh
+    q = (lm / lp) ** N
+    return ((dlp_db / lp + q * dlm_db / lm) / (1.0 + q), (dlp_dh / lp + q * dlm_dh / lm) / (1.0 + q))
+
+
 def lnz_1d(beta: float, h: float, N: int) -> float:
     """ln Z of the periodic Ising chain: ln(lam+^N + lam-^N), transfer-matrix eigenvalues
     lam_pm = e^b cosh(bh) +- sqrt(e^{2b} sinh^2(bh) + e^{-2b})."""

@@ -317,6 +317,7 @@ class Flow:
     spectra: list[dict[int, np.ndarray]] = field(default_factory=list)
     gaps: list[dict[int, float]] = field(default_factory=list)
     x: list[float] = field(default_factory=list)
+    isometries: list[dict[int, np.ndarray]] = field(default_factory=list)   # U of every step
     tensor: np.ndarray | None = None
 
     @property
@@ -330,8 +331,10 @@ class Flow:
 
 
 def run(d: int, beta: float, h: float, Dcut: int, nsteps: int, order: list[int] | None = None,
-        norm=frobenius, T0: np.ndarray | None = None, keep_tensor: bool = False) -> Flow:
-    """Full flow (reading R4): normalise T^(0), then n steps with ln-norm accumulation."""
+        norm=frobenius, T0: np.ndarray | None = None, keep_tensor: bool = False,
+        isometries: list[dict[int, np.ndarray]] | None = None) -> Flow:
+    """Full flow (reading R4): normalise T^(0), then n steps with ln-norm accumulation.
+    `isometries` (one dict per step, as recorded in Flow.isometries) freezes U at every step."""
     order = default_order(d) if order is None else list(order)
     T = initial_tensor(d, beta, h) if T0 is None else np.array(T0, dtype=np.float64)
     flow = Flow(d=d, beta=beta, h=h, Dcut=Dcut)
@@ -342,7 +345,7 @@ def run(d: int, beta: float, h: float, Dcut: int, nsteps: int, order: list[int] 
     flow.lnz.append(L + math.log(trace(T)))
     for n in range(1, nsteps + 1):
         a = order[(n - 1) % len(order)]
-        T, info = coarse_grain(T, a, Dcut)
+        T, info = coarse_grain(T, a, Dcut, None if isometries is None else isometries[n - 1])
         c = norm(T)
         if not np.isfinite(c) or c <= 0:
             raise FloatingPointError(f"step {n}: norm {c}")
@@ -358,9 +361,36 @@ def run(d: int, beta: float, h: float, Dcut: int, nsteps: int, order: list[int] 
         flow.spectra.append({b: iso.eigenvalues for b, iso in info.isometries.items()})
         flow.gaps.append({b: iso.gap for b, iso in info.isometries.items()})
         flow.x.append(x_indicator(T, a))
+        flow.isometries.append({b: iso.U for b, iso in info.isometries.items()}
+                               if isometries is None else isometries[n - 1])
     if keep_tensor:
         flow.tensor = T
     return flow
+
+
+def fixed_isometry_derivatives(d: int, beta: float, h: float, Dcut: int, nsteps: int,
+                               eps: float = 1e-3) -> tuple[np.ndarray, np.ndarray]:
+    """d/d beta and d/d h of the ln Z_N / N estimate after every step 0..nsteps, with the
+    isometries of every step frozen at their values at (beta, h) (reading R9).
+
+    Central differences of the frozen flow, Richardson-extrapolated from steps eps and eps/2
+    (truncation error O(eps^4)). Where every step is lossless (chi = D^2), the frozen U is an
+    orthogonal change of basis and these are the exact derivatives of ln Z / N of the lattice;
+    with H = -sum s s' - h sum s they give <H>/N = -d/d beta and <s> = (d/d h) / beta."""
+    base = run(d, beta, h, Dcut, nsteps)
+    U = base.isometries
+
+    def lnz(b, hh):
+        return np.array(run(d, b, hh, Dcut, nsteps, isometries=U).lnz)
+
+    def central(f, e):
+        return (f(e) - f(-e)) / (2.0 * e)
+
+    out = []
+    for f in (lambda e: lnz(beta + e, h), lambda e: lnz(beta, h + e)):
+        d1, d2 = central(f, eps), central(f, eps / 2)
+        out.append((4.0 * d2 - d1) / 3.0)
+    return out[0], out[1]
 
 
 def dims_schedule(d: int, Dcut: int, nsteps: int, order: list[int] | None = None) -> list[list[int]]:

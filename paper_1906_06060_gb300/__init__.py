@@ -32,7 +32,7 @@ def _torch():
 
 
 def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0, kblock=0,
-          graphs=True, fold_group=0):
+          graphs=True, fold_group=0, derivatives=False):
     lib = _lib.load()
     o = _lib.Opts()
     lib.hotrg_opts_default(byref(o))
@@ -43,14 +43,15 @@ def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=
     o.kblock = int(kblock)
     o.graphs = 1 if graphs else 0
     o.fold_group = int(fold_group)
+    o.derivatives = 1 if derivatives else 0
     o.max_steps = int(max_steps)
     o.wait_timeout_s = float(wait_timeout_s)
     return o
 
 
 def workspace_bytes(d: int, Dcut: int, precision="fp64", batch: int = 1, fp64_steps: int = 2,
-                    max_steps: int = 64, x6_steps: int = 0) -> int:
-    o = _opts(precision, batch, fp64_steps, max_steps, x6_steps=x6_steps)
+                    max_steps: int = 64, x6_steps: int = 0, derivatives: bool = False) -> int:
+    o = _opts(precision, batch, fp64_steps, max_steps, x6_steps=x6_steps, derivatives=derivatives)
     n = c_size_t(0)
     check(_lib.load().hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
     return int(n.value)
@@ -66,7 +67,7 @@ class HOTRG:
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
                  max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0,
-                 kblock: int = 0, graphs: bool = True, fold_group: int = 0):
+                 kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives: bool = False):
         torch = _torch()
         lib = _lib.load()
         betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))
@@ -81,7 +82,8 @@ class HOTRG:
         self.d, self.Dcut, self.batch, self.precision = d, Dcut, batch, precision
         self.beta = betas
         self.h = hs
-        o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps, kblock, graphs, fold_group)
+        o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps, kblock, graphs, fold_group,
+                  derivatives)
         n = c_size_t(0)
         check(lib.hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -50,6 +50,11 @@ struct hotrg_ctx {
   double *G = nullptr, *U = nullptr, *ework = nullptr;
   int* status = nullptr;
   int* dstep = nullptr;       // device-side step counter (steps done)
+  // tangents d/d beta (0) and d/d h (1) of the flow with the isometries held fixed
+  bool deriv = false;
+  double *dT = nullptr;       // [2][batch][Pmax^2] tangents of the normalised tensors
+  double *D1 = nullptr, *D2 = nullptr;  // tangent squeeze outputs (one instance at a time)
+  double *dL = nullptr, *dlnc = nullptr, *dout = nullptr;  // [2][batch]
   long long q_stride = 0, g_stride = 0, u_stride = 0;  // per-instance strides (doubles)
   void *Tt = nullptr, *Bt = nullptr, *X1 = nullptr, *X2 = nullptr, *Y = nullptr, *O = nullptr;
   void *R1 = nullptr, *R2 = nullptr;
@@ -259,6 +264,14 @@ size_t carve(hotrg_ctx* c, char* base) {
   c->U = k.take<double>(sizeof(double) * c->u_stride * c->batch);
   c->ework = k.take<double>(sizeof(double) * 2 * nmax * nmax * c->batch);
   (void)nr_max;
+  if (c->deriv) {
+    c->dT = k.take<double>(sizeof(double) * 2 * P2 * c->batch);
+    c->D1 = k.take<double>(sizeof(double) * P2);
+    c->D2 = k.take<double>(sizeof(double) * P2);
+    c->dL = k.take<double>(sizeof(double) * 2 * c->batch);
+    c->dlnc = k.take<double>(sizeof(double) * 2 * c->batch);
+    c->dout = k.take<double>(sizeof(double) * 2 * c->batch);
+  }
   c->sz_Tt = n.Tt; c->Tt = k.take<char>(n.Tt);
   c->sz_Bt = n.Bt; c->Bt = k.take<char>(n.Bt);
   c->sz_X = n.X;   c->X1 = k.take<char>(n.X); c->X2 = k.take<char>(n.X);
@@ -391,8 +404,11 @@ struct Ops<float> {
 
 // planes: 0 = FP64 path (TC = double), 2 / 3 = tensor-core path (TC = float) with 3 / 6 passes.
 template <class TC>
-int squeeze(hotrg_ctx* c, const double* Tin, const double* U, const Geom& g, const Geom& gn, int a,
-            const int* chi, const int* trans, int nt, int planes, int npass) {
+// Coarse-grained tensor of the pair (T1 lower site, T2 upper site along a) into `out` (new
+// geometry gn): T1 feeds the A operand, T2 the B operand. The flow uses T1 = T2 = T; the tangent
+// of a step uses (dT, T) and (T, dT).
+int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const double* U, const Geom& g,
+            const Geom& gn, int a, const int* chi, const int* trans, int nt, int planes, int npass) {
   using Op = typename Ops<TC>::Op;
   constexpr bool mixed = std::is_same<TC, float>::value;
   cudaStream_t s = c->stream;
@@ -410,7 +426,7 @@ int squeeze(hotrg_ctx* c, const double* Tin, const double* U, const Geom& g, con
   // B operand
   PhaseScope* ops_scope = new PhaseScope(c, PH_OPERANDS);
   TC* Tt = static_cast<TC*>(c->Tt);
-  launch_transpose<TC>(Tin, Tt, P, s);
+  launch_transpose<TC>(T2, Tt, P, s);
   Planes<Op> Bt;
   Bt.nparts = nparts;
   for (int k = 0; k < 3; ++k) Bt.p[k] = static_cast<Op*>(c->Bt) + (size_t)(k < nparts ? k : 0) * chi3 * P * ldk;
@@ -436,12 +452,12 @@ int squeeze(hotrg_ctx* c, const double* Tin, const double* U, const Geom& g, con
     // producer: mode products on the unprimed legs of the other transverse axes
     ops_scope = new PhaseScope(c, PH_OPERANDS);
     if (no == 0) {
-      launch_build_y<double, Op>(Tin, Y, ldk, g, a, s);
+      launch_build_y<double, Op>(T1, Y, ldk, g, a, s);
     } else {
       TC* X1 = static_cast<TC*>(c->X1);
       TC* X2 = static_cast<TC*>(c->X2);
       if (kcnt[0] != prev_k0) {
-        launch_mode_unprimed<double, TC>(Tin, X1, g, trans[0], Ub(trans[0]), kcnt[0], s);
+        launch_mode_unprimed<double, TC>(T1, X1, g, trans[0], Ub(trans[0]), kcnt[0], s);
         prev_k0 = kcnt[0];
       }
       const TC* X = X1;
@@ -494,7 +510,7 @@ int squeeze(hotrg_ctx* c, const double* Tin, const double* U, const Geom& g, con
     if (c3 >= 0) {
       // final axes after contracting c3 (m_c3 removed, n_c3 -> k'_c3)
       final_strides(axes, c3, c3, gn, c3, fs);
-      contract_axes<TC, double>(axes, cur, c->Tnext, c3, chi3, Ub(c3), fs, out_base, s);
+      contract_axes<TC, double>(axes, cur, out, c3, chi3, Ub(c3), fs, out_base, s);
     } else {
       // d = 1: plain copy O[m][n] -> Tnext[u'][p']
       final_strides(axes, -2, -1, gn, -1, fs);
@@ -505,7 +521,7 @@ int squeeze(hotrg_ctx* c, const double* Tin, const double* U, const Geom& g, con
         v.in_stride[i] = axes[i].stride;
         v.out_stride[i] = fs[i];
       }
-      launch_pair_contract<TC, double>(cur, c->Tnext, v, -1, 1, 1, 0, 0, nullptr, 1, 0, 0, s);
+      launch_pair_contract<TC, double>(cur, out, v, -1, 1, 1, 0, 0, nullptr, 1, 0, 0, s);
     }
   }
   return HOTRG_OK;
@@ -544,6 +560,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   c.fp64_steps = opt->fp64_steps;
   c.x6_steps = opt->x6_steps;
   c.max_steps = opt->max_steps;
+  c.deriv = opt->derivatives != 0;
   *bytes = carve(&c, nullptr);
   return HOTRG_OK;
 }
@@ -581,6 +598,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->kblock_fixed = opt->kblock != 0;
   c->fold_group = opt->fold_group;
   c->graphs = opt->graphs != 0;
+  c->deriv = opt->derivatives != 0;
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
@@ -605,13 +623,27 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   launch_init_tensor(c->T, P2, c->batch, d, c->dbeta, c->dh, s);
   const long long n0 = 1LL << (2 * d);
   Geom g = make_geom(d, c->dims);
+  if (c->deriv) {
+    cudaMemsetAsync(c->dL, 0, sizeof(double) * 2 * c->batch, s);
+    for (int w = 0; w < 2; ++w) launch_init_tangent(c->dT + w * P2 * c->batch, P2, c->batch, d, c->dbeta, c->dh, w, s);
+  }
   for (int i = 0; i < c->batch; ++i) {
     double* Ti = c->T + i * P2;
     launch_norm_log(Ti, n0, c->norm_partial, c->cval + i, c->lnc_log + (long long)i * (c->max_steps + 1),
                     c->L + i, c->dstep, c->status, s);
+    if (c->deriv)
+      for (int w = 0; w < 2; ++w) {
+        double* dTi = c->dT + (w * c->batch + i) * P2;
+        launch_tangent_norm(Ti, dTi, nullptr, dTi, n0, c->cval + i, c->norm_partial, c->dlnc + w * c->batch + i,
+                            c->dL + w * c->batch + i, c->dstep, s);
+      }
     launch_scale(Ti, Ti, n0, c->cval + i, s);
   }
   launch_trace_x(c->T, P2, c->batch, g, d - 1, c->L, c->dstep, c->out3, s);
+  if (c->deriv)
+    for (int w = 0; w < 2; ++w)
+      launch_trace_tangent(c->T, c->dT + w * P2 * c->batch, P2, c->batch, g.P, c->dL + w * c->batch, c->dstep,
+                           c->dout + w * c->batch, s);
   if (cuda_err(c)) {
     delete c;
     return HOTRG_EDEVICE;
@@ -661,16 +693,34 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
   for (int i = 0; i < c->batch; ++i) {
     const double* Ti = c->T + i * P2max;
     const double* Ui = c->U + i * c->u_stride;
-    const int rc = planes ? squeeze<float>(c, Ti, Ui, g, gn, a, chi, trans, nt, planes, npass)
-                          : squeeze<double>(c, Ti, Ui, g, gn, a, chi, trans, nt, 0, 0);
+    auto sq = [&](const double* A1, const double* A2, double* out) {
+      return planes ? squeeze<float>(c, A1, A2, out, Ui, g, gn, a, chi, trans, nt, planes, npass)
+                    : squeeze<double>(c, A1, A2, out, Ui, g, gn, a, chi, trans, nt, 0, 0);
+    };
+    int rc = sq(Ti, Ti, c->Tnext);
     if (rc) return rc;
-    PhaseScope norm_scope(c, PH_NORM);
     double* Tw = c->T + i * P2max;
-    launch_norm_log(c->Tnext, gn.P * gn.P, c->norm_partial, c->cval + i,
-                    c->lnc_log + (long long)i * (c->max_steps + 1), c->L + i, c->dstep, c->status, s);
+    {
+      PhaseScope norm_scope(c, PH_NORM);
+      launch_norm_log(c->Tnext, gn.P * gn.P, c->norm_partial, c->cval + i,
+                      c->lnc_log + (long long)i * (c->max_steps + 1), c->L + i, c->dstep, c->status, s);
+    }
+    if (c->deriv) {
+      // tangent of the step with U fixed: dT' = S(dT, T) + S(T, dT), then of T' / ||T'||
+      for (int w = 0; w < 2; ++w) {
+        double* dTi = c->dT + (w * c->batch + i) * P2max;
+        if ((rc = sq(dTi, Ti, c->D1)) || (rc = sq(Ti, dTi, c->D2))) return rc;
+        launch_tangent_norm(c->Tnext, c->D1, c->D2, dTi, gn.P * gn.P, c->cval + i, c->norm_partial,
+                            c->dlnc + w * c->batch + i, c->dL + w * c->batch + i, c->dstep, s);
+      }
+    }
     launch_scale(c->Tnext, Tw, gn.P * gn.P, c->cval + i, s);
   }
   launch_trace_x(c->T, P2max, c->batch, gn, a, c->L, c->dstep, c->out3, s);
+  if (c->deriv)
+    for (int w = 0; w < 2; ++w)
+      launch_trace_tangent(c->T, c->dT + w * P2max * c->batch, P2max, c->batch, gn.P, c->dL + w * c->batch,
+                           c->dstep, c->dout + w * c->batch, s);
   if (c->timing) {
     double f = 2.0 * (double)g.P * (double)g.P * (double)g.P * c->batch;
     for (int t = 0; t < nt; ++t) f *= chi[trans[t]];
@@ -779,6 +829,17 @@ int hotrg_observables(hotrg_ctx* c, int instance, hotrg_obs* out) {
   out->lnz_per_site = o3[1];
   out->last_ln_c = lc;
   out->x_indicator = c->steps ? o3[2] : 1.0;
+  out->dlnz_dbeta = out->dlnz_dh = out->internal_energy = out->magnetization = std::nan("");
+  if (c->deriv) {
+    double db = 0.0, dh = 0.0;
+    if (cudaMemcpy(&db, c->dout + instance, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&dh, c->dout + c->batch + instance, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return c->sticky = HOTRG_EDEVICE;
+    out->dlnz_dbeta = db;
+    out->dlnz_dh = dh;
+    out->internal_energy = -db;                 // <H>/N with H = -sum s s' - h sum s
+    out->magnetization = dh / c->beta[instance];  // <s>
+  }
   return HOTRG_OK;
 }
 
@@ -842,6 +903,11 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
       cudaMemcpy(c->T + instance * c->Pmax * c->Pmax, host, sizeof(double) * g.P * g.P,
                  cudaMemcpyHostToDevice) != cudaSuccess)
     return c->sticky = HOTRG_EDEVICE;
+  // a tensor supplied from outside does not depend on (beta, h): its tangents are zero
+  for (int w = 0; c->deriv && w < 2; ++w)
+    if (cudaMemsetAsync(c->dT + (w * c->batch + instance) * c->Pmax * c->Pmax, 0, sizeof(double) * g.P * g.P,
+                        c->stream) != cudaSuccess)
+      return c->sticky = HOTRG_EDEVICE;
   for (int b = 0; b < c->d; ++b) c->dims[b] = dims[b];
   return HOTRG_OK;
 }
@@ -849,18 +915,25 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
 // ---- checkpoint format: header, then per instance T (P^2), L, lnc_log, spec_log, out3
 struct StateHeader {
   char magic[8];
-  int version, d, Dcut, batch, precision, max_steps, steps, last_axis;
+  int version, d, Dcut, batch, precision, max_steps, steps, last_axis, deriv;
   int dims[kMaxD];
   long long P;
   int hist_dims[64][kMaxD];
   int hist_axis[64];
 };
 
+// Bytes saved per instance: T, L, the ln c log, the spectra, out3 and, with tangents, for each
+// of the two parameters dT, dL and the derivative of ln Z / N.
+size_t state_per_instance(const hotrg_ctx* c, long long P) {
+  size_t n = (size_t)P * P + 1 + (c->max_steps + 1) + c->spec_stride + 3;
+  if (c->deriv) n += 2 * ((size_t)P * P + 2);
+  return sizeof(double) * n;
+}
+
 int hotrg_state_size(hotrg_ctx* c, size_t* bytes) {
   if (!c || !bytes) return HOTRG_EINVAL;
   Geom g = make_geom(c->d, c->dims);
-  const size_t per = sizeof(double) * ((size_t)g.P * g.P + 1 + (c->max_steps + 1) + c->spec_stride + 3);
-  *bytes = sizeof(StateHeader) + per * c->batch;
+  *bytes = sizeof(StateHeader) + state_per_instance(c, g.P) * c->batch;
   return HOTRG_OK;
 }
 
@@ -872,7 +945,8 @@ int hotrg_state_save(hotrg_ctx* c, void* host, size_t cap) {
   StateHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "HOTRGST", 8);
-  h.version = 1;
+  h.version = 2;
+  h.deriv = c->deriv ? 1 : 0;
   h.d = c->d; h.Dcut = c->Dcut; h.batch = c->batch; h.precision = c->precision;
   h.max_steps = c->max_steps; h.steps = c->steps; h.last_axis = c->last_axis;
   for (int b = 0; b < kMaxD; ++b) h.dims[b] = c->dims[b];
@@ -896,6 +970,16 @@ int hotrg_state_save(hotrg_ctx* c, void* host, size_t cap) {
     p += sizeof(double) * c->spec_stride;
     ok = ok && cudaMemcpy(p, c->out3 + 3 * i, sizeof(double) * 3, cudaMemcpyDeviceToHost) == cudaSuccess;
     p += sizeof(double) * 3;
+    for (int w = 0; c->deriv && w < 2; ++w) {
+      const long long j = w * c->batch + i;
+      ok = ok && cudaMemcpy(p, c->dT + j * c->Pmax * c->Pmax, sizeof(double) * g.P * g.P,
+                            cudaMemcpyDeviceToHost) == cudaSuccess;
+      p += sizeof(double) * g.P * g.P;
+      ok = ok && cudaMemcpy(p, c->dL + j, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess;
+      p += sizeof(double);
+      ok = ok && cudaMemcpy(p, c->dout + j, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess;
+      p += sizeof(double);
+    }
     if (!ok) return c->sticky = HOTRG_EDEVICE;
   }
   return HOTRG_OK;
@@ -905,13 +989,13 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
   if (!c || !host || size < sizeof(StateHeader)) return HOTRG_EINVAL;
   StateHeader h;
   std::memcpy(&h, host, sizeof(h));
-  if (std::memcmp(h.magic, "HOTRGST", 8) || h.version != 1 || h.d != c->d || h.Dcut != c->Dcut ||
-      h.batch != c->batch || h.precision != c->precision || h.max_steps != c->max_steps)
+  if (std::memcmp(h.magic, "HOTRGST", 8) || h.version != 2 || h.d != c->d || h.Dcut != c->Dcut ||
+      h.batch != c->batch || h.precision != c->precision || h.max_steps != c->max_steps ||
+      h.deriv != (c->deriv ? 1 : 0))
     return HOTRG_EINVAL;
   Geom g = make_geom(h.d, h.dims);
   if (g.P != h.P || g.P > c->Pmax) return HOTRG_EINVAL;
-  const size_t per = sizeof(double) * ((size_t)g.P * g.P + 1 + (c->max_steps + 1) + c->spec_stride + 3);
-  if (size < sizeof(StateHeader) + per * c->batch) return HOTRG_EINVAL;
+  if (size < sizeof(StateHeader) + state_per_instance(c, g.P) * c->batch) return HOTRG_EINVAL;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return c->sticky = HOTRG_EDEVICE;
   const char* p = static_cast<const char*>(host) + sizeof(h);
   for (int i = 0; i < c->batch; ++i) {
@@ -927,6 +1011,16 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
     p += sizeof(double) * c->spec_stride;
     ok = ok && cudaMemcpy(c->out3 + 3 * i, p, sizeof(double) * 3, cudaMemcpyHostToDevice) == cudaSuccess;
     p += sizeof(double) * 3;
+    for (int w = 0; c->deriv && w < 2; ++w) {
+      const long long j = w * c->batch + i;
+      ok = ok && cudaMemcpy(c->dT + j * c->Pmax * c->Pmax, p, sizeof(double) * g.P * g.P,
+                            cudaMemcpyHostToDevice) == cudaSuccess;
+      p += sizeof(double) * g.P * g.P;
+      ok = ok && cudaMemcpy(c->dL + j, p, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+      p += sizeof(double);
+      ok = ok && cudaMemcpy(c->dout + j, p, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+      p += sizeof(double);
+    }
     if (!ok) return c->sticky = HOTRG_EDEVICE;
   }
   if (cudaMemcpy(c->dstep, &h.steps, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)

@@ -21,6 +21,17 @@ void launch_step_advance(int* dstep, cudaStream_t s);
 // norm.
 void launch_norm_log(const double* x, long long n, double* partial, double* c_out,
                      double* lnc_log, double* L, const int* dstep, int* status, cudaStream_t s);
+// Tangents of the flow (fixed isometries). dT = d T^(0) / d beta (which = 0) or d / d h (which = 1).
+void launch_init_tangent(double* dT, long long inst_stride, int batch, int d, const double* beta, const double* h,
+                         int which, cudaStream_t s);
+// For an unnormalised tensor T with norm *c and tangent D = D1 + D2 (D2 may be null):
+// dlnc = <T, D> / c^2, dL += 2^-n dlnc (n = *dstep), dTn = (D - dlnc T) / c (tangent of T / c).
+void launch_tangent_norm(const double* T, const double* D1, const double* D2, double* dTn, long long n,
+                         const double* c, double* partial, double* dlnc, double* dL, const int* dstep,
+                         cudaStream_t s);
+// out[i] = dL[i] + 2^-n Tr dT_i / Tr T_i for every instance.
+void launch_trace_tangent(const double* T, const double* dT, long long t_stride, int batch, long long P,
+                          const double* dL, const int* dstep, double* out, cudaStream_t s);
 // dst = src / *c
 void launch_scale(const double* src, double* dst, long long n, const double* c, cudaStream_t s);
 // Tr T (Eq. (tTr)) and ln Z/N = L + 2^-n ln Tr (n = *dstep); X^(n) along `axis` (Eq. (x)).

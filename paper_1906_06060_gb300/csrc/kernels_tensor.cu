@@ -51,6 +51,36 @@ __global__ void k_init_tensor(double* T, long long inst_stride, int d, const dou
   T[inst * inst_stride + idx] = acc;
 }
 
+// ---------------------------------------------------------------------------- T^(0) tangents
+// dT[idx] = d T^(0)[idx] / d beta (which = 0) or d / d h (which = 1). With n1 legs at index 1 and
+// n0 = 2d - n1 at index 0, prod W = cosh^{n0/2} (s sinh^{1/2})^{n1} and
+//   d/d beta [V_s prod W] = V_s prod W (h s + n0 tanh(b)/2 + n1 coth(b)/2),
+//   d/d h    [V_s prod W] = V_s prod W (b s).
+__global__ void k_init_tangent(double* dT, long long inst_stride, int d, const double* beta, const double* hfield,
+                               int which) {
+  const int nlegs = 2 * d;
+  const int total = 1 << nlegs;
+  const int inst = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const double b = beta[inst], h = hfield[inst];
+  const double wc = sqrt(cosh(b)), ws = sqrt(sinh(b));
+  const int n1 = __popc(idx);
+  const int n0 = nlegs - n1;
+  double acc = 0.0;
+  for (int si = 0; si < 2; ++si) {
+    const double s = si ? -1.0 : 1.0;
+    double v = exp(s * b * h);
+    for (int l = 0; l < nlegs; ++l) {
+      const int bit = (idx >> (nlegs - 1 - l)) & 1;
+      v *= bit ? s * ws : wc;
+    }
+    const double f = which == 0 ? h * s + 0.5 * n0 * tanh(b) + 0.5 * n1 / tanh(b) : b * s;
+    acc += v * f;
+  }
+  dT[inst * inst_stride + idx] = acc;
+}
+
 // ---------------------------------------------------------------------------- norms
 template <int BS>
 __device__ double block_sum(double v, double* sh) {
@@ -94,6 +124,65 @@ __global__ void __launch_bounds__(256) k_norm_finish(const double* __restrict__ 
     lnc_log[step] = lc;
     *L += ldexp(lc, -step);
   }
+}
+
+// partial[b] = sum over this block's share of x[i] (y1[i] + y2[i]) (y2 may be null): fixed grid.
+__global__ void __launch_bounds__(256) k_dot_partial(const double* __restrict__ x, const double* __restrict__ y1,
+                                                     const double* __restrict__ y2, long long n,
+                                                     double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)kNormBlocks * 256) {
+    const double y = y2 ? y1[i] + y2[i] : y1[i];
+    s = fma(x[i], y, s);
+  }
+  const double t = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// dlnc = <T, D> / c^2 for the tangent D of an unnormalised tensor T with norm c; dL += 2^-n dlnc.
+__global__ void __launch_bounds__(256) k_tangent_finish(const double* __restrict__ partial, const double* c,
+                                                        double* dlnc, double* dL, const int* dstep) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kNormBlocks; i += 256) s += partial[i];
+  const double t = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) {
+    const double cv = *c;
+    const double v = t / (cv * cv);
+    *dlnc = v;
+    *dL += ldexp(v, -*dstep);
+  }
+}
+
+// dTn = (D1 + D2) / c - dlnc T / c : the tangent of T / ||T||.
+// D1 and dTn may be the same buffer (each element is read before it is written, by one thread).
+__global__ void k_tangent_update(const double* __restrict__ T, const double* D1,
+                                 const double* __restrict__ D2, double* dTn, long long n,
+                                 const double* c, const double* dlnc) {
+  const double inv = 1.0 / *c, g = *dlnc;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double d = D2 ? D1[i] + D2[i] : D1[i];
+    dTn[i] = (d - g * T[i]) * inv;
+  }
+}
+
+// d(ln Z/N) = dL + 2^-n Tr dT / Tr T for every instance (one CTA each).
+__global__ void __launch_bounds__(256) k_trace_tangent(const double* __restrict__ T, const double* __restrict__ dT,
+                                                       long long t_stride, long long P, const double* dL,
+                                                       const int* dstep, double* out) {
+  __shared__ double sh[256];
+  T += (long long)blockIdx.x * t_stride;
+  dT += (long long)blockIdx.x * t_stride;
+  double a = 0.0, b = 0.0;
+  for (long long u = threadIdx.x; u < P; u += 256) {
+    a += T[u * P + u];
+    b += dT[u * P + u];
+  }
+  const double ta = block_sum<256>(a, sh);
+  const double tb = block_sum<256>(b, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = dL[blockIdx.x] + ldexp(tb / ta, -*dstep);
 }
 
 __global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst, long long n,
@@ -362,6 +451,30 @@ void launch_norm_log(const double* x, long long n, double* partial, double* c_ou
   k_sumsq_partial<<<kNormBlocks, 256, 0, s>>>(x, n, partial);
   count_launches(1);
   k_norm_finish<<<1, 256, 0, s>>>(partial, c_out, lnc_log, L, dstep, status);
+  count_launches(1);
+}
+
+void launch_init_tangent(double* dT, long long inst_stride, int batch, int d, const double* beta, const double* h,
+                         int which, cudaStream_t s) {
+  const int total = 1 << (2 * d);
+  k_init_tangent<<<dim3((total + 255) / 256, batch), 256, 0, s>>>(dT, inst_stride, d, beta, h, which);
+  count_launches(1);
+}
+
+void launch_tangent_norm(const double* T, const double* D1, const double* D2, double* dTn, long long n,
+                         const double* c, double* partial, double* dlnc, double* dL, const int* dstep,
+                         cudaStream_t s) {
+  k_dot_partial<<<kNormBlocks, 256, 0, s>>>(T, D1, D2, n, partial);
+  count_launches(1);
+  k_tangent_finish<<<1, 256, 0, s>>>(partial, c, dlnc, dL, dstep);
+  count_launches(1);
+  k_tangent_update<<<grid_for(n, 256), 256, 0, s>>>(T, D1, D2, dTn, n, c, dlnc);
+  count_launches(1);
+}
+
+void launch_trace_tangent(const double* T, const double* dT, long long t_stride, int batch, long long P,
+                          const double* dL, const int* dstep, double* out, cudaStream_t s) {
+  k_trace_tangent<<<batch, 256, 0, s>>>(T, dT, t_stride, P, dL, dstep, out);
   count_launches(1);
 }
 

@@ -6,6 +6,11 @@ Each file records the FP64 oracle flow of one configuration: per step the axis, 
 dimensions, ln c_n, the ln Z/N estimate, X^(n), the cut gaps and the leading Gram spectra
 (normalised by the largest eigenvalue). A flow whose cut splits a degenerate multiplet
 (gap < 1e-10) is cut-ambiguous from that step on; the file records the first such step.
+
+The deriv_* files record d(ln Z/N)/d beta and d(ln Z/N)/d h after every step with the isometries
+frozen (oracle.hotrg_ref.fixed_isometry_derivatives).
+
+    python tests/golden/make_golden.py [name ...]     # only the named files
 """
 import json
 import os
@@ -25,6 +30,12 @@ CONFIGS = {
     "flow_d4_b0.1497_h1e-6_D4_n8": dict(d=4, beta=0.1497, h=1e-6, Dcut=4, nsteps=8),
     # 2D, Dcut = 8, 40 steps to 2^40 sites
     "flow_d2_b0.3_h0_D8_n40": dict(d=2, beta=0.3, h=0.0, Dcut=8, nsteps=40),
+}
+
+DERIV_CONFIGS = {
+    # 4D, Dcut = 5, 8 steps: near the transition at h = 0, and with a field of 0.01
+    "deriv_d4_b0.1497_h0_D5_n8": dict(d=4, beta=0.1497, h=0.0, Dcut=5, nsteps=8),
+    "deriv_d4_b0.16_h0.01_D5_n8": dict(d=4, beta=0.16, h=0.01, Dcut=5, nsteps=8),
 }
 
 AMBIGUOUS_GAP = 1e-10
@@ -48,8 +59,27 @@ def flow_record(cfg):
                 steps=steps, source="oracle/hotrg_ref.py run(), FP64")
 
 
+def deriv_record(cfg):
+    f = R.run(**cfg)
+    gaps = [min(g.values()) for g in f.gaps if g]
+    db, dh = R.fixed_isometry_derivatives(**cfg)
+    return dict(config=cfg, lnz=[float(x) for x in f.lnz], dlnz_dbeta=[float(x) for x in db],
+                dlnz_dh=[float(x) for x in dh], min_cut_gap=float(min(gaps)),
+                source="oracle/hotrg_ref.py fixed_isometry_derivatives(), FP64, eps = 1e-3 Richardson")
+
+
 def main():
+    only = set(sys.argv[1:])
+    for name, cfg in DERIV_CONFIGS.items():
+        if only and name not in only:
+            continue
+        rec = deriv_record(cfg)
+        with open(os.path.join(HERE, name + ".json"), "w") as fh:
+            json.dump(rec, fh, indent=1)
+        print(name, rec["dlnz_dbeta"][-1], rec["dlnz_dh"][-1], "min gap", rec["min_cut_gap"])
     for name, cfg in CONFIGS.items():
+        if only and name not in only:
+            continue
         rec = flow_record(cfg)
         with open(os.path.join(HERE, name + ".json"), "w") as fh:
             json.dump(rec, fh, indent=1)

@@ -229,3 +229,84 @@ def test_planted_mistakes_are_caught(monkeypatch):
     Q2 = R.half_gram(Tr, 1, 3)
     wrong = np.einsum("ikab,jlab->ijkl", Q1, Q2).reshape(4, 4)
     assert not np.allclose(wrong, good, rtol=1e-6)
+
+
+# ------------------------------------------------------------------ derivatives (reading R9)
+@pytest.mark.parametrize("beta,h", [(0.7, 0.2), (0.3, 0.0), (1.1, -0.05)])
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 8])
+def test_dlnz_1d_matches_enumeration(beta, h, N):
+    """The differentiated transfer-matrix result against thermal averages by enumeration:
+    d(lnZ/N)/d beta = <sum s s'>/N + h <s>, d(lnZ/N)/d h = beta <s>."""
+    e, m = E.moments_bruteforce(beta, h, (N,))
+    db, dh = E.dlnz_1d(beta, h, N)
+    assert abs(db - (e + h * m)) < 1e-13
+    assert abs(dh - beta * m) < 1e-13
+
+
+@pytest.mark.parametrize("beta,h", [(0.7, 0.2), (0.3, 0.0)])
+def test_dlnz_1d_matches_difference_quotient_of_lnz_1d(beta, h):
+    N, eps = 2 ** 20, 1e-4
+    f = lambda b, hh: E.lnz_1d(b, hh, N) / N
+    db, dh = E.dlnz_1d(beta, h, N)
+    assert abs(db - (f(beta + eps, h) - f(beta - eps, h)) / (2 * eps)) < 1e-7
+    assert abs(dh - (f(beta, h + eps) - f(beta, h - eps)) / (2 * eps)) < 1e-7
+
+
+def test_moments_bruteforce_symmetry_and_difference_quotient():
+    """<s> = 0 at h = 0 (Z2 symmetry); the moments are the derivatives of lnz_bruteforce."""
+    L = (2, 2, 2)
+    e0, m0 = E.moments_bruteforce(0.3, 0.0, L)
+    assert abs(m0) < 1e-15 and e0 > 0
+    beta, h, eps, N = 0.3, 0.07, 1e-4, 8
+    e, m = E.moments_bruteforce(beta, h, L)
+    f = lambda b, hh: E.lnz_bruteforce(b, hh, L) / N
+    assert abs((f(beta + eps, h) - f(beta - eps, h)) / (2 * eps) - (e + h * m)) < 1e-7
+    assert abs((f(beta, h + eps) - f(beta, h - eps)) / (2 * eps) - beta * m) < 1e-7
+
+
+@pytest.mark.parametrize("beta,h", [(0.7, 0.2), (0.44, 0.0)])
+def test_fixed_isometry_derivatives_1d_match_transfer_matrix(beta, h):
+    """d = 1 has no transverse legs: every step is exact and after n steps the flow describes a
+    ring of 2^n sites."""
+    db, dh = R.fixed_isometry_derivatives(1, beta, h, 2, 12)
+    for n in range(13):
+        rb, rh = E.dlnz_1d(beta, h, 2 ** n)
+        assert abs(db[n] - rb) < 1e-10 * max(1.0, abs(rb))
+        assert abs(dh[n] - rh) < 1e-10 * max(1.0, abs(rh))
+
+
+@pytest.mark.parametrize("beta,h", [(0.4407, 0.05), (0.3, 0.0)])
+def test_fixed_isometry_derivatives_2d_lossless_match_enumeration(beta, h):
+    """Lossless steps (Dcut = 16) give the 2x2 and 4x4 periodic lattices; with square
+    orthogonal U the frozen-U derivative is the exact one."""
+    db, dh = R.fixed_isometry_derivatives(2, beta, h, 16, 4)
+    for n, L in ((2, (2, 2)), (4, (4, 4))):
+        e, m = E.moments_bruteforce(beta, h, L)
+        assert abs(db[n] - (e + h * m)) < 1e-10
+        assert abs(dh[n] - beta * m) < 1e-10
+
+
+def test_fixed_isometry_derivatives_4d_lossless_match_enumeration():
+    beta, h = 0.3, 0.01
+    db, dh = R.fixed_isometry_derivatives(4, beta, h, 16, 1)
+    e, m = E.moments_bruteforce(beta, h, (1, 1, 1, 2))
+    assert abs(db[1] - (e + h * m)) < 1e-10
+    assert abs(dh[1] - beta * m) < 1e-10
+
+
+def test_fixed_isometry_derivative_detects_a_dropped_field_term(monkeypatch):
+    """Planted mistake: a site weight that forgets the field must fail the enumeration pin."""
+    beta, h = 0.4407, 0.05
+    orig = R.site_weight
+    monkeypatch.setattr(R, "site_weight", lambda b, hh: orig(b, 0.0))
+    db, _ = R.fixed_isometry_derivatives(2, beta, h, 16, 2)
+    monkeypatch.setattr(R, "site_weight", orig)
+    e, m = E.moments_bruteforce(beta, h, (2, 2))
+    assert abs(db[2] - (e + h * m)) > 1e-4
+
+
+def test_fixed_isometries_reproduce_the_free_flow():
+    """Freezing U at the values the flow itself chose changes nothing at the same (beta, h)."""
+    f = R.run(4, 0.1497, 0.0, 3, 6)
+    g = R.run(4, 0.1497, 0.0, 3, 6, isometries=f.isometries)
+    assert f.lnz == g.lnz
