@@ -74,8 +74,13 @@ typedef struct hotrg_opts {
   int kblock;             /* split modes: K width of a pipeline stage, 32 or 64 (0 = 64) */
   int fold_group;         /* split modes: stages per accumulator fold, 1 or 2 (0 = 1): the tensor
                              cores' FP32 accumulator restarts every fold_group * kblock K */
-  int derivatives;        /* 1: also propagate d/d beta and d/d h of the flow with the isometries
-                             held fixed (forward-mode tangents, 4 extra squeezes per step) */
+  int derivatives;        /* also propagate d/d beta and d/d h of the flow (forward-mode tangents;
+                             each step adds two squeeze GEMMs over a doubled k range):
+                             0 none; 1 with the isometries of every step held fixed;
+                             2 exact derivative of the truncated flow, differentiating the
+                               isometries through the Gram eigendecomposition (first-order
+                               eigenvector perturbation; NaN where a cut splits a degenerate
+                               eigenvalue, where no derivative exists). EINVAL otherwise. */
   int graphs;             /* 1: capture a steady-state step (bond dimensions unchanged) once per
                              axis as a CUDA graph and replay it (default 1; off while timing and
                              on the legacy default stream, which cannot be captured) */
@@ -88,8 +93,9 @@ typedef struct hotrg_obs {
   double lnz_per_site;    /* ln Z_N / N estimate after the last step, N = 2^steps */
   double last_ln_c;       /* ln c_n of the last step */
   double x_indicator;     /* X^(n) of Eq. (x) along the last axis (1 for steps == 0) */
-  /* with opts.derivatives (NaN otherwise), derivatives of the ln Z_N / N estimate with the
-   * isometries of every step held fixed, and what they give (H = -sum s s' - h sum s):
+  /* with opts.derivatives (NaN otherwise), derivatives of the ln Z_N / N estimate (isometries
+   * held fixed, or differentiated, per opts.derivatives) and what they give
+   * (H = -sum s s' - h sum s):
    *   d(lnZ/N)/d beta = -<H>/N = d <s s'> + h <s>,   d(lnZ/N)/d h = beta <s>   */
   double dlnz_dbeta;
   double dlnz_dh;

@@ -393,6 +393,27 @@ def fixed_isometry_derivatives(d: int, beta: float, h: float, Dcut: int, nsteps:
     return out[0], out[1]
 
 
+def flow_derivatives(d: int, beta: float, h: float, Dcut: int, nsteps: int,
+                     eps: float = 1e-4) -> tuple[np.ndarray, np.ndarray]:
+    """d/d beta and d/d h of the ln Z_N / N estimate after every step 0..nsteps of the truncated
+    flow itself (isometries recomputed at every point), by central differences Richardson-
+    extrapolated from steps eps and eps/2. This is what differentiating the isometries through
+    the eigendecomposition computes; it differs from fixed_isometry_derivatives by terms of the
+    order of the truncation. It exists only where no cut splits a degenerate eigenvalue pair."""
+
+    def lnz(b, hh):
+        return np.array(run(d, b, hh, Dcut, nsteps).lnz)
+
+    def central(f, e):
+        return (f(e) - f(-e)) / (2.0 * e)
+
+    out = []
+    for f in (lambda e: lnz(beta + e, h), lambda e: lnz(beta, h + e)):
+        d1, d2 = central(f, eps), central(f, eps / 2)
+        out.append((4.0 * d2 - d1) / 3.0)
+    return out[0], out[1]
+
+
 def dims_schedule(d: int, Dcut: int, nsteps: int, order: list[int] | None = None) -> list[list[int]]:
     """Bond dimensions after each step under chi = min(D^2, Dcut) (reading R3)."""
     order = default_order(d) if order is None else order

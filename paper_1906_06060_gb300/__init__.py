@@ -22,6 +22,8 @@ from ._lib import HOTRG_BF16X3, HOTRG_BF16X4, HOTRG_BF16X6, HOTRG_FP64, HotrgErr
 __all__ = ["HOTRG", "HotrgError", "gemm_split", "workspace_bytes", "PRECISIONS"]
 
 PRECISIONS = {"fp64": HOTRG_FP64, "bf16x3": HOTRG_BF16X3, "bf16x4": HOTRG_BF16X4, "bf16x6": HOTRG_BF16X6}
+# derivative modes: isometries held fixed, or differentiated through the eigendecomposition
+_DERIV = {"none": 0, "fixed": 1, "eig": 2}
 
 
 def _torch():
@@ -43,14 +45,14 @@ def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=
     o.kblock = int(kblock)
     o.graphs = 1 if graphs else 0
     o.fold_group = int(fold_group)
-    o.derivatives = 1 if derivatives else 0
+    o.derivatives = _DERIV[derivatives] if isinstance(derivatives, str) else int(derivatives)
     o.max_steps = int(max_steps)
     o.wait_timeout_s = float(wait_timeout_s)
     return o
 
 
 def workspace_bytes(d: int, Dcut: int, precision="fp64", batch: int = 1, fp64_steps: int = 2,
-                    max_steps: int = 64, x6_steps: int = 0, derivatives: bool = False) -> int:
+                    max_steps: int = 64, x6_steps: int = 0, derivatives=False) -> int:
     o = _opts(precision, batch, fp64_steps, max_steps, x6_steps=x6_steps, derivatives=derivatives)
     n = c_size_t(0)
     check(_lib.load().hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
@@ -63,11 +65,14 @@ class HOTRG:
     beta, h: scalars, or sequences of equal length `batch` for a temperature/field scan.
     precision: "fp64", "bf16x3", "bf16x4" or "bf16x6" (tensor-core squeeze with split operands);
     fp64_steps / x6_steps: precision schedule of the split modes (see include/hotrg.h).
+    derivatives: False / "none", True / "fixed" (isometries held fixed) or "eig" (exact derivative
+    of the truncated flow, isometries differentiated through the eigendecomposition); the
+    observables then carry d(lnZ/N)/d beta, d(lnZ/N)/d h, the internal energy and magnetisation.
     """
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
                  max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0,
-                 kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives: bool = False):
+                 kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives=False):
         torch = _torch()
         lib = _lib.load()
         betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))

@@ -166,7 +166,89 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict
   }
 }
 
+// First-order perturbation of the kept eigenvectors (one CTA per instance). work holds the
+// Jacobi result of launch_eig: A (diagonal = eigenvalues, unsorted) and V (columns = eigenvectors).
+// Shared memory: lambda[n], perm[n], sign[chi], Z = dG V_kept [n][chi], W [(n - chi)][chi].
+__global__ void __launch_bounds__(256) k_eig_tangent(const double* __restrict__ work, const double* __restrict__ U,
+                                                     long long u_stride, const double* __restrict__ dG,
+                                                     long long g_stride, int n, int chi,
+                                                     double* __restrict__ dU) {
+  extern __shared__ double sm[];
+  work += (long long)blockIdx.x * 2 * n * n;
+  U += (long long)blockIdx.x * u_stride;
+  dU += (long long)blockIdx.x * u_stride;
+  dG += (long long)blockIdx.x * g_stride;
+  const double* A = work;
+  const double* V = work + (long long)n * n;
+  double* lam = sm;                                   // [n]
+  double* sgn = lam + n;                              // [chi]
+  double* Z = sgn + kMaxBond;                         // [n][chi]
+  double* W = Z + (long long)n * chi;                 // [n - chi][chi]
+  int* perm = reinterpret_cast<int*>(W + (long long)(n - chi) * chi);  // [n]
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += blockDim.x) lam[i] = A[(long long)i * n + i];
+  __syncthreads();
+  // the same descending, index-stable order as launch_eig
+  for (int i = tid; i < n; i += blockDim.x) {
+    const double li = lam[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double lj = lam[j];
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    perm[rank] = i;
+  }
+  __syncthreads();
+  // sign convention of U_k relative to column perm[k] of V: U_k = sign_k V[:, perm[k]]
+  const int warp = tid / 32, lane = tid % 32;
+  for (int k = warp; k < chi; k += blockDim.x / 32) {
+    double dot = 0.0;
+    for (int r = lane; r < n; r += 32) dot += U[(long long)k * n + r] * V[(long long)r * n + perm[k]];
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    if (lane == 0) sgn[k] = dot < 0 ? -1.0 : 1.0;
+  }
+  // Z[r][k] = sum_c dG[r][c] V[c][perm[k]]
+  for (int e = tid; e < n * chi; e += blockDim.x) {
+    const int r = e / chi, k = e % chi;
+    const int col = perm[k];
+    double acc = 0.0;
+    for (int c2 = 0; c2 < n; ++c2) acc = fma(dG[(long long)r * n + c2], V[(long long)c2 * n + col], acc);
+    Z[e] = acc;
+  }
+  __syncthreads();
+  // W[j - chi][k] = (V_j^T Z_k) / (lambda_k - lambda_j)
+  for (int e = tid; e < (n - chi) * chi; e += blockDim.x) {
+    const int jj = e / chi, k = e % chi;
+    const int colj = perm[chi + jj];
+    double acc = 0.0;
+    for (int r = 0; r < n; ++r) acc = fma(V[(long long)r * n + colj], Z[r * chi + k], acc);
+    const double gap = lam[perm[k]] - lam[colj];
+    W[e] = gap != 0.0 ? acc / gap : nan("");
+  }
+  __syncthreads();
+  // dU[k][r] = sign_k sum_j V[r][perm[j]] W[j][k]
+  for (int e = tid; e < chi * n; e += blockDim.x) {
+    const int k = e / n, r = e % n;
+    double acc = 0.0;
+    for (int jj = 0; jj < n - chi; ++jj) acc = fma(V[(long long)r * n + perm[chi + jj]], W[jj * chi + k], acc);
+    dU[(long long)k * n + r] = sgn[k] * acc;
+  }
+}
+
 }  // namespace
+
+void launch_eig_tangent(const double* work, const double* U, long long u_stride, const double* dG,
+                        long long g_stride, int batch, int n, int chi, double* dU, cudaStream_t s) {
+  const size_t smem = sizeof(double) * ((size_t)n + kMaxBond + (size_t)n * chi + (size_t)(n - chi) * chi) +
+                      sizeof(int) * (size_t)n;
+  k_eig_tangent<<<batch, 256, smem, s>>>(work, U, u_stride, dG, g_stride, n, chi, dU);
+  count_launches(1);
+}
+
+void prepare_eig_attributes() {
+  const int big = (int)(sizeof(double) * (kMaxGram + kMaxBond + 2 * kMaxGram * kMaxBond) + sizeof(int) * kMaxGram);
+  cudaFuncSetAttribute(k_eig_tangent, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
 
 void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o, double* U,
                 long long u_stride, double* work, int* status, cudaStream_t s) {

@@ -22,11 +22,15 @@ struct LegInfo {
   long long stride[kMaxLegs];
 };
 
-__global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ T, long long t_stride, LegInfo li,
+// Rows of the output tile come from TA, columns from TB (both T for the Gram itself; the tangent
+// dT and T for its derivative).
+__global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ TA, const double* __restrict__ TB,
+                                                   long long t_stride, LegInfo li,
                                                    long long S1, long long S2, int Da, int nr,
                                                    long long K, int ntile, int nsplit,
                                                    double* __restrict__ partial) {
-  T += (long long)blockIdx.z * t_stride;
+  TA += (long long)blockIdx.z * t_stride;
+  TB += (long long)blockIdx.z * t_stride;
   partial += (long long)blockIdx.z * nsplit * nr * nr;
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
@@ -71,8 +75,8 @@ __global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ T,
       const int kk = e % GK, rr = e / GK;
       const long long co = coloff[kk];
       const long long ra = rowoffA[rr], rb = rowoffB[rr];
-      As[kk][rr] = (co >= 0 && ra >= 0) ? T[ra + co] : 0.0;
-      Bs[kk][rr] = (co >= 0 && rb >= 0) ? T[rb + co] : 0.0;
+      As[kk][rr] = (co >= 0 && ra >= 0) ? TA[ra + co] : 0.0;
+      Bs[kk][rr] = (co >= 0 && rb >= 0) ? TB[rb + co] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -132,6 +136,33 @@ __global__ void k_gram_combine(const double* __restrict__ Q1, const double* __re
   G[e] = s;
 }
 
+// Tangent of G from the tangents of the half-Grams: with H1 = Q1(dT, T) and H2 = Q2(dT, T)
+// (rows from dT), dQ = H + H^T and dG = sum dQ1 Q2 + Q1 dQ2.
+__global__ void k_gram_combine_tangent(const double* __restrict__ Q1, const double* __restrict__ Q2,
+                                       const double* __restrict__ H1, const double* __restrict__ H2,
+                                       long long q_stride, int Db, int Da, double* __restrict__ dG,
+                                       long long g_stride) {
+  const int n = Db * Db, nr = Db * Da;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const long long qo = (long long)blockIdx.y * q_stride;
+  Q1 += qo; Q2 += qo; H1 += qo; H2 += qo;
+  dG += (long long)blockIdx.y * g_stride;
+  const int row = e / n, col = e % n;
+  const int b1 = row / Db, b2 = row % Db, c1 = col / Db, c2 = col % Db;
+  double s = 0.0;
+  for (int al = 0; al < Da; ++al)
+    for (int at = 0; at < Da; ++at) {
+      const long long i1 = (long long)(b1 * Da + al) * nr + c1 * Da + at;   // Q1[(b1,al)][(c1,at)]
+      const long long t1 = (long long)(c1 * Da + at) * nr + b1 * Da + al;   // transposed entry
+      const long long i2 = (long long)(b2 * Da + al) * nr + c2 * Da + at;
+      const long long t2 = (long long)(c2 * Da + at) * nr + b2 * Da + al;
+      s = fma(H1[i1] + H1[t1], Q2[i2], s);
+      s = fma(Q1[i1], H2[i2] + H2[t2], s);
+    }
+  dG[e] = s;
+}
+
 }  // namespace
 
 int gram_nsplit() { return kGramCTAs; }
@@ -155,7 +186,7 @@ size_t gram_partial_doubles(int nr_max, int batch) {
 }
 
 void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, int l1, int l2, double* partial,
-                      double* Q, long long q_stride, cudaStream_t s) {
+                      double* Q, long long q_stride, cudaStream_t s, const double* TA) {
   const int d = g.d;
   auto leg_dim = [&](int l) { return g.D[l % d]; };
   auto leg_stride = [&](int l) { return l < d ? g.Sn[l] * g.P : g.Sn[l - d]; };
@@ -174,8 +205,8 @@ void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, in
   const int tiles = ntile * ntile;
   const int nsplit = nsplit_for(nr, K, batch);
   dim3 grid(tiles, nsplit, batch);
-  k_half_gram<<<grid, 256, 0, s>>>(T, t_stride, li, leg_stride(l1), leg_stride(l2), Da, nr, K, ntile, nsplit,
-                                    partial);
+  k_half_gram<<<grid, 256, 0, s>>>(TA ? TA : T, T, t_stride, li, leg_stride(l1), leg_stride(l2), Da, nr, K, ntile,
+                                    nsplit, partial);
   count_launches(1);
   const int nn = nr * nr;
   k_reduce_splits<<<dim3((nn + 255) / 256, batch), 256, 0, s>>>(partial, nsplit, nn, Q, q_stride);
@@ -186,6 +217,15 @@ void launch_gram_combine(const double* Q1, const double* Q2, long long q_stride,
                          double* G, long long g_stride, cudaStream_t s) {
   const int n = Db * Db;
   k_gram_combine<<<dim3((n * n + 255) / 256, batch), 256, 0, s>>>(Q1, Q2, q_stride, Db, Da, G, g_stride);
+  count_launches(1);
+}
+
+void launch_gram_combine_tangent(const double* Q1, const double* Q2, const double* H1, const double* H2,
+                                 long long q_stride, int batch, int Db, int Da, double* dG, long long g_stride,
+                                 cudaStream_t s) {
+  const int n = Db * Db;
+  k_gram_combine_tangent<<<dim3((n * n + 255) / 256, batch), 256, 0, s>>>(Q1, Q2, H1, H2, q_stride, Db, Da, dG,
+                                                                          g_stride);
   count_launches(1);
 }
 

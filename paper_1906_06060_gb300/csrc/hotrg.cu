@@ -50,11 +50,18 @@ struct hotrg_ctx {
   double *G = nullptr, *U = nullptr, *ework = nullptr;
   int* status = nullptr;
   int* dstep = nullptr;       // device-side step counter (steps done)
-  // tangents d/d beta (0) and d/d h (1) of the flow with the isometries held fixed
+  // tangents d/d beta (0) and d/d h (1) of the flow: deriv_mode 1 holds the isometries fixed,
+  // 2 also differentiates them through the eigendecomposition
   bool deriv = false;
+  int deriv_mode = 0;
   double *dT = nullptr;       // [2][batch][Pmax^2] tangents of the normalised tensors
   double *D1 = nullptr, *D2 = nullptr;  // tangent squeeze outputs (one instance at a time)
   double *dL = nullptr, *dlnc = nullptr, *dout = nullptr;  // [2][batch]
+  double *dU = nullptr;       // [2][batch][u_stride] isometry tangents (mode 2)
+  double *H1 = nullptr, *H2 = nullptr, *dG = nullptr;  // half-Gram and Gram tangents (mode 2)
+  long long dg_stride = 0;
+  void *Tt2 = nullptr, *dX1[2] = {nullptr, nullptr}, *dX2 = nullptr, *dO = nullptr;  // tangent squeeze scratch
+  void *dR1 = nullptr, *dR2 = nullptr;
   long long q_stride = 0, g_stride = 0, u_stride = 0;  // per-instance strides (doubles)
   void *Tt = nullptr, *Bt = nullptr, *X1 = nullptr, *X2 = nullptr, *Y = nullptr, *O = nullptr;
   void *R1 = nullptr, *R2 = nullptr;
@@ -272,13 +279,31 @@ size_t carve(hotrg_ctx* c, char* base) {
     c->dlnc = k.take<double>(sizeof(double) * 2 * c->batch);
     c->dout = k.take<double>(sizeof(double) * 2 * c->batch);
   }
+  if (c->deriv_mode == 2) {
+    c->dU = k.take<double>(sizeof(double) * 2 * c->u_stride * c->batch);
+    c->H1 = k.take<double>(sizeof(double) * c->q_stride * c->batch);
+    c->H2 = k.take<double>(sizeof(double) * c->q_stride * c->batch);
+    c->dg_stride = (long long)nmax * nmax;
+    c->dG = k.take<double>(sizeof(double) * c->dg_stride * c->batch);
+  }
+  // with tangents the operands hold three column blocks per row (see squeeze)
+  const size_t blk = c->deriv ? 3 : 1;
   c->sz_Tt = n.Tt; c->Tt = k.take<char>(n.Tt);
-  c->sz_Bt = n.Bt; c->Bt = k.take<char>(n.Bt);
+  c->sz_Bt = n.Bt * blk; c->Bt = k.take<char>(n.Bt * blk);
   c->sz_X = n.X;   c->X1 = k.take<char>(n.X); c->X2 = k.take<char>(n.X);
-  c->sz_Y = n.Y;   c->Y = k.take<char>(n.Y);
+  c->sz_Y = n.Y * blk; c->Y = k.take<char>(n.Y * blk);
   c->sz_O = n.O;   c->O = k.take<char>(n.O);
   c->sz_R1 = n.R1; c->R1 = k.take<char>(n.R1 ? n.R1 : 256);
   c->sz_R2 = n.R2; c->R2 = k.take<char>(n.R2 ? n.R2 : 256);
+  if (c->deriv) {
+    c->Tt2 = k.take<char>(n.Tt);
+    c->dX1[0] = k.take<char>(n.X);
+    c->dX1[1] = k.take<char>(n.X);
+    c->dX2 = k.take<char>(n.X);
+    c->dO = k.take<char>(n.O);
+    c->dR1 = k.take<char>(n.R1 ? n.R1 : 256);
+    c->dR2 = k.take<char>(n.R2 ? n.R2 : 256);
+  }
   return k.off;
 }
 
@@ -323,9 +348,11 @@ struct Ax {
 };
 
 // Contract (m_b, n_b) with U_b into k'_b; output dense row-major unless out_strides given.
+// With in2 (laid out like in), the same contraction of in2 with U2 is added.
 template <class Tin, class Tout>
 void contract_axes(std::vector<Ax>& axes, const Tin* in, Tout* out, int b, int chi_b, const double* Ub,
-                   const long long* final_out_stride, long long out_base, cudaStream_t s) {
+                   const long long* final_out_stride, long long out_base, cudaStream_t s,
+                   const Tin* in2 = nullptr, const double* U2 = nullptr) {
   int im = -1, in_ = -1;
   for (int i = 0; i < (int)axes.size(); ++i) {
     if (axes[i].kind == 0 && axes[i].slot == b) im = i;
@@ -365,7 +392,7 @@ void contract_axes(std::vector<Ax>& axes, const Tin* in, Tout* out, int b, int c
     ++rest.ndim;
   }
   launch_pair_contract_all<Tin, Tout>(in, out, rest, axes[im].dim, axes[in_].dim, axes[im].stride,
-                                      axes[in_].stride, v.out_stride[kaxis], Ub, chi_b, 0, out_base, s);
+                                      axes[in_].stride, v.out_stride[kaxis], Ub, chi_b, 0, out_base, s, in2, U2);
   // new axes describe the dense output (only meaningful when not final)
   st = 1;
   for (int i = v.ndim - 1; i >= 0; --i) {
@@ -390,6 +417,21 @@ void final_strides(const std::vector<Ax>& axes, int skip_m_slot, int kslot, cons
   }
 }
 
+// d = 1: no transverse axes, the GEMM output O[m][n] is the new tensor Tnext[u'][p'].
+template <class TC>
+void copy_final(const std::vector<Ax>& axes, const TC* in, double* out, const Geom& gn, cudaStream_t s) {
+  long long fs[kMaxAxes];
+  final_strides(axes, -2, -1, gn, -1, fs);
+  View v;
+  v.ndim = (int)axes.size();
+  for (int i = 0; i < v.ndim; ++i) {
+    v.shape[i] = axes[i].dim;
+    v.in_stride[i] = axes[i].stride;
+    v.out_stride[i] = fs[i];
+  }
+  launch_pair_contract<TC, double>(in, out, v, -1, 1, 1, 0, 0, nullptr, 1, 0, 0, s);
+}
+
 template <class TC>
 struct Ops;  // operand element types of a path
 
@@ -402,40 +444,81 @@ struct Ops<float> {
   using Op = __nv_bfloat16;
 };
 
+// Tangent inputs of a squeeze of T with itself: for each of n parameters the tangent dT (same
+// layout as T), the output tangent (new geometry, before normalisation) and the isometry
+// tangents dU (null: isometries held fixed).
+struct Tangents {
+  int n = 0;
+  const double* dT[2] = {nullptr, nullptr};
+  double* dout[2] = {nullptr, nullptr};
+  const double* dU[2] = {nullptr, nullptr};
+};
+
 // planes: 0 = FP64 path (TC = double), 2 / 3 = tensor-core path (TC = float) with 3 / 6 passes.
 template <class TC>
 // Coarse-grained tensor of the pair (T1 lower site, T2 upper site along a) into `out` (new
-// geometry gn): T1 feeds the A operand, T2 the B operand. The flow uses T1 = T2 = T; the tangent
-// of a step uses (dT, T) and (T, dT).
+// geometry gn): T1 feeds the A operand, T2 the B operand. With tangents (T1 = T2 = T), also
+//   dT' = S(dT, T) + S(T, dT) + sum over the six places of an isometry of S with dU there,
+// computed as a dual-number pass: every producer and epilogue stage propagates (x, dx), and the
+// O(D^15) contraction of a tangent is one GEMM over the concatenated k range,
+//   dO = [dY | Y] . [Bt | dBt]^T,
+// with the operand blocks laid out side by side in one row: Y' = [dY_0 | Y | dY_1] and
+// Bt' = [dBt_1 | Bt | dBt_0] (row stride 3 ldk), so that [dY_0 | Y] pairs with [Bt | dBt_0] and
+// [Y | dY_1] with [dBt_1 | Bt].
 int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const double* U, const Geom& g,
-            const Geom& gn, int a, const int* chi, const int* trans, int nt, int planes, int npass) {
+            const Geom& gn, int a, const int* chi, const int* trans, int nt, int planes, int npass,
+            const Tangents& tg = Tangents()) {
   using Op = typename Ops<TC>::Op;
   constexpr bool mixed = std::is_same<TC, float>::value;
   cudaStream_t s = c->stream;
   const long long P = g.P;
   const long long ldk = mixed ? round_up(P, 64) : P;
+  const int nblk = tg.n ? 3 : 1;
+  const long long ld = nblk * ldk;
+  const int fwd_blk = tg.n ? 1 : 0;
   const int c3 = nt ? trans[nt - 1] : -1;
   const int chi3 = c3 >= 0 ? chi[c3] : 1;
-  auto Ub = [&](int b) { return U + (long long)b * kMaxBond * kMaxGram; };
+  auto Ub = [&](const double* base, int b) { return base + (long long)b * kMaxBond * kMaxGram; };
   // bounds of this step's buffers against the plan
   StepNeeds need = needs_for(c->d, g.D, a, c->Dcut, planes);
-  if (need.Tt > c->sz_Tt || need.Bt > c->sz_Bt || need.X > c->sz_X || need.Y > c->sz_Y ||
+  if (need.Tt > c->sz_Tt || need.Bt * nblk > c->sz_Bt || need.X > c->sz_X || need.Y * nblk > c->sz_Y ||
       need.O > c->sz_O || need.R1 > c->sz_R1 || need.R2 > c->sz_R2)
     return HOTRG_ENOMEM;
+  if (tg.n && (!c->Tt2 || !c->dO || tg.n > 2)) return HOTRG_ESTATE;
   const int nparts = mixed ? planes : 1;
-  // B operand
+  const long long bt_plane = (long long)chi3 * P * ld, y_plane = P * ld;
+  auto blocks = [&](void* base, long long plane_elems, int blk) {
+    Planes<Op> pl;
+    pl.nparts = nparts;
+    for (int k = 0; k < 3; ++k)
+      pl.p[k] = static_cast<Op*>(base) + (size_t)(k < nparts ? k : 0) * plane_elems + blk * ldk;
+    return pl;
+  };
+  // tangent p: A operand block, B operand block written by its build, and the GEMM's first blocks
+  auto dy_blk = [](int p) { return p == 0 ? 0 : 2; };
+  auto dbt_blk = [](int p) { return p == 0 ? 2 : 0; };
+  auto gemm_a_blk = [](int p) { return p == 0 ? 0 : 1; };
+  auto gemm_b_blk = [](int p) { return p == 0 ? 1 : 0; };
+  // B operand(s)
   PhaseScope* ops_scope = new PhaseScope(c, PH_OPERANDS);
+  if (tg.n && mixed && ldk != P) {
+    // the concatenated k range runs over the zero padding between blocks
+    cudaMemsetAsync(c->Bt, 0, sizeof(Op) * nparts * bt_plane, s);
+    cudaMemsetAsync(c->Y, 0, sizeof(Op) * nparts * y_plane, s);
+  }
   TC* Tt = static_cast<TC*>(c->Tt);
   launch_transpose<TC>(T2, Tt, P, s);
-  Planes<Op> Bt;
-  Bt.nparts = nparts;
-  for (int k = 0; k < 3; ++k) Bt.p[k] = static_cast<Op*>(c->Bt) + (size_t)(k < nparts ? k : 0) * chi3 * P * ldk;
-  launch_build_bt<TC, Op>(Tt, Bt, ldk, g, c3, c3 >= 0 ? Ub(c3) : nullptr, chi3, s);
+  launch_build_bt<TC, Op>(Tt, blocks(c->Bt, bt_plane, fwd_blk), ld, g, c3, c3 >= 0 ? Ub(U, c3) : nullptr, chi3, s);
+  for (int p = 0; p < tg.n; ++p) {
+    TC* dTt = static_cast<TC*>(c->Tt2);
+    launch_transpose<TC>(tg.dT[p], dTt, P, s);
+    const bool two = tg.dU[p] && c3 >= 0;
+    launch_build_bt<TC, Op>(dTt, blocks(c->Bt, bt_plane, dbt_blk(p)), ld, g, c3, c3 >= 0 ? Ub(U, c3) : nullptr,
+                            chi3, s, two ? Tt : nullptr, two ? Ub(tg.dU[p], c3) : nullptr);
+  }
   delete ops_scope;
-  Planes<Op> Y;
-  Y.nparts = nparts;
-  for (int k = 0; k < 3; ++k) Y.p[k] = static_cast<Op*>(c->Y) + (size_t)(k < nparts ? k : 0) * P * ldk;
   TC* O = static_cast<TC*>(c->O);
+  TC* dO = static_cast<TC*>(c->dO);
   const long long ldO = (long long)chi3 * P;
   // chunks over the other transverse axes
   const int no = nt > 0 ? nt - 1 : 0;
@@ -443,6 +526,25 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   long long nchunks = 1;
   for (int i = 0; i < no; ++i) nchunks *= chi[trans[i]];
   int prev_k0 = -1;
+  auto gemm = [&](int ablk, int bblk, TC* C, long long K) -> int {
+    PhaseScope gemm_scope(c, PH_GEMM);
+    if constexpr (mixed) {
+      const int rc = launch_gemm_split(blocks(c->Y, y_plane, ablk), ld, blocks(c->Bt, bt_plane, bblk), ld,
+                                       reinterpret_cast<float*>(C), ldO, P, ldO, K, npass, c->status, c->timeout_s,
+                                       s, c->kblock, c->group_m, fold_group_for(c, npass));
+      if (rc) return rc;
+      if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * K * npass;
+    } else {
+      launch_gemm_f64(blocks(c->Y, y_plane, ablk).p[0], ld, blocks(c->Bt, bt_plane, bblk).p[0], ld, C, ldO, P, ldO,
+                      K, s);
+      if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * K;
+    }
+    if (c->timing) {
+      c->t_gemm_flops += 2.0 * P * (double)ldO * K;
+      ++c->t_gemm_launches;
+    }
+    return HOTRG_OK;
+  };
   for (long long ch = 0; ch < nchunks; ++ch) {
     long long r = ch;
     for (int i = no - 1; i >= 0; --i) {
@@ -452,76 +554,100 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
     // producer: mode products on the unprimed legs of the other transverse axes
     ops_scope = new PhaseScope(c, PH_OPERANDS);
     if (no == 0) {
-      launch_build_y<double, Op>(T1, Y, ldk, g, a, s);
+      launch_build_y<double, Op>(T1, blocks(c->Y, y_plane, fwd_blk), ld, g, a, s);
+      for (int p = 0; p < tg.n; ++p) launch_build_y<double, Op>(tg.dT[p], blocks(c->Y, y_plane, dy_blk(p)), ld, g, a, s);
     } else {
       TC* X1 = static_cast<TC*>(c->X1);
       TC* X2 = static_cast<TC*>(c->X2);
+      const int b0 = trans[0];
       if (kcnt[0] != prev_k0) {
-        launch_mode_unprimed<double, TC>(T1, X1, g, trans[0], Ub(trans[0]), kcnt[0], s);
+        launch_mode_unprimed<double, TC>(T1, X1, g, b0, Ub(U, b0), kcnt[0], s);
+        for (int p = 0; p < tg.n; ++p)
+          launch_mode_unprimed<double, TC>(tg.dT[p], static_cast<TC*>(c->dX1[p]), g, b0, Ub(U, b0), kcnt[0], s,
+                                           tg.dU[p] ? T1 : nullptr, tg.dU[p] ? Ub(tg.dU[p], b0) : nullptr);
         prev_k0 = kcnt[0];
       }
       const TC* X = X1;
       if (no >= 2) {
-        launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(trans[1]), kcnt[1], s);
+        launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(U, trans[1]), kcnt[1], s);
         X = X2;
       }
-      launch_build_y<TC, Op>(X, Y, ldk, g, a, s);
+      launch_build_y<TC, Op>(X, blocks(c->Y, y_plane, fwd_blk), ld, g, a, s);
+      for (int p = 0; p < tg.n; ++p) {
+        const TC* dX = static_cast<TC*>(c->dX1[p]);
+        if (no >= 2) {
+          TC* dX2 = static_cast<TC*>(c->dX2);
+          launch_mode_unprimed<TC, TC>(dX, dX2, g, trans[1], Ub(U, trans[1]), kcnt[1], s,
+                                       tg.dU[p] ? X1 : nullptr, tg.dU[p] ? Ub(tg.dU[p], trans[1]) : nullptr);
+          dX = dX2;
+        }
+        launch_build_y<TC, Op>(dX, blocks(c->Y, y_plane, dy_blk(p)), ld, g, a, s);
+      }
     }
     delete ops_scope;
     // the O(D^15) GEMM
     {
-      PhaseScope gemm_scope(c, PH_GEMM);
-      if constexpr (mixed) {
-        const int rc = launch_gemm_split(Y, ldk, Bt, ldk, reinterpret_cast<float*>(O), ldO, P, ldO, P,
-                                         npass, c->status, c->timeout_s, s, c->kblock, c->group_m,
-                                         fold_group_for(c, npass));
-        c->last_gemm.M = P;
-        c->last_gemm.N = ldO;
-        c->last_gemm.K = P;
-        c->last_gemm.ldk = ldk;
-        c->last_gemm.npass = npass;
-        c->last_gemm.nparts = planes;
-        if (rc) return rc;
-        if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * P * npass;
-      } else {
-        launch_gemm_f64(Y.p[0], ldk, Bt.p[0], ldk, O, ldO, P, ldO, P, s);
-        if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * P;
-      }
-      if (c->timing) {
-        c->t_gemm_flops += 2.0 * P * (double)ldO * P;
-        ++c->t_gemm_launches;
-      }
+      const int rc = gemm(fwd_blk, fwd_blk, O, P);
+      if (rc) return rc;
+      c->last_gemm.M = P;
+      c->last_gemm.N = ldO;
+      c->last_gemm.K = P;
+      c->last_gemm.ldk = ld;
+      c->last_gemm.npass = npass;
+      c->last_gemm.nparts = planes;
     }
     // epilogue: O axes [m_0..m_{d-1}, j, n_0..n_{d-1}]
-    PhaseScope epi_scope(c, PH_EPILOGUE);
-    std::vector<Ax> axes;
-    for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b] * ldO, 0, b});
-    axes.push_back({chi3, P, 1, -1});
-    for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
+    std::vector<Ax> hist[kMaxD];  // axes of the input of each contraction of the chain
+    TC* bufs[2] = {static_cast<TC*>(c->R1), static_cast<TC*>(c->R2)};
+    TC* dbufs[2] = {static_cast<TC*>(c->dR1), static_cast<TC*>(c->dR2)};
     long long out_base = 0;
     for (int i = 0; i < no; ++i) out_base += (long long)kcnt[i] * gn.Sn[trans[i]] * gn.P;
-    const TC* cur = O;
-    TC* bufs[2] = {static_cast<TC*>(c->R1), static_cast<TC*>(c->R2)};
-    for (int i = 0; i < no; ++i) {
-      contract_axes<TC, TC>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(trans[i]), nullptr, 0, s);
-      cur = bufs[i];
-    }
-    long long fs[kMaxAxes];
-    if (c3 >= 0) {
-      // final axes after contracting c3 (m_c3 removed, n_c3 -> k'_c3)
-      final_strides(axes, c3, c3, gn, c3, fs);
-      contract_axes<TC, double>(axes, cur, out, c3, chi3, Ub(c3), fs, out_base, s);
-    } else {
-      // d = 1: plain copy O[m][n] -> Tnext[u'][p']
-      final_strides(axes, -2, -1, gn, -1, fs);
-      View v;
-      v.ndim = (int)axes.size();
-      for (int i = 0; i < v.ndim; ++i) {
-        v.shape[i] = axes[i].dim;
-        v.in_stride[i] = axes[i].stride;
-        v.out_stride[i] = fs[i];
+    {
+      PhaseScope epi_scope(c, PH_EPILOGUE);
+      std::vector<Ax> axes;
+      for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b] * ldO, 0, b});
+      axes.push_back({chi3, P, 1, -1});
+      for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
+      const TC* cur = O;
+      for (int i = 0; i < no; ++i) {
+        hist[i] = axes;
+        contract_axes<TC, TC>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(U, trans[i]), nullptr, 0, s);
+        cur = bufs[i];
       }
-      launch_pair_contract<TC, double>(cur, out, v, -1, 1, 1, 0, 0, nullptr, 1, 0, 0, s);
+      hist[no] = axes;
+      long long fs[kMaxAxes];
+      if (c3 >= 0) {
+        // final axes after contracting c3 (m_c3 removed, n_c3 -> k'_c3)
+        final_strides(axes, c3, c3, gn, c3, fs);
+        contract_axes<TC, double>(axes, cur, out, c3, chi3, Ub(U, c3), fs, out_base, s);
+      } else {
+        copy_final<TC>(axes, cur, out, gn, s);
+      }
+    }
+    // tangents: dO by one GEMM over the concatenated k range, then the epilogue chain in
+    // dual numbers (dR' = C_U(dR) + C_dU(R))
+    for (int p = 0; p < tg.n; ++p) {
+      const int rc = gemm(gemm_a_blk(p), gemm_b_blk(p), dO, ldk + P);
+      if (rc) return rc;
+      PhaseScope epi_scope(c, PH_EPILOGUE);
+      const TC* cur = dO;
+      const TC* curF = O;
+      for (int i = 0; i < no; ++i) {
+        std::vector<Ax> ax = hist[i];
+        contract_axes<TC, TC>(ax, cur, dbufs[i], trans[i], chi[trans[i]], Ub(U, trans[i]), nullptr, 0, s,
+                              tg.dU[p] ? curF : nullptr, tg.dU[p] ? Ub(tg.dU[p], trans[i]) : nullptr);
+        cur = dbufs[i];
+        curF = bufs[i];
+      }
+      std::vector<Ax> ax = hist[no];
+      long long fs[kMaxAxes];
+      if (c3 >= 0) {
+        final_strides(ax, c3, c3, gn, c3, fs);
+        contract_axes<TC, double>(ax, cur, tg.dout[p], c3, chi3, Ub(U, c3), fs, out_base, s,
+                                  tg.dU[p] ? curF : nullptr, tg.dU[p] ? Ub(tg.dU[p], c3) : nullptr);
+      } else {
+        copy_final<TC>(ax, cur, tg.dout[p], gn, s);
+      }
     }
   }
   return HOTRG_OK;
@@ -552,6 +678,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   if (!opt) opt = &def;
   if (opt->batch < 1 || opt->max_steps < 1 || opt->max_steps > 64) return HOTRG_EINVAL;
   if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X4) return HOTRG_EINVAL;
+  if (opt->derivatives < 0 || opt->derivatives > 2) return HOTRG_EINVAL;
   hotrg_ctx c;
   c.d = d;
   c.Dcut = Dcut;
@@ -561,6 +688,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   c.x6_steps = opt->x6_steps;
   c.max_steps = opt->max_steps;
   c.deriv = opt->derivatives != 0;
+  c.deriv_mode = opt->derivatives;
   *bytes = carve(&c, nullptr);
   return HOTRG_OK;
 }
@@ -573,6 +701,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   if (opt->kblock != 0 && opt->kblock != 32 && opt->kblock != 64) return HOTRG_EINVAL;
   if (opt->fold_group < 0) return HOTRG_EINVAL;
   if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X4) return HOTRG_EINVAL;
+  if (opt->derivatives < 0 || opt->derivatives > 2) return HOTRG_EINVAL;
   std::vector<double> vb(opt->batch), vh(opt->batch);
   for (int i = 0; i < opt->batch; ++i) {
     vb[i] = opt->beta ? opt->beta[i] : beta;
@@ -586,6 +715,8 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
     return HOTRG_EDEVICE;
   }
   if (!(prop.major == 10 && prop.minor == 3)) return HOTRG_EDEVICE;
+  prepare_kernel_attributes();
+  prepare_eig_attributes();
   hotrg_ctx* c = new hotrg_ctx();
   c->d = d;
   c->Dcut = Dcut;
@@ -599,6 +730,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->fold_group = opt->fold_group;
   c->graphs = opt->graphs != 0;
   c->deriv = opt->derivatives != 0;
+  c->deriv_mode = opt->derivatives;
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
@@ -687,17 +819,34 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
       EigOut eo{c->spec_log + (long long)b * kSpecCap, c->spec_stride, (long long)c->d * kSpecCap, c->dstep,
                 c->max_steps};
       launch_eig(Gb, c->g_stride, c->batch, n, chi[b], eo, Ub, c->u_stride, c->ework, c->status, s);
+      if (c->deriv_mode == 2)
+        for (int w = 0; w < 2; ++w) {
+          // dG from the half-Gram tangents, then dU from the eigensystem still in ework
+          const double* dTw = c->dT + w * P2max * c->batch;
+          launch_half_gram(c->T, P2max, c->batch, g, b, c->d + a, c->gpartial, c->H1, c->q_stride, s, dTw);
+          launch_half_gram(c->T, P2max, c->batch, g, b, a, c->gpartial, c->H2, c->q_stride, s, dTw);
+          launch_gram_combine_tangent(c->Q1, c->Q2, c->H1, c->H2, c->q_stride, c->batch, g.D[b], g.D[a], c->dG,
+                                      c->dg_stride, s);
+          launch_eig_tangent(c->ework, Ub, c->u_stride, c->dG, c->dg_stride, c->batch, n, chi[b],
+                             c->dU + w * c->u_stride * c->batch + (long long)b * kMaxBond * kMaxGram, s);
+        }
     }
   }
   // 2-4. squeeze, normalise and accumulate, instance by instance (each fills the GPU)
   for (int i = 0; i < c->batch; ++i) {
     const double* Ti = c->T + i * P2max;
     const double* Ui = c->U + i * c->u_stride;
-    auto sq = [&](const double* A1, const double* A2, double* out) {
-      return planes ? squeeze<float>(c, A1, A2, out, Ui, g, gn, a, chi, trans, nt, planes, npass)
-                    : squeeze<double>(c, A1, A2, out, Ui, g, gn, a, chi, trans, nt, 0, 0);
-    };
-    int rc = sq(Ti, Ti, c->Tnext);
+    Tangents tg;
+    if (c->deriv) {
+      tg.n = 2;
+      for (int w = 0; w < 2; ++w) {
+        tg.dT[w] = c->dT + (w * c->batch + i) * P2max;
+        tg.dout[w] = w ? c->D2 : c->D1;
+        tg.dU[w] = c->deriv_mode == 2 ? c->dU + (w * c->batch + i) * c->u_stride : nullptr;
+      }
+    }
+    const int rc = planes ? squeeze<float>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass, tg)
+                          : squeeze<double>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0, tg);
     if (rc) return rc;
     double* Tw = c->T + i * P2max;
     {
@@ -705,14 +854,11 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
       launch_norm_log(c->Tnext, gn.P * gn.P, c->norm_partial, c->cval + i,
                       c->lnc_log + (long long)i * (c->max_steps + 1), c->L + i, c->dstep, c->status, s);
     }
-    if (c->deriv) {
-      // tangent of the step with U fixed: dT' = S(dT, T) + S(T, dT), then of T' / ||T'||
-      for (int w = 0; w < 2; ++w) {
-        double* dTi = c->dT + (w * c->batch + i) * P2max;
-        if ((rc = sq(dTi, Ti, c->D1)) || (rc = sq(Ti, dTi, c->D2))) return rc;
-        launch_tangent_norm(c->Tnext, c->D1, c->D2, dTi, gn.P * gn.P, c->cval + i, c->norm_partial,
-                            c->dlnc + w * c->batch + i, c->dL + w * c->batch + i, c->dstep, s);
-      }
+    // tangent of T' / ||T'||
+    for (int w = 0; w < tg.n; ++w) {
+      double* dTi = c->dT + (w * c->batch + i) * P2max;
+      launch_tangent_norm(c->Tnext, tg.dout[w], nullptr, dTi, gn.P * gn.P, c->cval + i, c->norm_partial,
+                          c->dlnc + w * c->batch + i, c->dL + w * c->batch + i, c->dstep, s);
     }
     launch_scale(c->Tnext, Tw, gn.P * gn.P, c->cval + i, s);
   }

@@ -38,18 +38,21 @@ void launch_scale(const double* src, double* dst, long long n, const double* c, 
 // One CTA per instance: T + i*t_stride, L + i, out3 + 3 i.
 void launch_trace_x(const double* T, long long t_stride, int batch, Geom g, int axis, const double* L,
                     const int* dstep, double* out3, cudaStream_t s);
-// out[..u_b=j..] = sum_i U[kk][i][j] in[..u_b=i..] on unprimed leg b (U: [chi][Db][Db] fp64).
+// out[..u_b=j..] = sum_i U[kk][i][j] in[..u_b=i..] on unprimed leg b (U: [chi][Db][Db] fp64);
+// with in2, plus the same product of in2 with U2.
 template <class Tin, class Tout>
 void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double* U, int kk,
-                          cudaStream_t s);
+                          cudaStream_t s, const Tin* in2 = nullptr, const double* U2 = nullptr);
 // Tt[p][u] = T[u][p] (P x P), converted to Tout.
 template <class Tout>
 void launch_transpose(const double* T, Tout* Tt, long long P, cudaStream_t s);
 // B operand, K-major: Bt[(j*P + n)][k] = sum_x U3[j][k_c3][x] Tt[n][k | c3 := x], j < chi3.
-// c3 < 0: Bt = Tt. Mixed: 2 or 3 bf16 planes; FP64: one double plane.
+// c3 < 0: Bt = Tt. Mixed: 2 or 3 bf16 planes; FP64: one double plane. With Tt2 (c3 >= 0), plus
+// the same sum over Tt2 with U3b.
 template <class Tin, class Tout>
 void launch_build_bt(const Tin* Tt, const Planes<Tout>& out, long long ld, Geom g, int c3,
-                     const double* U3, int chi3, cudaStream_t s);
+                     const double* U3, int chi3, cudaStream_t s, const Tin* Tt2 = nullptr,
+                     const double* U3b = nullptr);
 // A operand, K-major: Y[m][k] = X[u = (k_b, m_a)][p = (m_b, k_a)] for a step along `a`.
 template <class Tin, class Tout>
 void launch_build_y(const Tin* X, const Planes<Tout>& out, long long ld, Geom g, int a,
@@ -60,11 +63,15 @@ void launch_pair_contract(const Tin* in, Tout* out, const View& v, int kaxis, in
                           long long si, long long sj, const double* U, int chi, long long in_base,
                           long long out_base, cudaStream_t s);
 // Same contraction with one thread per index of `rest` (the output axes without k'), computing
-// all chi outputs out[o + k' sk]; every input element is read once.
+// all chi outputs out[o + k' sk]; every input element is read once. With in2 (same layout), plus
+// the same contraction of in2 with U2.
 template <class Tin, class Tout>
 void launch_pair_contract_all(const Tin* in, Tout* out, const View& rest, int Di, int Dj, long long si,
                               long long sj, long long sk, const double* U, int chi, long long in_base,
-                              long long out_base, cudaStream_t s);
+                              long long out_base, cudaStream_t s, const Tin* in2 = nullptr,
+                              const double* U2 = nullptr);
+// Raise the dynamic shared-memory limit of the two-input kernels (call once, before any capture).
+void prepare_kernel_attributes();
 
 // ---- gram.cu -------------------------------------------------------------------------------
 // Q[(i,al)][(i~,al~)] = sum over all other legs of T[..i..al..] T[..i~..al~..]; legs l1, l2 are
@@ -72,11 +79,17 @@ void launch_pair_contract_all(const Tin* in, Tout* out, const View& rest, int Di
 // Instance i reads T + i*t_stride and writes Q + i*q_stride.
 int gram_nsplit();
 size_t gram_partial_doubles(int nr_max, int batch);  // scratch for `partial`
+// With TA: rows from TA (same layout and strides as T), columns from T: Q(TA, T).
 void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, int l1, int l2,
-                      double* partial, double* Q, long long q_stride, cudaStream_t s);
+                      double* partial, double* Q, long long q_stride, cudaStream_t s,
+                      const double* TA = nullptr);
 // G[(b1 b2)][(b1~ b2~)] = sum_{al,al~} Q1[(b1,al)][(b1~,al~)] Q2[(b2,al)][(b2~,al~)] per instance
 void launch_gram_combine(const double* Q1, const double* Q2, long long q_stride, int batch, int Db,
                          int Da, double* G, long long g_stride, cudaStream_t s);
+// dG = sum (H1 + H1^T) Q2 + Q1 (H2 + H2^T), H = Q(dT, T): the tangent of the Gram matrix.
+void launch_gram_combine_tangent(const double* Q1, const double* Q2, const double* H1, const double* H2,
+                                 long long q_stride, int batch, int Db, int Da, double* dG, long long g_stride,
+                                 cudaStream_t s);
 
 // ---- eig.cu --------------------------------------------------------------------------------
 // Where the sorted eigenvalues go: base + i*inst_stride + (*step - 1)*step_stride for instance
@@ -92,6 +105,15 @@ struct EigOut {
 // work: batch * 2*n*n doubles. Sets ST_NOCONV on the sweep limit.
 void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o,
                 double* U, long long u_stride, double* work, int* status, cudaStream_t s);
+// First-order change of the kept eigenvectors for a change dG of G, from the eigensystem that
+// launch_eig left in `work` (call before the next launch_eig reuses it):
+//   dU_k = sign_k sum_{j >= chi} V_j (V_j^T dG V_k) / (lambda_k - lambda_j),  k < chi,
+// with sign_k the sign convention applied to U_k. Rotations inside the kept space are left out:
+// they are a gauge change of the new bond under which the flow's ln Z is invariant. A cut with
+// lambda_k == lambda_j (k < chi <= j) has no derivative: dU gets NaN.
+void launch_eig_tangent(const double* work, const double* U, long long u_stride, const double* dG,
+                        long long g_stride, int batch, int n, int chi, double* dU, cudaStream_t s);
+void prepare_eig_attributes();  // shared-memory limit of the tangent kernel (once, before any capture)
 
 // ---- gemm_simt.cu --------------------------------------------------------------------------
 // C[m][n] = sum_k A[m][k] Bt[n][k] in FP64 (CUDA cores).

@@ -236,13 +236,20 @@ __global__ void __launch_bounds__(256) k_trace_x(const double* __restrict__ T, l
 }
 
 // ---------------------------------------------------------------------------- mode product
-template <class Tin, class Tout>
+// TWO: out also accumulates the same product of a second input with a second matrix (the
+// tangent of a mode product: dX = M_U(dT) + M_dU(T)).
+template <class Tin, class Tout, bool TWO>
 __global__ void __launch_bounds__(256) k_mode_unprimed(const Tin* __restrict__ in, Tout* __restrict__ out,
                                                        long long total, long long stride_b, int Db,
-                                                       const double* __restrict__ U, int kk) {
+                                                       const double* __restrict__ U, int kk,
+                                                       const Tin* __restrict__ in2, const double* __restrict__ U2) {
   using Acc = AccT<Tout>;
   __shared__ Acc W[kMaxGram];
-  for (int t = threadIdx.x; t < Db * Db; t += blockDim.x) W[t] = (Acc)U[(long long)kk * Db * Db + t];
+  __shared__ Acc W2[TWO ? kMaxGram : 1];
+  for (int t = threadIdx.x; t < Db * Db; t += blockDim.x) {
+    W[t] = (Acc)U[(long long)kk * Db * Db + t];
+    if (TWO) W2[t] = (Acc)U2[(long long)kk * Db * Db + t];
+  }
   __syncthreads();
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -250,6 +257,8 @@ __global__ void __launch_bounds__(256) k_mode_unprimed(const Tin* __restrict__ i
     const long long base = idx - (long long)j * stride_b;
     Acc acc = 0;
     for (int i = 0; i < Db; ++i) acc += W[i * Db + j] * (Acc)in[base + i * stride_b];
+    if (TWO)
+      for (int i = 0; i < Db; ++i) acc += W2[i * Db + j] * (Acc)in2[base + i * stride_b];
     out[idx] = (Tout)acc;
   }
 }
@@ -273,16 +282,23 @@ __global__ void __launch_bounds__(256) k_transpose(const double* __restrict__ T,
 
 // ---------------------------------------------------------------------------- B operand
 // Bt[(j*P + n)][k] = sum_x U3[j][k_c3][x] Tt[n][k | c3 := x]
-template <class Tin, class Tout>
+// TWO: the row also accumulates sum_x U3b[j][k_c3][x] Tt2[n][k | c3 := x] (the tangent of the
+// B operand: dBt = B_U3(dTt) + B_dU3(Tt)).
+template <class Tin, class Tout, bool TWO>
 __global__ void __launch_bounds__(256) k_build_bt(const Tin* __restrict__ Tt, Planes<Tout> out,
                                                   long long ld, long long P,
                                                   long long Sc, int Dc, const double* __restrict__ U3,
-                                                  int chi3) {
+                                                  int chi3, const Tin* __restrict__ Tt2,
+                                                  const double* __restrict__ U3b) {
   using Acc = AccT<Tout>;
   extern __shared__ unsigned char smraw[];
-  Acc* W = reinterpret_cast<Acc*>(smraw);  // [chi3][Dc][Dc]
+  Acc* W = reinterpret_cast<Acc*>(smraw);  // [chi3][Dc][Dc], then the same for U3b
   const int nW = chi3 * Dc * Dc;
-  for (int t = threadIdx.x; t < nW; t += blockDim.x) W[t] = U3 ? (Acc)U3[t] : (Acc)1;
+  Acc* W2 = W + nW;
+  for (int t = threadIdx.x; t < nW; t += blockDim.x) {
+    W[t] = U3 ? (Acc)U3[t] : (Acc)1;
+    if (TWO) W2[t] = (Acc)U3b[t];
+  }
   __syncthreads();
   const long long total = (long long)chi3 * P * P;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -298,6 +314,10 @@ __global__ void __launch_bounds__(256) k_build_bt(const Tin* __restrict__ Tt, Pl
       const Acc* w = W + ((long long)j * Dc + kc) * Dc;
       acc = 0;
       for (int x = 0; x < Dc; ++x) acc += w[x] * (Acc)Tt[base + x * Sc];
+      if (TWO) {
+        const Acc* w2 = W2 + ((long long)j * Dc + kc) * Dc;
+        for (int x = 0; x < Dc; ++x) acc += w2[x] * (Acc)Tt2[base + x * Sc];
+      }
     } else {
       acc = (Acc)Tt[n * P + k];
     }
@@ -386,20 +406,26 @@ __global__ void __launch_bounds__(256) k_pair_contract(const Tin* __restrict__ i
 // All chi outputs of one "rest" index per thread: out[o + k' sk] = sum_{i,j} U[k'][i][j] in[r + i si + j sj]
 // (r, o: offsets of the rest index in the input and output views). Every input element is read
 // once; W is held in shared memory as [i][j][k'] so a warp reads it by broadcast.
-template <class Tin, class Tout>
+// TWO: out also accumulates the same contraction of in2 with U2 (the tangent of an epilogue
+// contraction: dR' = C_U(dR) + C_dU(R)).
+template <class Tin, class Tout, bool TWO>
 __global__ void __launch_bounds__(256) k_pair_contract_all(const Tin* __restrict__ in, Tout* __restrict__ out,
                                                            View v, long long total, int Di, int Dj,
                                                            long long si, long long sj, long long sk,
                                                            const double* __restrict__ U, int chi,
-                                                           long long in_base, long long out_base) {
+                                                           long long in_base, long long out_base,
+                                                           const Tin* __restrict__ in2,
+                                                           const double* __restrict__ U2) {
   using Acc = AccT<Tout>;
   constexpr int kMaxChi = kMaxBond;
   extern __shared__ unsigned char smraw[];
-  Acc* W = reinterpret_cast<Acc*>(smraw);  // [Di*Dj][chi]
+  Acc* W = reinterpret_cast<Acc*>(smraw);  // [Di*Dj][chi], then the same for U2
   const int nij = Di * Dj;
+  Acc* W2 = W + (long long)chi * nij;
   for (int t = threadIdx.x; t < chi * nij; t += blockDim.x) {
     const int k = t / nij, ij = t % nij;
     W[ij * chi + k] = U ? (Acc)U[t] : (Acc)1;
+    if (TWO) W2[ij * chi + k] = (Acc)U2[t];
   }
   __syncthreads();
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -424,6 +450,17 @@ __global__ void __launch_bounds__(256) k_pair_contract_all(const Tin* __restrict
           if (k < chi) acc[k] += w[k] * x;
       }
     }
+    if (TWO)
+      for (int i = 0; i < Di; ++i) {
+        const Tin* src = in2 + ioff + i * si;
+        for (int j = 0; j < Dj; ++j) {
+          const Acc x = (Acc)src[j * sj];
+          const Acc* w = W2 + (i * Dj + j) * chi;
+#pragma unroll
+          for (int k = 0; k < kMaxChi; ++k)
+            if (k < chi) acc[k] += w[k] * x;
+        }
+      }
 #pragma unroll
     for (int k = 0; k < kMaxChi; ++k)
       if (k < chi) out[ooff + k * sk] = (Tout)acc[k];
@@ -491,10 +528,14 @@ void launch_trace_x(const double* T, long long t_stride, int batch, Geom g, int 
 
 template <class Tin, class Tout>
 void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double* U, int kk,
-                          cudaStream_t s) {
+                          cudaStream_t s, const Tin* in2, const double* U2) {
   const long long total = g.P * g.P;
-  k_mode_unprimed<Tin, Tout><<<grid_for(total, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
-                                                                   g.D[b], U, kk);
+  if (in2)
+    k_mode_unprimed<Tin, Tout, true><<<grid_for(total, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
+                                                                           g.D[b], U, kk, in2, U2);
+  else
+    k_mode_unprimed<Tin, Tout, false><<<grid_for(total, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
+                                                                            g.D[b], U, kk, nullptr, nullptr);
   count_launches(1);
 }
 
@@ -507,15 +548,21 @@ void launch_transpose(const double* T, Tout* Tt, long long P, cudaStream_t s) {
 
 template <class Tin, class Tout>
 void launch_build_bt(const Tin* Tt, const Planes<Tout>& out, long long ld, Geom g, int c3,
-                     const double* U3, int chi3, cudaStream_t s) {
+                     const double* U3, int chi3, cudaStream_t s, const Tin* Tt2, const double* U3b) {
   using Acc = AccT<Tout>;
   const long long Sc = c3 >= 0 ? g.Sn[c3] : 0;
   const int Dc = c3 >= 0 ? g.D[c3] : 1;
   const int nchi = c3 >= 0 ? chi3 : 1;
-  const size_t smem = sizeof(Acc) * (size_t)nchi * Dc * Dc;
+  const bool two = Tt2 && c3 >= 0;
+  const size_t smem = sizeof(Acc) * (size_t)nchi * Dc * Dc * (two ? 2 : 1);
   const long long total = (long long)nchi * g.P * g.P;
-  k_build_bt<Tin, Tout><<<grid_for(total, 256), 256, smem, s>>>(Tt, out, ld, g.P, Sc, Dc,
-                                                                 c3 >= 0 ? U3 : nullptr, nchi);
+  if (two)
+    k_build_bt<Tin, Tout, true><<<grid_for(total, 256), 256, smem, s>>>(Tt, out, ld, g.P, Sc, Dc, U3, nchi,
+                                                                         Tt2, U3b);
+  else
+    k_build_bt<Tin, Tout, false><<<grid_for(total, 256), 256, smem, s>>>(Tt, out, ld, g.P, Sc, Dc,
+                                                                          c3 >= 0 ? U3 : nullptr, nchi,
+                                                                          nullptr, nullptr);
   count_launches(1);
 }
 
@@ -544,32 +591,58 @@ void launch_pair_contract(const Tin* in, Tout* out, const View& v, int kaxis, in
 template <class Tin, class Tout>
 void launch_pair_contract_all(const Tin* in, Tout* out, const View& rest, int Di, int Dj, long long si,
                               long long sj, long long sk, const double* U, int chi, long long in_base,
-                              long long out_base, cudaStream_t s) {
+                              long long out_base, cudaStream_t s, const Tin* in2, const double* U2) {
   using Acc = AccT<Tout>;
   long long total = 1;
   for (int i = 0; i < rest.ndim; ++i) total *= rest.shape[i];
-  const size_t smem = sizeof(Acc) * (size_t)chi * Di * Dj;
-  k_pair_contract_all<Tin, Tout><<<grid_for(total, 256), 256, smem, s>>>(in, out, rest, total, Di, Dj, si, sj, sk,
-                                                                          U, chi, in_base, out_base);
+  const size_t smem = sizeof(Acc) * (size_t)chi * Di * Dj * (in2 ? 2 : 1);
+  if (in2)
+    k_pair_contract_all<Tin, Tout, true><<<grid_for(total, 256), 256, smem, s>>>(
+        in, out, rest, total, Di, Dj, si, sj, sk, U, chi, in_base, out_base, in2, U2);
+  else
+    k_pair_contract_all<Tin, Tout, false><<<grid_for(total, 256), 256, smem, s>>>(
+        in, out, rest, total, Di, Dj, si, sj, sk, U, chi, in_base, out_base, nullptr, nullptr);
   count_launches(1);
 }
 
+// The two-input contractions and B-operand builds in FP64 can need more than the default 48 KB
+// of dynamic shared memory (2 x 16 x 256 doubles): raise the limit once, outside any capture.
+void prepare_kernel_attributes() {
+  const int big = (int)(2 * sizeof(double) * kMaxBond * kMaxGram);
+  cudaFuncSetAttribute(k_pair_contract_all<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_pair_contract_all<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_pair_contract_all<float, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_build_bt<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_build_bt<float, __nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
 // explicit instantiations: FP64 path (double everywhere) and BF16X3 path (float intermediates)
-template void launch_mode_unprimed<double, double>(const double*, double*, Geom, int, const double*, int, cudaStream_t);
-template void launch_mode_unprimed<double, float>(const double*, float*, Geom, int, const double*, int, cudaStream_t);
-template void launch_mode_unprimed<float, float>(const float*, float*, Geom, int, const double*, int, cudaStream_t);
+template void launch_mode_unprimed<double, double>(const double*, double*, Geom, int, const double*, int, cudaStream_t,
+                                                   const double*, const double*);
+template void launch_mode_unprimed<double, float>(const double*, float*, Geom, int, const double*, int, cudaStream_t,
+                                                  const double*, const double*);
+template void launch_mode_unprimed<float, float>(const float*, float*, Geom, int, const double*, int, cudaStream_t,
+                                                 const float*, const double*);
 template void launch_transpose<double>(const double*, double*, long long, cudaStream_t);
 template void launch_transpose<float>(const double*, float*, long long, cudaStream_t);
-template void launch_build_bt<double, double>(const double*, const Planes<double>&, long long, Geom, int, const double*, int, cudaStream_t);
-template void launch_build_bt<float, __nv_bfloat16>(const float*, const Planes<__nv_bfloat16>&, long long, Geom, int, const double*, int, cudaStream_t);
+template void launch_build_bt<double, double>(const double*, const Planes<double>&, long long, Geom, int, const double*, int,
+                                              cudaStream_t, const double*, const double*);
+template void launch_build_bt<float, __nv_bfloat16>(const float*, const Planes<__nv_bfloat16>&, long long, Geom, int,
+                                                    const double*, int, cudaStream_t, const float*, const double*);
 template void launch_build_y<double, double>(const double*, const Planes<double>&, long long, Geom, int, cudaStream_t);
 template void launch_build_y<float, __nv_bfloat16>(const float*, const Planes<__nv_bfloat16>&, long long, Geom, int, cudaStream_t);
 template void launch_build_y<double, __nv_bfloat16>(const double*, const Planes<__nv_bfloat16>&, long long, Geom, int, cudaStream_t);
 template void launch_pair_contract<double, double>(const double*, double*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
 template void launch_pair_contract<float, float>(const float*, float*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
 template void launch_pair_contract<float, double>(const float*, double*, const View&, int, int, int, long long, long long, const double*, int, long long, long long, cudaStream_t);
-template void launch_pair_contract_all<double, double>(const double*, double*, const View&, int, int, long long, long long, long long, const double*, int, long long, long long, cudaStream_t);
-template void launch_pair_contract_all<float, float>(const float*, float*, const View&, int, int, long long, long long, long long, const double*, int, long long, long long, cudaStream_t);
-template void launch_pair_contract_all<float, double>(const float*, double*, const View&, int, int, long long, long long, long long, const double*, int, long long, long long, cudaStream_t);
+template void launch_pair_contract_all<double, double>(const double*, double*, const View&, int, int, long long, long long,
+                                                       long long, const double*, int, long long, long long, cudaStream_t,
+                                                       const double*, const double*);
+template void launch_pair_contract_all<float, float>(const float*, float*, const View&, int, int, long long, long long,
+                                                     long long, const double*, int, long long, long long, cudaStream_t,
+                                                     const float*, const double*);
+template void launch_pair_contract_all<float, double>(const float*, double*, const View&, int, int, long long, long long,
+                                                      long long, const double*, int, long long, long long, cudaStream_t,
+                                                      const float*, const double*);
 
 }  // namespace hotrg

@@ -63,9 +63,12 @@ def deriv_record(cfg):
     f = R.run(**cfg)
     gaps = [min(g.values()) for g in f.gaps if g]
     db, dh = R.fixed_isometry_derivatives(**cfg)
+    fb, fh = R.flow_derivatives(**cfg)
     return dict(config=cfg, lnz=[float(x) for x in f.lnz], dlnz_dbeta=[float(x) for x in db],
-                dlnz_dh=[float(x) for x in dh], min_cut_gap=float(min(gaps)),
-                source="oracle/hotrg_ref.py fixed_isometry_derivatives(), FP64, eps = 1e-3 Richardson")
+                dlnz_dh=[float(x) for x in dh], flow_dlnz_dbeta=[float(x) for x in fb],
+                flow_dlnz_dh=[float(x) for x in fh], min_cut_gap=float(min(gaps)),
+                source="oracle/hotrg_ref.py fixed_isometry_derivatives() (eps = 1e-3) and "
+                       "flow_derivatives() (eps = 1e-4), FP64 central differences, Richardson")
 
 
 def main():

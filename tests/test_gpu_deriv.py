@@ -178,3 +178,89 @@ def test_checkpoint_roundtrip_keeps_tangents():
     with HOTRG(4, 0.1497, 0.01, 4, max_steps=8) as c:
         with pytest.raises(RuntimeError):
             c.state_load(blob)          # saved with tangents, loaded without
+
+
+# ------------------------------------------------------------------ derivatives through the isometries
+def eig_flow(d, beta, h, Dcut, **kw):
+    from paper_1906_06060_gb300 import HOTRG
+    return HOTRG(d, beta, h, Dcut, derivatives="eig", **kw)
+
+
+@pytest.mark.parametrize("beta,h", [(0.7, 0.2)])
+def test_eig_mode_d1_matches_transfer_matrix(beta, h):
+    with eig_flow(1, beta, h, 2, max_steps=16) as f:
+        for n in range(1, 17):
+            f.step()
+            db, dh, _ = derivs(f)
+            rb, rh = E.dlnz_1d(beta, h, 2 ** n)
+            assert abs(db - rb) < 1e-13 * max(1.0, abs(rb)) and abs(dh - rh) < 1e-13 * max(1.0, abs(rh))
+
+
+def test_eig_mode_2d_lossless_matches_enumeration():
+    beta, h = 0.4407, 0.05
+    with eig_flow(2, beta, h, 16) as f:
+        for _ in range(4):
+            f.step()
+        e, m = E.moments_bruteforce(beta, h, (4, 4))
+        db, dh, _ = derivs(f)
+        assert abs(db - (e + h * m)) < 1e-12 and abs(dh - beta * m) < 1e-12
+
+
+@pytest.mark.parametrize("beta,h,Dcut,nsteps", [(0.4407, 0.01, 8, 16), (0.3, 0.05, 4, 20)])
+def test_eig_mode_2d_truncated_matches_oracle_flow_difference_quotients(beta, h, Dcut, nsteps):
+    fb, fh = R.flow_derivatives(2, beta, h, Dcut, nsteps)
+    gaps = R.run(2, beta, h, Dcut, nsteps).gaps
+    last = next((n for n, g in enumerate(gaps) if g and min(g.values()) < 1e-8), nsteps)
+    assert last >= 8
+    with eig_flow(2, beta, h, Dcut, max_steps=nsteps) as f:
+        for n in range(1, last + 1):
+            f.step()
+            db, dh, _ = derivs(f)
+            assert abs(db - fb[n]) < 1e-8 * max(1.0, abs(fb[n])), n
+            assert abs(dh - fh[n]) < 1e-8 * max(1.0, abs(fh[n])), n
+
+
+@pytest.mark.parametrize("beta,h", [(0.1497, 0.0), (0.16, 0.01)])
+def test_eig_mode_4d_dcut3_matches_oracle_flow_difference_quotients(beta, h):
+    nsteps = 12
+    fb, fh = R.flow_derivatives(4, beta, h, 3, nsteps)
+    gaps = R.run(4, beta, h, 3, nsteps).gaps
+    last = next((n for n, g in enumerate(gaps) if g and min(g.values()) < 1e-8), nsteps)
+    with eig_flow(4, beta, h, 3, max_steps=nsteps) as f:
+        for n in range(1, last + 1):
+            f.step()
+            db, dh, _ = derivs(f)
+            assert abs(db - fb[n]) < 1e-8 * max(1.0, abs(fb[n])), n
+            assert abs(dh - fh[n]) < 1e-8 * max(1.0, abs(fh[n])), n
+
+
+@pytest.mark.parametrize("name", ["deriv_d4_b0.1497_h0_D5_n8", "deriv_d4_b0.16_h0.01_D5_n8"])
+@pytest.mark.parametrize("precision,fp64_steps,x6_steps,tol", [
+    ("fp64", 0, 0, 1e-8),        # bounded by the difference quotients of the golden values
+    ("bf16x3", 3, 12, 1e-6),     # the benchmark's precision schedule
+])
+def test_eig_mode_4d_dcut5_matches_golden(name, precision, fp64_steps, x6_steps, tol):
+    with open(os.path.join(GOLDEN, name + ".json")) as fh:
+        g = json.load(fh)
+    c = g["config"]
+    with eig_flow(4, c["beta"], c["h"], c["Dcut"], precision=precision, fp64_steps=fp64_steps,
+                  x6_steps=x6_steps, max_steps=c["nsteps"]) as f:
+        for n in range(1, c["nsteps"] + 1):
+            f.step()
+            db, dh, _ = derivs(f)
+            assert abs(db - g["flow_dlnz_dbeta"][n]) < tol * max(1.0, abs(g["flow_dlnz_dbeta"][n])), n
+            assert abs(dh - g["flow_dlnz_dh"][n]) < tol * max(1.0, abs(g["flow_dlnz_dh"][n])), n
+
+
+def test_eig_mode_graph_replay_is_bitwise():
+    import torch
+    from paper_1906_06060_gb300 import HOTRG
+    st = torch.cuda.Stream()
+    out = []
+    for graphs in (False, True):
+        with HOTRG(4, [0.1497, 0.15], 1e-5, 5, precision="bf16x3", fp64_steps=1, max_steps=10, stream=st,
+                   graphs=graphs, derivatives="eig") as f:
+            for _ in range(10):
+                f.step()
+            out.append([derivs(f, i)[:2] for i in range(2)])
+    assert out[0] == out[1]

@@ -310,3 +310,26 @@ def test_fixed_isometries_reproduce_the_free_flow():
     f = R.run(4, 0.1497, 0.0, 3, 6)
     g = R.run(4, 0.1497, 0.0, 3, 6, isometries=f.isometries)
     assert f.lnz == g.lnz
+
+
+@pytest.mark.parametrize("d,beta,h,Dcut,nsteps,L", [(1, 0.7, 0.2, 2, 10, (1024,)),
+                                                    (2, 0.4407, 0.05, 16, 4, (4, 4))])
+def test_flow_derivatives_lossless_match_exact(d, beta, h, Dcut, nsteps, L):
+    """Without truncation the flow's derivative is the lattice's: transfer matrix or enumeration."""
+    db, dh = R.flow_derivatives(d, beta, h, Dcut, nsteps)
+    if d == 1:
+        rb, rh = E.dlnz_1d(beta, h, L[0])
+    else:
+        e, m = E.moments_bruteforce(beta, h, L)
+        rb, rh = e + h * m, beta * m
+    assert abs(db[-1] - rb) < 1e-9 and abs(dh[-1] - rh) < 1e-9
+
+
+def test_flow_and_fixed_isometry_derivatives_differ_by_truncation_terms():
+    """Under truncation the two derivatives are different quantities (reading R9): at Dcut = 3
+    they part from step 2 on by far more than either's error."""
+    fb, fh = R.flow_derivatives(4, 0.16, 0.01, 3, 4)
+    xb, xh = R.fixed_isometry_derivatives(4, 0.16, 0.01, 3, 4)
+    assert abs(fb[0] - xb[0]) < 1e-10           # T^(0): nothing truncated yet
+    for n in (2, 3, 4):
+        assert abs(fb[n] - xb[n]) > 1e-3 and abs(fh[n] - xh[n]) > 1e-6
