@@ -15,6 +15,13 @@ of that schedule; with W = 3 they are BF16X6 steps.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|bf16x6|fp64]
     python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
 
+Other workloads of the same path (same JSON line; e2e and the CPU baseline only for the default):
+    --workload scan    batched temperature scan: beta in linspace(0.1490, 0.1505, n) x h in {0, 1e-5}
+                       (2n instances, default n = 64), Dcut = 8, one context, graph-captured steps
+    --workload deriv   d lnZ/d beta and d lnZ/d h through the eigendecomposition: beta in
+                       linspace(0.1494, 0.1500, n) (default n = 16), h = 1e-6, Dcut = 10
+    --instances n      fewer instances of a scan / deriv workload (a bounded sample of it)
+
 Multi-GPU (torchrun, one process per GPU): the single-flow workload does not shard, so each rank
 runs an independent replica; value = total flops of all ranks / max time over ranks.
 """
@@ -49,19 +56,50 @@ def parse():
     ap.add_argument("--kblock", type=int, default=64)
     ap.add_argument("--fold-group", type=int, default=0)
     ap.add_argument("--x6-steps", type=int, default=12)
-    ap.add_argument("--dcut", type=int, default=10)
+    ap.add_argument("--workload", default="flow", choices=["flow", "scan", "deriv"])
+    ap.add_argument("--instances", type=int, default=0)
+    ap.add_argument("--dcut", type=int, default=0)
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--h", type=float, default=0.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=2)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if not a.dcut:
+        a.dcut = 8 if a.workload == "scan" else 10
+    return a
+
+
+def instances(a):
+    """(betas, hs) of the workload's instances."""
+    import numpy as np
+    if a.workload == "scan":
+        n = a.instances or 64
+        b = [float(x) for x in np.linspace(0.1490, 0.1505, n)]
+        return b + b, [0.0] * n + [1e-5] * n
+    if a.workload == "deriv":
+        n = a.instances or 16
+        return [float(x) for x in np.linspace(0.1494, 0.1500, n)], [1e-6] * n
+    return [a.beta], [a.h]
 
 
 def workload_config(a):
-    return {"workload": f"4D Ising HOTRG, beta={a.beta}, h={a.h}, Dcut={a.dcut}: steady-state "
-                        f"coarse-graining steps (bond dims {a.dcut}^4) of the 40-step flow to 1024^4",
-            "d": 4, "Dcut": a.dcut, "beta": a.beta, "h": a.h, "precision": a.precision,
+    betas, hs = instances(a)
+    if a.workload == "scan":
+        what = (f"4D Ising HOTRG batched temperature scan: {len(betas)} instances (beta in "
+                f"linspace(0.1490, 0.1505, {len(betas) // 2}) x h in {{0, 1e-5}}), Dcut={a.dcut}: steady-state "
+                f"steps of the 40-step flows to 1024^4, one context, graph-captured steps")
+    elif a.workload == "deriv":
+        what = (f"4D Ising HOTRG with d lnZ/d beta and d lnZ/d h through the eigendecomposition: "
+                f"{len(betas)} instances (beta in linspace(0.1494, 0.1500, {len(betas)}), h = 1e-6), "
+                f"Dcut={a.dcut}: steady-state steps of the 40-step flow to 1024^4; flops counted: forward "
+                f"squeeze + two tangent contractions over a doubled k range (5x the forward)")
+    else:
+        what = (f"4D Ising HOTRG, beta={a.beta}, h={a.h}, Dcut={a.dcut}: steady-state "
+                f"coarse-graining steps (bond dims {a.dcut}^4) of the 40-step flow to 1024^4")
+    return {"workload": what, "instances": len(betas),
+            "d": 4, "Dcut": a.dcut, "beta": a.beta if len(betas) == 1 else [min(betas), max(betas)],
+            "h": a.h if len(hs) == 1 else sorted(set(hs)), "precision": a.precision,
             "timed_steps": [a.warmup + 1, a.warmup + a.steps],
             "fp64_steps": a.fp64_steps, "x6_steps": a.x6_steps, "kblock": a.kblock,
             "fold_group": a.fold_group,
@@ -214,7 +252,10 @@ def run_ours(a, rank, world, dist):
         if dist:
             dist.barrier()
 
-    flow = HOTRG(4, a.beta, a.h, a.dcut, **kw)
+    betas, hs = instances(a)
+    if a.workload == "deriv":
+        kw["derivatives"] = "eig"
+    flow = HOTRG(4, betas, hs, a.dcut, **kw)
     for _ in range(a.warmup):
         flow.step()
     flow.free_energy()
@@ -235,8 +276,9 @@ def run_ours(a, rank, world, dist):
     t = flow.timing_stop()
     ms = ev0.elapsed_time(ev1)
     lnz = flow.free_energy()[0][0]
+    flow_obs = [flow.observables(i) for i in range(flow.batch)] if a.workload == "deriv" else []
     flow.close()
-    step_flops = t["step_flops"]
+    step_flops = t["step_flops"] * (5.0 if a.workload == "deriv" else 1.0)
     # max time over ranks, total flops over ranks
     if dist:
         buf = torch.tensor([ms, step_flops], dtype=torch.float64, device=dev)
@@ -255,7 +297,10 @@ def run_ours(a, rank, world, dist):
     achieved = (t["gemm_flops"] / max(1, t["gemm_launches"])) / (gemm_ms * 1e-3) / 1e12
     peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic_from_profile(),
+            "frac": achieved / peak,
+            # the committed ncu capture is of the Dcut = 10 BF16X3 steady-step GEMM
+            "traffic": (traffic_from_profile() if (a.workload == "flow" and a.dcut == 10 and a.precision == "bf16x3")
+                        else None),
             "peak_source": f"{src} bf16 sustained (kernel timed inside long steps)",
             "kernel": "k_gemm_split (tcgen05 squeeze GEMM)" if a.precision != "fp64" else "k_gemm_f64",
             "tensor_pipe_tflops": (t["gemm_tensor_flops"] / max(1, t["gemm_launches"])) / (gemm_ms * 1e-3) / 1e12,
@@ -264,13 +309,18 @@ def run_ours(a, rank, world, dist):
     if a.precision == "fp64":
         roof.update({"bound": "alu", "peak": 1.25, "peak_source": "nominal GB300 FP64 rate",
                      "frac": achieved / 1.25})
+    if a.workload == "deriv":
+        o = [flow_obs[i] for i in range(len(flow_obs))]
+        extra = {"internal_energy": [x["internal_energy"] for x in o], "magnetization": [x["magnetization"] for x in o]}
+    else:
+        extra = {}
     out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "bf16",
            "data": "synthetic", "config": workload_config(a),
            "steps_per_s": a.steps / (ms_max * 1e-3), "roofline": roof,
            "phases_ms_per_step": {k[3:]: v / a.steps for k, v in t.items() if k.startswith("ms_")},
-           "gpu_launches": int(t["kernel_launches"]), "lnz_per_site_after": lnz}
+           "gpu_launches": int(t["kernel_launches"]), "lnz_per_site_after": lnz, **extra}
     out["clocks"] = clk.summary()
     return out
 
@@ -327,9 +377,9 @@ def main():
     build.build()
     out = run_ours(a, rank, world, dist)
     if out is not None:
-        if not a.no_e2e:
+        if not a.no_e2e and a.workload == "flow":
             out["e2e"] = e2e(a)
-        if not a.no_cpu_baseline and world == 1:
+        if not a.no_cpu_baseline and world == 1 and a.workload == "flow":
             dt, f = oracle_sample(a.dcut, a.cpu_slices)
             out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_threads(),
                                    "kind": "oracle",

@@ -95,3 +95,33 @@ def test_product_path_fails_loudly_without_a_device():
     from paper_1906_06060_gb300 import HOTRG
     with pytest.raises(RuntimeError, match="CUDA device"):
         HOTRG(4, 0.1497, 0.0, 4)
+
+
+def test_derivative_modes_size_the_workspace_and_reject_unknown_modes(lib):
+    from paper_1906_06060_gb300 import _lib
+    n = ctypes.c_size_t()
+    o = _lib.Opts()
+    lib.hotrg_opts_default(ctypes.byref(o))
+    sizes = []
+    for mode in (0, 1, 2):
+        o.derivatives = mode
+        assert lib.hotrg_workspace_size(4, 6, ctypes.byref(o), ctypes.byref(n)) == 0
+        sizes.append(n.value)
+    # tangent tensors, three operand blocks per row, and (mode 2) the Gram / isometry tangents
+    assert sizes[0] < sizes[1] < sizes[2]
+    for bad in (-1, 3):
+        o.derivatives = bad
+        assert lib.hotrg_workspace_size(4, 6, ctypes.byref(o), ctypes.byref(n)) == _lib.HOTRG_EINVAL
+        ctx = ctypes.c_void_p()
+        assert lib.hotrg_init(ctypes.byref(ctx), 4, 0.1, 0.0, 6, ctypes.byref(o)) == _lib.HOTRG_EINVAL
+
+
+def test_autograd_entry_fails_loudly_without_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("has a GPU")
+    from paper_1906_06060_gb300.autograd import lnz
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        lnz(torch.tensor([0.15]), torch.tensor([0.0]), d=2, Dcut=4, nsteps=2)
+    with pytest.raises(ValueError):
+        lnz(torch.tensor([0.15]), torch.tensor([0.0]), mode="adjoint")

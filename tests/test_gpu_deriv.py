@@ -264,3 +264,44 @@ def test_eig_mode_graph_replay_is_bitwise():
                 f.step()
             out.append([derivs(f, i)[:2] for i in range(2)])
     assert out[0] == out[1]
+
+
+# ------------------------------------------------------------------ torch.autograd
+@pytest.mark.parametrize("mode", ["eig", "fixed"])
+def test_autograd_function_returns_the_library_derivatives(mode):
+    import torch
+    from paper_1906_06060_gb300.autograd import lnz
+    beta = torch.tensor([0.1497, 0.16], dtype=torch.float64, requires_grad=True)
+    h = torch.tensor([0.0, 0.01], dtype=torch.float64, requires_grad=True)
+    y = lnz(beta, h, d=4, Dcut=5, nsteps=8, mode=mode)
+    gb, gh = torch.autograd.grad(y.sum(), (beta, h))
+    for i, name in enumerate(["deriv_d4_b0.1497_h0_D5_n8", "deriv_d4_b0.16_h0.01_D5_n8"]):
+        with open(os.path.join(GOLDEN, name + ".json")) as fh:
+            g = json.load(fh)
+        kb, kh = ("flow_dlnz_dbeta", "flow_dlnz_dh") if mode == "eig" else ("dlnz_dbeta", "dlnz_dh")
+        assert abs(float(y[i]) - g["lnz"][8]) < 1e-12 * abs(g["lnz"][8])
+        assert abs(float(gb[i]) - g[kb][8]) < 1e-8 and abs(float(gh[i]) - g[kh][8]) < 1e-8
+
+
+def test_autograd_eig_mode_matches_gpu_finite_differences():
+    """The derivative of the flow against central differences of the GPU's own FP64 free energy
+    (step 1e-5, as the differentiation workload asks), 2D Dcut = 8, 20 steps."""
+    import torch
+    from paper_1906_06060_gb300 import HOTRG
+    from paper_1906_06060_gb300.autograd import lnz
+    b0, h0, eps = 0.4407, 0.01, 1e-5
+    beta = torch.tensor([b0], dtype=torch.float64, requires_grad=True)
+    h = torch.tensor([h0], dtype=torch.float64, requires_grad=True)
+    y = lnz(beta, h, d=2, Dcut=8, nsteps=20, mode="eig")
+    gb, gh = torch.autograd.grad(y.sum(), (beta, h))
+
+    def f(b, hh):
+        with HOTRG(2, b, hh, 8, max_steps=20) as fl:
+            for _ in range(20):
+                fl.step()
+            return fl.free_energy()[0][0]
+
+    fd_b = (f(b0 + eps, h0) - f(b0 - eps, h0)) / (2 * eps)
+    fd_h = (f(b0, h0 + eps) - f(b0, h0 - eps)) / (2 * eps)
+    # FD error: eps^2 f''' / 6 plus ~1e-16 / eps rounding of the FP64 flow
+    assert abs(float(gb[0]) - fd_b) < 1e-6 and abs(float(gh[0]) - fd_h) < 1e-6
