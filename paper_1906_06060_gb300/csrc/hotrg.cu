@@ -1045,6 +1045,8 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
     for (int b = 0; b < c->d; ++b)
       if (dims[b] != c->dims[b]) return HOTRG_EINVAL;
   Geom g = make_geom(c->d, dims);
+  // the tensor slot holds Pmax^2 entries (the largest state the workspace plan reaches)
+  if (g.P > c->Pmax) return HOTRG_EINVAL;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
       cudaMemcpy(c->T + instance * c->Pmax * c->Pmax, host, sizeof(double) * g.P * g.P,
                  cudaMemcpyHostToDevice) != cudaSuccess)

@@ -282,6 +282,12 @@ def test_error_codes():
         assert f.observables()["steps"] == 2
     with pytest.raises(HotrgError):
         flow(4, -0.1, 0.0, 4)
+    # a tensor larger than the workspace plan's largest state is refused, not copied
+    with flow(4, 0.1497, 0.0, 4, max_steps=1) as f:
+        with pytest.raises(HotrgError) as e:
+            f.set_tensor(np.zeros((4,) * 8))
+        assert e.value.code == _lib.HOTRG_EINVAL
+        f.step()
 
 
 def test_autotune_picks_a_candidate_and_keeps_accuracy():
