@@ -81,6 +81,9 @@ typedef struct hotrg_opts {
                                isometries through the Gram eigendecomposition (first-order
                                eigenvector perturbation; NaN where a cut splits a degenerate
                                eigenvalue, where no derivative exists). EINVAL otherwise. */
+  int impurities;         /* 1: also coarse-grain the impure tensors of Sec. 2 (Eqs. (impTN),
+                             (SS), (ST)) with the pure flow's isometries and report the
+                             estimates of Eqs. (energy) and (spin): two extra squeezes per step */
   int graphs;             /* 1: capture a steady-state step (bond dimensions unchanged) once per
                              axis as a CUDA graph and replay it (default 1; off while timing and
                              on the legacy default stream, which cannot be captured) */
@@ -101,6 +104,11 @@ typedef struct hotrg_obs {
   double dlnz_dh;
   double internal_energy; /* <H>/N = -d(lnZ/N)/d beta */
   double magnetization;   /* <s> = (1/beta) d(lnZ/N)/d h */
+  /* with opts.impurities (NaN otherwise), the impure-tensor estimates Tr S^(n) / Tr T^(n):
+   * <s_i s_j> for a nearest-neighbour pair along the first step's axis (Eq. (energy); NaN
+   * before the first step) and <s_i> (Eq. (spin)) */
+  double nn_correlation;
+  double spin;
 } hotrg_obs;
 
 typedef struct hotrg_ctx hotrg_ctx;
@@ -155,7 +163,7 @@ int hotrg_get_tensor(hotrg_ctx *c, int instance, int *dims, double *host, size_t
 /* Replace the tensor of `instance` by a host array in natural layout with bond dimensions
  * dims[0..d) (each 1..Dcut). Used to coarse-grain arbitrary tensors. It does not normalise and
  * does not touch the ln Z accumulator; with opts.derivatives it zeroes the instance's tangents
- * (the supplied tensor does not depend on beta or h). Errors: EINVAL (also when prod dims
+ * (the supplied tensor does not depend on beta or h), with opts.impurities its impure tensors. Errors: EINVAL (also when prod dims
  * exceeds the largest P of the workspace plan, i.e. of the states reachable from T^(0) within
  * opts.max_steps steps). */
 int hotrg_set_tensor(hotrg_ctx *c, int instance, const int *dims, const double *host);

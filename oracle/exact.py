@@ -73,6 +73,33 @@ def moments_bruteforce(beta: float, h: float, L: tuple[int, ...]) -> tuple[float
     return float(np.dot(w, e_bond) / z / N), float(np.dot(w, e_field) / z / N)
 
 
+def pair_and_spin_bruteforce(beta: float, h: float, L: tuple[int, ...], axis: int) -> tuple[float, float]:
+    """(<s_0 s_{0 + e_axis}>, <s_0>) on the same periodic lattice as lnz_bruteforce, by
+    enumeration (site 0 is the origin; with L_axis = 1 the neighbour is the site itself)."""
+    L = tuple(int(x) for x in L)
+    N = int(np.prod(L))
+    if N > 20:
+        raise ValueError("enumeration limited to 20 spins")
+    sites = list(itertools.product(*[range(n) for n in L]))
+    index = {s: i for i, s in enumerate(sites)}
+    bonds = []
+    for s in sites:
+        for a, La in enumerate(L):
+            t = list(s)
+            t[a] = (t[a] + 1) % La
+            bonds.append((index[s], index[tuple(t)]))
+    cfg = ((np.arange(2 ** N)[:, None] >> np.arange(N)[None, :]) & 1).astype(np.int8)
+    spins = 1 - 2 * cfg.astype(np.float64)
+    i, j = np.array(bonds).T
+    expo = beta * np.sum(spins[:, i] * spins[:, j], axis=1) + beta * h * np.sum(spins, axis=1)
+    w = np.exp(expo - expo.max())
+    o = [0] * len(L)
+    nb = list(o)
+    nb[axis] = 1 % L[axis]
+    s0, s1 = spins[:, index[tuple(o)]], spins[:, index[tuple(nb)]]
+    return float(np.dot(w, s0 * s1) / w.sum()), float(np.dot(w, s0) / w.sum())
+
+
 def dlnz_1d(beta: float, h: float, N: int) -> tuple[float, float]:
     """(d/d beta, d/d h) of lnz_1d(beta, h, N) / N, differentiating the transfer-matrix
     eigenvalues: with q = (lam-/lam+)^N, d(ln Z)/N = (dlam+/lam+ + q dlam-/lam-) / (1 + q)."""

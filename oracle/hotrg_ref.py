@@ -368,6 +368,44 @@ def run(d: int, beta: float, h: float, Dcut: int, nsteps: int, order: list[int] 
     return flow
 
 
+@dataclass
+class ImpurityFlow:
+    nn: list[float] = field(default_factory=list)     # <s_i s_j> estimate after step n (n >= 1)
+    spin: list[float] = field(default_factory=list)   # <s_i> estimate after step n (n >= 0)
+
+
+def impurity_flow(d: int, beta: float, h: float, Dcut: int, nsteps: int,
+                  order: list[int] | None = None) -> ImpurityFlow:
+    """The impure-tensor estimates of Sec. 2, Eqs. (impTN), (SS), (ST), (energy), (spin).
+
+    Energy: impure tensors S^(0) (spin inserted) on two neighbouring sites, site 1 and its
+    neighbour along the first coarse-graining axis; step 1 merges the two (Eq. (SS)), every later
+    step merges the impure site 1 with a pure site 2 (Eq. (ST)). Magnetisation: one impure tensor,
+    merged with a pure site from step 1 on. The isometries are always the pure flow's; the impure
+    tensors are divided by the pure flow's norm c_n at every step, so the ratio
+    Tr S^(n) / Tr T^(n) (Eq. (tTr) on both) is the estimate of <s_i s_j> resp. <s_i>.
+    """
+    order = default_order(d) if order is None else list(order)
+    T = initial_tensor(d, beta, h)
+    S0 = initial_tensor(d, beta, h, spin_insertion=True)
+    c = frobenius(T)
+    T, SE, SM = T / c, S0 / c, S0 / c
+    out = ImpurityFlow()
+    out.spin.append(trace(SM) / trace(T))
+    for n in range(1, nsteps + 1):
+        a = order[(n - 1) % len(order)]
+        Tn, info = coarse_grain(T, a, Dcut)
+        U = {b: iso.U for b, iso in info.isometries.items()}
+        SEn = squeeze(SE, SE if n == 1 else T, a, U)
+        SMn = squeeze(SM, T, a, U)
+        c = frobenius(Tn)
+        T, SE, SM = Tn / c, SEn / c, SMn / c
+        tr = trace(T)
+        out.nn.append(trace(SE) / tr)
+        out.spin.append(trace(SM) / tr)
+    return out
+
+
 def fixed_isometry_derivatives(d: int, beta: float, h: float, Dcut: int, nsteps: int,
                                eps: float = 1e-3) -> tuple[np.ndarray, np.ndarray]:
     """d/d beta and d/d h of the ln Z_N / N estimate after every step 0..nsteps, with the

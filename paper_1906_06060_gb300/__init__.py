@@ -34,7 +34,7 @@ def _torch():
 
 
 def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0, kblock=0,
-          graphs=True, fold_group=0, derivatives=False):
+          graphs=True, fold_group=0, derivatives=False, impurities=False):
     lib = _lib.load()
     o = _lib.Opts()
     lib.hotrg_opts_default(byref(o))
@@ -46,14 +46,16 @@ def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=
     o.graphs = 1 if graphs else 0
     o.fold_group = int(fold_group)
     o.derivatives = _DERIV[derivatives] if isinstance(derivatives, str) else int(derivatives)
+    o.impurities = 1 if impurities else 0
     o.max_steps = int(max_steps)
     o.wait_timeout_s = float(wait_timeout_s)
     return o
 
 
 def workspace_bytes(d: int, Dcut: int, precision="fp64", batch: int = 1, fp64_steps: int = 2,
-                    max_steps: int = 64, x6_steps: int = 0, derivatives=False) -> int:
-    o = _opts(precision, batch, fp64_steps, max_steps, x6_steps=x6_steps, derivatives=derivatives)
+                    max_steps: int = 64, x6_steps: int = 0, derivatives=False, impurities=False) -> int:
+    o = _opts(precision, batch, fp64_steps, max_steps, x6_steps=x6_steps, derivatives=derivatives,
+              impurities=impurities)
     n = c_size_t(0)
     check(_lib.load().hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
     return int(n.value)
@@ -68,11 +70,14 @@ class HOTRG:
     derivatives: False / "none", True / "fixed" (isometries held fixed) or "eig" (exact derivative
     of the truncated flow, isometries differentiated through the eigendecomposition); the
     observables then carry d(lnZ/N)/d beta, d(lnZ/N)/d h, the internal energy and magnetisation.
+    impurities: also coarse-grain the impure tensors of Sec. 2; the observables then carry the
+    estimates <s_i s_j> (nn_correlation) and <s_i> (spin).
     """
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
                  max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0,
-                 kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives=False):
+                 kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives=False,
+                 impurities: bool = False):
         torch = _torch()
         lib = _lib.load()
         betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))
@@ -88,7 +93,7 @@ class HOTRG:
         self.beta = betas
         self.h = hs
         o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps, kblock, graphs, fold_group,
-                  derivatives)
+                  derivatives, impurities)
         n = c_size_t(0)
         check(lib.hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
         self.stream = stream if stream is not None else torch.cuda.current_stream()

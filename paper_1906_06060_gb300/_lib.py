@@ -17,14 +17,16 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("fp64_steps", c_int), ("x6_steps", c_int), ("batch", c_int),
                 ("beta", POINTER(c_double)), ("h", POINTER(c_double)), ("stream", c_void_p),
                 ("workspace", c_void_p), ("workspace_bytes", c_size_t), ("max_steps", c_int),
-                ("kblock", c_int), ("fold_group", c_int), ("derivatives", c_int), ("graphs", c_int),
+                ("kblock", c_int), ("fold_group", c_int), ("derivatives", c_int), ("impurities", c_int),
+                ("graphs", c_int),
                 ("wait_timeout_s", c_double)]
 
 
 class Obs(ctypes.Structure):
     _fields_ = [("steps", c_int), ("last_axis", c_int), ("lnz_per_site", c_double),
                 ("last_ln_c", c_double), ("x_indicator", c_double), ("dlnz_dbeta", c_double),
-                ("dlnz_dh", c_double), ("internal_energy", c_double), ("magnetization", c_double)]
+                ("dlnz_dh", c_double), ("internal_energy", c_double), ("magnetization", c_double),
+                ("nn_correlation", c_double), ("spin", c_double)]
 
 
 class Timing(ctypes.Structure):

@@ -62,6 +62,11 @@ struct hotrg_ctx {
   long long dg_stride = 0;
   void *Tt2 = nullptr, *dX1[2] = {nullptr, nullptr}, *dX2 = nullptr, *dO = nullptr;  // tangent squeeze scratch
   void *dR1 = nullptr, *dR2 = nullptr;
+  // impure tensors (Eqs. (SS), (ST)): [0] the nearest-neighbour pair, [1] the single spin
+  bool impure = false;
+  double *SI = nullptr;       // [2][batch][Pmax^2], normalised by the pure flow's c_n
+  double *Stmp = nullptr;     // [2][Pmax^2] unnormalised squeeze outputs (one instance at a time)
+  double *imp_out = nullptr;  // [2][batch] Tr S / Tr T
   long long q_stride = 0, g_stride = 0, u_stride = 0;  // per-instance strides (doubles)
   void *Tt = nullptr, *Bt = nullptr, *X1 = nullptr, *X2 = nullptr, *Y = nullptr, *O = nullptr;
   void *R1 = nullptr, *R2 = nullptr;
@@ -285,6 +290,11 @@ size_t carve(hotrg_ctx* c, char* base) {
     c->H2 = k.take<double>(sizeof(double) * c->q_stride * c->batch);
     c->dg_stride = (long long)nmax * nmax;
     c->dG = k.take<double>(sizeof(double) * c->dg_stride * c->batch);
+  }
+  if (c->impure) {
+    c->SI = k.take<double>(sizeof(double) * 2 * P2 * c->batch);
+    c->Stmp = k.take<double>(sizeof(double) * 2 * P2);
+    c->imp_out = k.take<double>(sizeof(double) * 2 * c->batch);
   }
   // with tangents the operands hold three column blocks per row (see squeeze)
   const size_t blk = c->deriv ? 3 : 1;
@@ -689,6 +699,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   c.max_steps = opt->max_steps;
   c.deriv = opt->derivatives != 0;
   c.deriv_mode = opt->derivatives;
+  c.impure = opt->impurities != 0;
   *bytes = carve(&c, nullptr);
   return HOTRG_OK;
 }
@@ -731,6 +742,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->graphs = opt->graphs != 0;
   c->deriv = opt->derivatives != 0;
   c->deriv_mode = opt->derivatives;
+  c->impure = opt->impurities != 0;
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
@@ -753,6 +765,8 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   cudaMemcpyAsync(c->dh, vh.data(), sizeof(double) * c->batch, cudaMemcpyHostToDevice, s);
   const long long P2 = c->Pmax * c->Pmax;
   launch_init_tensor(c->T, P2, c->batch, d, c->dbeta, c->dh, s);
+  if (c->impure)
+    for (int w = 0; w < 2; ++w) launch_init_tensor(c->SI + w * P2 * c->batch, P2, c->batch, d, c->dbeta, c->dh, s, 1);
   const long long n0 = 1LL << (2 * d);
   Geom g = make_geom(d, c->dims);
   if (c->deriv) {
@@ -770,8 +784,14 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
                             c->dL + w * c->batch + i, c->dstep, s);
       }
     launch_scale(Ti, Ti, n0, c->cval + i, s);
+    for (int w = 0; c->impure && w < 2; ++w) {
+      double* Si = c->SI + (w * c->batch + i) * P2;
+      launch_scale(Si, Si, n0, c->cval + i, s);
+    }
   }
   launch_trace_x(c->T, P2, c->batch, g, d - 1, c->L, c->dstep, c->out3, s);
+  for (int w = 0; c->impure && w < 2; ++w)
+    launch_trace_ratio(c->SI + w * P2 * c->batch, c->T, P2, c->batch, g.P, c->imp_out + w * c->batch, s);
   if (c->deriv)
     for (int w = 0; w < 2; ++w)
       launch_trace_tangent(c->T, c->dT + w * P2 * c->batch, P2, c->batch, g.P, c->dL + w * c->batch, c->dstep,
@@ -845,9 +865,19 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
         tg.dU[w] = c->deriv_mode == 2 ? c->dU + (w * c->batch + i) * c->u_stride : nullptr;
       }
     }
-    const int rc = planes ? squeeze<float>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass, tg)
-                          : squeeze<double>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0, tg);
+    int rc = planes ? squeeze<float>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass, tg)
+                    : squeeze<double>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0, tg);
     if (rc) return rc;
+    // impure tensors with the pure flow's isometries: the pair merges with itself at step 1
+    // (Eq. (SS)) and with a pure site after (Eq. (ST)); the single spin always with a pure site
+    for (int w = 0; c->impure && w < 2; ++w) {
+      const double* Si = c->SI + (w * c->batch + i) * P2max;
+      const double* partner = (w == 0 && step == 1) ? Si : Ti;
+      double* out = c->Stmp + w * P2max;
+      rc = planes ? squeeze<float>(c, Si, partner, out, Ui, g, gn, a, chi, trans, nt, planes, npass)
+                  : squeeze<double>(c, Si, partner, out, Ui, g, gn, a, chi, trans, nt, 0, 0);
+      if (rc) return rc;
+    }
     double* Tw = c->T + i * P2max;
     {
       PhaseScope norm_scope(c, PH_NORM);
@@ -861,8 +891,12 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
                           c->dlnc + w * c->batch + i, c->dL + w * c->batch + i, c->dstep, s);
     }
     launch_scale(c->Tnext, Tw, gn.P * gn.P, c->cval + i, s);
+    for (int w = 0; c->impure && w < 2; ++w)
+      launch_scale(c->Stmp + w * P2max, c->SI + (w * c->batch + i) * P2max, gn.P * gn.P, c->cval + i, s);
   }
   launch_trace_x(c->T, P2max, c->batch, gn, a, c->L, c->dstep, c->out3, s);
+  for (int w = 0; c->impure && w < 2; ++w)
+    launch_trace_ratio(c->SI + w * P2max * c->batch, c->T, P2max, c->batch, gn.P, c->imp_out + w * c->batch, s);
   if (c->deriv)
     for (int w = 0; w < 2; ++w)
       launch_trace_tangent(c->T, c->dT + w * P2max * c->batch, P2max, c->batch, gn.P, c->dL + w * c->batch,
@@ -986,6 +1020,16 @@ int hotrg_observables(hotrg_ctx* c, int instance, hotrg_obs* out) {
     out->internal_energy = -db;                 // <H>/N with H = -sum s s' - h sum s
     out->magnetization = dh / c->beta[instance];  // <s>
   }
+  out->nn_correlation = out->spin = std::nan("");
+  if (c->impure) {
+    double r[2] = {0.0, 0.0};
+    for (int w = 0; w < 2; ++w)
+      if (cudaMemcpy(r + w, c->imp_out + w * c->batch + instance, sizeof(double), cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+        return c->sticky = HOTRG_EDEVICE;
+    if (c->steps > 0) out->nn_correlation = r[0];  // the pair exists only after the first merge
+    out->spin = r[1];
+  }
   return HOTRG_OK;
 }
 
@@ -1056,6 +1100,11 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
     if (cudaMemsetAsync(c->dT + (w * c->batch + instance) * c->Pmax * c->Pmax, 0, sizeof(double) * g.P * g.P,
                         c->stream) != cudaSuccess)
       return c->sticky = HOTRG_EDEVICE;
+  // nor does it carry impurities: the impure estimates restart from zero
+  for (int w = 0; c->impure && w < 2; ++w)
+    if (cudaMemsetAsync(c->SI + (w * c->batch + instance) * c->Pmax * c->Pmax, 0, sizeof(double) * g.P * g.P,
+                        c->stream) != cudaSuccess)
+      return c->sticky = HOTRG_EDEVICE;
   for (int b = 0; b < c->d; ++b) c->dims[b] = dims[b];
   return HOTRG_OK;
 }
@@ -1063,7 +1112,7 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
 // ---- checkpoint format: header, then per instance T (P^2), L, lnc_log, spec_log, out3
 struct StateHeader {
   char magic[8];
-  int version, d, Dcut, batch, precision, max_steps, steps, last_axis, deriv;
+  int version, d, Dcut, batch, precision, max_steps, steps, last_axis, deriv, impure;
   int dims[kMaxD];
   long long P;
   int hist_dims[64][kMaxD];
@@ -1075,6 +1124,7 @@ struct StateHeader {
 size_t state_per_instance(const hotrg_ctx* c, long long P) {
   size_t n = (size_t)P * P + 1 + (c->max_steps + 1) + c->spec_stride + 3;
   if (c->deriv) n += 2 * ((size_t)P * P + 2);
+  if (c->impure) n += 2 * ((size_t)P * P + 1);
   return sizeof(double) * n;
 }
 
@@ -1094,7 +1144,8 @@ int hotrg_state_save(hotrg_ctx* c, void* host, size_t cap) {
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "HOTRGST", 8);
   h.version = 2;
-  h.deriv = c->deriv ? 1 : 0;
+  h.deriv = c->deriv ? c->deriv_mode : 0;
+  h.impure = c->impure ? 1 : 0;
   h.d = c->d; h.Dcut = c->Dcut; h.batch = c->batch; h.precision = c->precision;
   h.max_steps = c->max_steps; h.steps = c->steps; h.last_axis = c->last_axis;
   for (int b = 0; b < kMaxD; ++b) h.dims[b] = c->dims[b];
@@ -1128,6 +1179,14 @@ int hotrg_state_save(hotrg_ctx* c, void* host, size_t cap) {
       ok = ok && cudaMemcpy(p, c->dout + j, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess;
       p += sizeof(double);
     }
+    for (int w = 0; c->impure && w < 2; ++w) {
+      const long long j = w * c->batch + i;
+      ok = ok && cudaMemcpy(p, c->SI + j * c->Pmax * c->Pmax, sizeof(double) * g.P * g.P,
+                            cudaMemcpyDeviceToHost) == cudaSuccess;
+      p += sizeof(double) * g.P * g.P;
+      ok = ok && cudaMemcpy(p, c->imp_out + j, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess;
+      p += sizeof(double);
+    }
     if (!ok) return c->sticky = HOTRG_EDEVICE;
   }
   return HOTRG_OK;
@@ -1139,7 +1198,7 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
   std::memcpy(&h, host, sizeof(h));
   if (std::memcmp(h.magic, "HOTRGST", 8) || h.version != 2 || h.d != c->d || h.Dcut != c->Dcut ||
       h.batch != c->batch || h.precision != c->precision || h.max_steps != c->max_steps ||
-      h.deriv != (c->deriv ? 1 : 0))
+      h.deriv != (c->deriv ? c->deriv_mode : 0) || h.impure != (c->impure ? 1 : 0))
     return HOTRG_EINVAL;
   Geom g = make_geom(h.d, h.dims);
   if (g.P != h.P || g.P > c->Pmax) return HOTRG_EINVAL;
@@ -1167,6 +1226,14 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
       ok = ok && cudaMemcpy(c->dL + j, p, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
       p += sizeof(double);
       ok = ok && cudaMemcpy(c->dout + j, p, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+      p += sizeof(double);
+    }
+    for (int w = 0; c->impure && w < 2; ++w) {
+      const long long j = w * c->batch + i;
+      ok = ok && cudaMemcpy(c->SI + j * c->Pmax * c->Pmax, p, sizeof(double) * g.P * g.P,
+                            cudaMemcpyHostToDevice) == cudaSuccess;
+      p += sizeof(double) * g.P * g.P;
+      ok = ok && cudaMemcpy(c->imp_out + j, p, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
       p += sizeof(double);
     }
     if (!ok) return c->sticky = HOTRG_EDEVICE;

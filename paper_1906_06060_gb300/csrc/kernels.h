@@ -11,9 +11,10 @@ void count_launches(int n);
 long long launches_total();
 
 // ---- kernels_tensor.cu --------------------------------------------------------------------
-// T^(0) (Sec. 2) for `batch` instances: T + i*stride gets beta[i], h[i] (device arrays).
+// T^(0) (Sec. 2) for `batch` instances: T + i*stride gets beta[i], h[i] (device arrays). With
+// spin_insertion, the impure tensor S^(0) (the summand carries the spin s).
 void launch_init_tensor(double* T, long long inst_stride, int batch, int d, const double* beta,
-                        const double* h, cudaStream_t s);
+                        const double* h, cudaStream_t s, int spin_insertion = 0);
 // *dstep += 1 (device-side step counter read by the kernels below, so that a captured step
 // can be replayed for any step number).
 void launch_step_advance(int* dstep, cudaStream_t s);
@@ -32,6 +33,9 @@ void launch_tangent_norm(const double* T, const double* D1, const double* D2, do
 // out[i] = dL[i] + 2^-n Tr dT_i / Tr T_i for every instance.
 void launch_trace_tangent(const double* T, const double* dT, long long t_stride, int batch, long long P,
                           const double* dL, const int* dstep, double* out, cudaStream_t s);
+// out[i] = Tr S_i / Tr T_i (Eqs. (energy), (spin)) for every instance.
+void launch_trace_ratio(const double* S, const double* T, long long t_stride, int batch, long long P, double* out,
+                        cudaStream_t s);
 // dst = src / *c
 void launch_scale(const double* src, double* dst, long long n, const double* c, cudaStream_t s);
 // Tr T (Eq. (tTr)) and ln Z/N = L + 2^-n ln Tr (n = *dstep); X^(n) along `axis` (Eq. (x)).

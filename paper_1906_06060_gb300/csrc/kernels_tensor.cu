@@ -30,7 +30,7 @@ constexpr int kNormBlocks = 1024;
 // T[idx] = sum_s V_s prod_{legs} W[s, leg]; W[s,0] = sqrt(cosh b), W[s,1] = s sqrt(sinh b),
 // V_s = e^{b h s}; bit l of idx (from the most significant) is the index of leg l.
 __global__ void k_init_tensor(double* T, long long inst_stride, int d, const double* beta,
-                              const double* hfield) {
+                              const double* hfield, int spin_insertion) {
   const int nlegs = 2 * d;
   const int total = 1 << nlegs;
   const int inst = blockIdx.y;
@@ -46,7 +46,7 @@ __global__ void k_init_tensor(double* T, long long inst_stride, int d, const dou
       const int bit = (idx >> (nlegs - 1 - l)) & 1;
       v *= bit ? s * ws : wc;
     }
-    acc += v;
+    acc += spin_insertion ? s * v : v;
   }
   T[inst * inst_stride + idx] = acc;
 }
@@ -183,6 +183,22 @@ __global__ void __launch_bounds__(256) k_trace_tangent(const double* __restrict_
   const double ta = block_sum<256>(a, sh);
   const double tb = block_sum<256>(b, sh);
   if (threadIdx.x == 0) out[blockIdx.x] = dL[blockIdx.x] + ldexp(tb / ta, -*dstep);
+}
+
+// out[i] = Tr S_i / Tr T_i for every instance (one CTA each): Eqs. (energy), (spin).
+__global__ void __launch_bounds__(256) k_trace_ratio(const double* __restrict__ S, const double* __restrict__ T,
+                                                     long long t_stride, long long P, double* out) {
+  __shared__ double sh[256];
+  S += (long long)blockIdx.x * t_stride;
+  T += (long long)blockIdx.x * t_stride;
+  double a = 0.0, b = 0.0;
+  for (long long u = threadIdx.x; u < P; u += 256) {
+    a += S[u * P + u];
+    b += T[u * P + u];
+  }
+  const double ta = block_sum<256>(a, sh);
+  const double tb = block_sum<256>(b, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = ta / tb;
 }
 
 __global__ void k_scale(const double* __restrict__ src, double* __restrict__ dst, long long n,
@@ -471,10 +487,10 @@ __global__ void __launch_bounds__(256) k_pair_contract_all(const Tin* __restrict
 
 // ============================================================================ launchers
 void launch_init_tensor(double* T, long long inst_stride, int batch, int d, const double* beta,
-                        const double* h, cudaStream_t s) {
+                        const double* h, cudaStream_t s, int spin_insertion) {
   const int total = 1 << (2 * d);
   dim3 grid((total + 255) / 256, batch);
-  k_init_tensor<<<grid, 256, 0, s>>>(T, inst_stride, d, beta, h);
+  k_init_tensor<<<grid, 256, 0, s>>>(T, inst_stride, d, beta, h, spin_insertion);
   count_launches(1);
 }
 
@@ -512,6 +528,12 @@ void launch_tangent_norm(const double* T, const double* D1, const double* D2, do
 void launch_trace_tangent(const double* T, const double* dT, long long t_stride, int batch, long long P,
                           const double* dL, const int* dstep, double* out, cudaStream_t s) {
   k_trace_tangent<<<batch, 256, 0, s>>>(T, dT, t_stride, P, dL, dstep, out);
+  count_launches(1);
+}
+
+void launch_trace_ratio(const double* S, const double* T, long long t_stride, int batch, long long P, double* out,
+                        cudaStream_t s) {
+  k_trace_ratio<<<batch, 256, 0, s>>>(S, T, t_stride, P, out);
   count_launches(1);
 }
 

@@ -7,7 +7,8 @@ dimensions, ln c_n, the ln Z/N estimate, X^(n), the cut gaps and the leading Gra
 (normalised by the largest eigenvalue). A flow whose cut splits a degenerate multiplet
 (gap < 1e-10) is cut-ambiguous from that step on; the file records the first such step.
 
-The deriv_* files record d(ln Z/N)/d beta and d(ln Z/N)/d h after every step with the isometries
+The impurity_* files record the impure-tensor estimates after every step
+(oracle.hotrg_ref.impurity_flow). The deriv_* files record d(ln Z/N)/d beta and d(ln Z/N)/d h after every step with the isometries
 frozen (oracle.hotrg_ref.fixed_isometry_derivatives).
 
     python tests/golden/make_golden.py [name ...]     # only the named files
@@ -36,6 +37,11 @@ DERIV_CONFIGS = {
     # 4D, Dcut = 5, 8 steps: near the transition at h = 0, and with a field of 0.01
     "deriv_d4_b0.1497_h0_D5_n8": dict(d=4, beta=0.1497, h=0.0, Dcut=5, nsteps=8),
     "deriv_d4_b0.16_h0.01_D5_n8": dict(d=4, beta=0.16, h=0.01, Dcut=5, nsteps=8),
+}
+
+IMPURITY_CONFIGS = {
+    # impure-tensor estimates <s_i s_j>, <s_i> (Eqs. (energy), (spin)), 4D Dcut = 5, 8 steps
+    "impurity_d4_b0.16_h0.01_D5_n8": dict(d=4, beta=0.16, h=0.01, Dcut=5, nsteps=8),
 }
 
 AMBIGUOUS_GAP = 1e-10
@@ -71,8 +77,21 @@ def deriv_record(cfg):
                        "flow_derivatives() (eps = 1e-4), FP64 central differences, Richardson")
 
 
+def impurity_record(cfg):
+    f = R.impurity_flow(**cfg)
+    return dict(config=cfg, nn=[float(x) for x in f.nn], spin=[float(x) for x in f.spin],
+                source="oracle/hotrg_ref.py impurity_flow(), FP64")
+
+
 def main():
     only = set(sys.argv[1:])
+    for name, cfg in IMPURITY_CONFIGS.items():
+        if only and name not in only:
+            continue
+        rec = impurity_record(cfg)
+        with open(os.path.join(HERE, name + ".json"), "w") as fh:
+            json.dump(rec, fh, indent=1)
+        print(name, rec["nn"][-1], rec["spin"][-1])
     for name, cfg in DERIV_CONFIGS.items():
         if only and name not in only:
             continue

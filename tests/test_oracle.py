@@ -333,3 +333,49 @@ def test_flow_and_fixed_isometry_derivatives_differ_by_truncation_terms():
     assert abs(fb[0] - xb[0]) < 1e-10           # T^(0): nothing truncated yet
     for n in (2, 3, 4):
         assert abs(fb[n] - xb[n]) > 1e-3 and abs(fh[n] - xh[n]) > 1e-6
+
+
+# ------------------------------------------------------------------ impure tensors (Eqs. (impTN)-(spin))
+@pytest.mark.parametrize("beta,h", [(0.4407, 0.05), (0.3, 0.0)])
+def test_impurity_flow_2d_lossless_matches_enumeration(beta, h):
+    """Without truncation Eqs. (energy), (spin) are exact on the 2^n-site lattice: the pair sits
+    along the first coarse-graining axis (axis 1 in 2D)."""
+    f = R.impurity_flow(2, beta, h, 16, 4)
+    for n, L in ((1, (1, 2)), (2, (2, 2)), (3, (2, 4)), (4, (4, 4))):
+        pe, ps = E.pair_and_spin_bruteforce(beta, h, L, 1)
+        assert abs(f.nn[n - 1] - pe) < 1e-13
+        assert abs(f.spin[n] - ps) < 1e-13
+
+
+def test_impurity_flow_4d_lossless_matches_enumeration():
+    beta, h = 0.3, 0.01
+    f = R.impurity_flow(4, beta, h, 16, 2)
+    for n, L in ((1, (1, 1, 1, 2)), (2, (1, 1, 2, 2))):
+        pe, ps = E.pair_and_spin_bruteforce(beta, h, L, 3)
+        assert abs(f.nn[n - 1] - pe) < 1e-13 and abs(f.spin[n] - ps) < 1e-13
+
+
+def test_pair_and_spin_bruteforce_consistent_with_moments():
+    """On an isotropic lattice d <s s'> along one axis + h <s> is d(lnZ/N)/d beta."""
+    beta, h, L = 0.35, 0.02, (2, 2, 2, 2)
+    pe, ps = E.pair_and_spin_bruteforce(beta, h, L, 0)
+    e, m = E.moments_bruteforce(beta, h, L)
+    # N d bonds (with L = 2 each neighbour pair is joined twice), each with mean <s s'>
+    assert abs(e - 4 * pe) < 1e-13 and abs(m - ps) < 1e-14
+
+
+def test_impurity_flow_symmetries_and_a_planted_mistake():
+    """<s> = 0 at h = 0 (Z2) at every step; merging the energy impurity with a pure tensor at
+    step 1 (instead of with the second impurity, Eq. (SS)) fails the enumeration pin."""
+    f = R.impurity_flow(4, 0.1497, 0.0, 3, 6)
+    assert max(abs(x) for x in f.spin) < 1e-15
+    assert all(0 < x < 1 for x in f.nn)
+    beta, h = 0.4407, 0.05
+    good = R.impurity_flow(2, beta, h, 16, 1).nn[0]
+    T0 = R.initial_tensor(2, beta, h)
+    S0 = R.initial_tensor(2, beta, h, spin_insertion=True)
+    _, info = R.coarse_grain(T0, 1, 16)
+    U = {b: iso.U for b, iso in info.isometries.items()}
+    bad = R.trace(R.squeeze(S0, T0, 1, U)) / R.trace(R.squeeze(T0, T0, 1, U))
+    pe, _ = E.pair_and_spin_bruteforce(beta, h, (1, 2), 1)
+    assert abs(good - pe) < 1e-13 and abs(bad - pe) > 1e-3
