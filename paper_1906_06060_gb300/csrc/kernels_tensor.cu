@@ -456,27 +456,25 @@ __global__ void __launch_bounds__(256) k_pair_contract_all(const Tin* __restrict
     Acc acc[kMaxChi];
 #pragma unroll
     for (int k = 0; k < kMaxChi; ++k) acc[k] = 0;
-    for (int i = 0; i < Di; ++i) {
-      const Tin* src = in + ioff + i * si;
-      for (int j = 0; j < Dj; ++j) {
-        const Acc x = (Acc)src[j * sj];
-        const Acc* w = W + (i * Dj + j) * chi;
-#pragma unroll
-        for (int k = 0; k < kMaxChi; ++k)
-          if (k < chi) acc[k] += w[k] * x;
-      }
-    }
-    if (TWO)
+    // one row of Dj loads issued before its FMAs (bytes in flight to stream HBM)
+    for (int pass = 0; pass < (TWO ? 2 : 1); ++pass) {
+      const Tin* base_in = pass ? in2 : in;
+      const Acc* Wp = pass ? W2 : W;
       for (int i = 0; i < Di; ++i) {
-        const Tin* src = in2 + ioff + i * si;
-        for (int j = 0; j < Dj; ++j) {
-          const Acc x = (Acc)src[j * sj];
-          const Acc* w = W2 + (i * Dj + j) * chi;
+        const Tin* src = base_in + ioff + i * si;
+        Acc x[kMaxBond];
+#pragma unroll
+        for (int j = 0; j < kMaxBond; ++j) x[j] = j < Dj ? (Acc)src[j * sj] : (Acc)0;
+#pragma unroll
+        for (int j = 0; j < kMaxBond; ++j) {
+          if (j >= Dj) break;
+          const Acc* w = Wp + (i * Dj + j) * chi;
 #pragma unroll
           for (int k = 0; k < kMaxChi; ++k)
-            if (k < chi) acc[k] += w[k] * x;
+            if (k < chi) acc[k] += w[k] * x[j];
         }
       }
+    }
 #pragma unroll
     for (int k = 0; k < kMaxChi; ++k)
       if (k < chi) out[ooff + k * sk] = (Tout)acc[k];
