@@ -84,6 +84,13 @@ typedef struct hotrg_opts {
   int impurities;         /* 1: also coarse-grain the impure tensors of Sec. 2 (Eqs. (impTN),
                              (SS), (ST)) with the pure flow's isometries and report the
                              estimates of Eqs. (energy) and (spin): two extra squeezes per step */
+  int z2;                 /* 1: zero-field block-sparse squeeze: at h = 0 every tensor entry whose
+                             legs' spin-flip parities add up to odd vanishes, and the split-
+                             precision squeeze computes only the two nonzero GEMM blocks per
+                             chunk (a quarter of the dense flops); bond indices are then
+                             ordered even-parity first. Needs h = 0 for every instance, d >= 2,
+                             no derivatives and no impurities (EINVAL otherwise); set_tensor
+                             turns it off. */
   int graphs;             /* 1: capture a steady-state step (bond dimensions unchanged) once per
                              axis as a CUDA graph and replay it (default 1; off while timing and
                              on the legacy default stream, which cannot be captured) */
@@ -191,7 +198,9 @@ typedef struct hotrg_timing {
   long long kernel_launches;/* all library kernels launched in this process since start */
   double gemm_flops;        /* algorithmic flops of those GEMMs, 2 M N K each */
   double gemm_tensor_flops; /* flops the tensor pipe executed (x 3 or x 6 split passes) */
-  double step_flops;        /* algorithmic squeeze flops of the steps, 2 prod(chi_b) P^3 */
+  double step_flops;        /* algorithmic squeeze flops of the steps, 2 prod(chi_b) P^3; with
+                               opts.z2, what the parity blocks compute (about a quarter) */
+  double dense_step_flops;  /* 2 prod(chi_b) P^3 per step, also with opts.z2 */
 } hotrg_timing;
 
 int hotrg_timing_start(hotrg_ctx *c);

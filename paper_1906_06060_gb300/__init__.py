@@ -34,7 +34,7 @@ def _torch():
 
 
 def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0, kblock=0,
-          graphs=True, fold_group=0, derivatives=False, impurities=False):
+          graphs=True, fold_group=0, derivatives=False, impurities=False, z2=False):
     lib = _lib.load()
     o = _lib.Opts()
     lib.hotrg_opts_default(byref(o))
@@ -47,15 +47,17 @@ def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=
     o.fold_group = int(fold_group)
     o.derivatives = _DERIV[derivatives] if isinstance(derivatives, str) else int(derivatives)
     o.impurities = 1 if impurities else 0
+    o.z2 = 1 if z2 else 0
     o.max_steps = int(max_steps)
     o.wait_timeout_s = float(wait_timeout_s)
     return o
 
 
 def workspace_bytes(d: int, Dcut: int, precision="fp64", batch: int = 1, fp64_steps: int = 2,
-                    max_steps: int = 64, x6_steps: int = 0, derivatives=False, impurities=False) -> int:
+                    max_steps: int = 64, x6_steps: int = 0, derivatives=False, impurities=False,
+                    z2=False) -> int:
     o = _opts(precision, batch, fp64_steps, max_steps, x6_steps=x6_steps, derivatives=derivatives,
-              impurities=impurities)
+              impurities=impurities, z2=z2)
     n = c_size_t(0)
     check(_lib.load().hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
     return int(n.value)
@@ -72,12 +74,13 @@ class HOTRG:
     observables then carry d(lnZ/N)/d beta, d(lnZ/N)/d h, the internal energy and magnetisation.
     impurities: also coarse-grain the impure tensors of Sec. 2; the observables then carry the
     estimates <s_i s_j> (nn_correlation) and <s_i> (spin).
+    z2: zero-field block-sparse squeeze (h = 0 only; see include/hotrg.h).
     """
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
                  max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0,
                  kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives=False,
-                 impurities: bool = False):
+                 impurities: bool = False, z2: bool = False):
         torch = _torch()
         lib = _lib.load()
         betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))
@@ -93,7 +96,7 @@ class HOTRG:
         self.beta = betas
         self.h = hs
         o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps, kblock, graphs, fold_group,
-                  derivatives, impurities)
+                  derivatives, impurities, z2)
         n = c_size_t(0)
         check(lib.hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
         self.stream = stream if stream is not None else torch.cuda.current_stream()

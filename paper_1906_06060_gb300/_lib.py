@@ -18,7 +18,7 @@ class Opts(ctypes.Structure):
                 ("beta", POINTER(c_double)), ("h", POINTER(c_double)), ("stream", c_void_p),
                 ("workspace", c_void_p), ("workspace_bytes", c_size_t), ("max_steps", c_int),
                 ("kblock", c_int), ("fold_group", c_int), ("derivatives", c_int), ("impurities", c_int),
-                ("graphs", c_int),
+                ("z2", c_int), ("graphs", c_int),
                 ("wait_timeout_s", c_double)]
 
 
@@ -33,7 +33,8 @@ class Timing(ctypes.Structure):
     _fields_ = [("ms_step", c_double), ("ms_isometry", c_double), ("ms_operands", c_double),
                 ("ms_gemm", c_double), ("ms_epilogue", c_double), ("ms_norm", c_double),
                 ("steps", c_longlong), ("gemm_launches", c_longlong), ("kernel_launches", c_longlong),
-                ("gemm_flops", c_double), ("gemm_tensor_flops", c_double), ("step_flops", c_double)]
+                ("gemm_flops", c_double), ("gemm_tensor_flops", c_double), ("step_flops", c_double),
+                ("dense_step_flops", c_double)]
 
 
 class Tuning(ctypes.Structure):

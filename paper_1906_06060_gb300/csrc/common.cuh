@@ -19,6 +19,7 @@ enum : int {
   ST_NOCONV = 2,    // eigensolver sweep limit reached
   ST_TIMEOUT = 4,   // bounded wait gave up
   ST_BOUNDS = 8,    // internal index check failed
+  ST_Z2 = 16,       // zero-field block structure broken (an eigenvector is not parity-pure)
 };
 
 // Geometry of a site tensor in natural layout T[u_0..u_{d-1}, p_0..p_{d-1}].

@@ -31,7 +31,8 @@ __device__ void sm_red_sum(double* sred, double v, int tid) {
 __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict__ G, long long g_stride, int n,
                                                         int chi, EigOut o, double* __restrict__ Uout,
                                                         long long u_stride, double* __restrict__ work,
-                                                        int* status) {
+                                                        int* status, const int* z2_ev, int* z2_ev_new,
+                                                        int z2_axis, int Db) {
   extern __shared__ double sm[];
   G += (long long)blockIdx.x * g_stride;
   Uout += (long long)blockIdx.x * u_stride;
@@ -148,6 +149,47 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict
     for (int k = tid; k < n; k += kEigThreads) evals[k] = lam[perm[k]];
   // sign-fixed eigenvectors: one warp per kept vector
   const int warp = tid / 32, lane = tid % 32;
+  // zero-field block structure: parity of fused index r = (b1, b2) of this axis
+  const int ez = z2_ev ? z2_ev[blockIdx.x * kMaxD + z2_axis] : 0;
+  auto rpar = [&](int r) { return ((r / Db) >= ez ? 1 : 0) ^ ((r % Db) >= ez ? 1 : 0); };
+  int* kpar = reinterpret_cast<int*>(sc);       // [chi] parity of kept vector k (sc, ss, st are free)
+  int* kpos = reinterpret_cast<int*>(ss);       // [chi] its output row
+  for (int k = warp; k < chi; k += kEigThreads / 32) {
+    const int col = perm[k];
+    double best = -1.0;
+    int bidx = n;
+    for (int r = lane; r < n; r += 32) {
+      const double a = fabs(V[(long long)r * n + col]);
+      if (a > best) { best = a; bidx = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if (z2_ev) {
+      // the vector must live in one parity sector: the other sector's weight is exactly zero
+      const int pk = rpar(bidx);
+      double bad = 0.0;
+      for (int r = lane; r < n; r += 32)
+        if (rpar(r) != pk) bad += V[(long long)r * n + col] * V[(long long)r * n + col];
+      for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+      if (lane == 0) {
+        kpar[k] = pk;
+        if (bad > 1e-24) atomic_status(status, ST_Z2);
+      }
+    }
+  }
+  __syncthreads();
+  if (z2_ev && tid == 0) {
+    // even vectors first, each group in descending eigenvalue order
+    int ne = 0;
+    for (int k = 0; k < chi; ++k) ne += kpar[k] == 0;
+    int ie = 0, io = ne;
+    for (int k = 0; k < chi; ++k) kpos[k] = kpar[k] == 0 ? ie++ : io++;
+    z2_ev_new[blockIdx.x * kMaxD + z2_axis] = ne;
+  }
+  __syncthreads();
   for (int k = warp; k < chi; k += kEigThreads / 32) {
     const int col = perm[k];
     double best = -1.0;
@@ -162,7 +204,8 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict
       if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
     }
     const double sgn = V[(long long)bidx * n + col] < 0 ? -1.0 : 1.0;
-    for (int r = lane; r < n; r += 32) Uout[(long long)k * n + r] = sgn * V[(long long)r * n + col];
+    const int row = z2_ev ? kpos[k] : k;
+    for (int r = lane; r < n; r += 32) Uout[(long long)row * n + r] = sgn * V[(long long)r * n + col];
   }
 }
 
@@ -251,9 +294,11 @@ void prepare_eig_attributes() {
 }
 
 void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o, double* U,
-                long long u_stride, double* work, int* status, cudaStream_t s) {
+                long long u_stride, double* work, int* status, cudaStream_t s, const int* z2_ev, int* z2_ev_new,
+                int z2_axis, int Db) {
   const size_t smem = sizeof(double) * (128 + 128 + 128 + 128 + kEigThreads);
-  k_jacobi<<<batch, kEigThreads, smem, s>>>(G, g_stride, n, chi, o, U, u_stride, work, status);
+  k_jacobi<<<batch, kEigThreads, smem, s>>>(G, g_stride, n, chi, o, U, u_stride, work, status, z2_ev, z2_ev_new,
+                                            z2_axis, Db > 0 ? Db : 1);
   count_launches(1);
 }
 

@@ -94,7 +94,44 @@ struct TcParams {
   int* status;
   unsigned long long timeout_ns;
   int vec4;
+  const GemmBlocks* blk;  // null: one dense product over M x N x K
 };
+
+// One output block of the product as the kernel sees it (clamped to the operand extents).
+struct Blk {
+  int m0, mc, n0, nc, k0, num_m, num_n, num_kb, tiles;
+};
+
+// The (at most two) blocks of this launch: from the device descriptor of a block-sparse
+// product, or the single dense block. Thread 0 fills shared memory before the CTA's first barrier.
+template <int BK>
+__device__ __forceinline__ int load_blocks(const TcParams& p, Blk* b) {
+  int nb = 1;
+  if (p.blk) {
+    nb = min(max(p.blk->nb, 0), 2);
+    for (int i = 0; i < nb; ++i) {
+      const long long m0 = max(p.blk->m0[i], 0), n0 = max(p.blk->n0[i], 0), k0 = max(p.blk->k0[i], 0);
+      b[i].m0 = (int)min(m0, p.M);
+      b[i].n0 = (int)min(n0, p.N);
+      b[i].k0 = (int)min(k0, p.K);
+      b[i].mc = (int)min((long long)max(p.blk->mc[i], 0), p.M - b[i].m0);
+      b[i].nc = (int)min((long long)max(p.blk->nc[i], 0), p.N - b[i].n0);
+      const int kc = (int)min((long long)max(p.blk->kc[i], 0), p.K - b[i].k0);
+      b[i].num_kb = (kc + BK - 1) / BK;
+    }
+  } else {
+    b[0].m0 = b[0].n0 = b[0].k0 = 0;
+    b[0].mc = (int)p.M;
+    b[0].nc = (int)p.N;
+    b[0].num_kb = p.num_kb;
+  }
+  for (int i = 0; i < nb; ++i) {
+    b[i].num_m = (b[i].mc + TC_BM - 1) / TC_BM;
+    b[i].num_n = (b[i].nc + TC_BN - 1) / TC_BN;
+    b[i].tiles = b[i].num_m * b[i].num_n;
+  }
+  return nb;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -201,6 +238,14 @@ __device__ __forceinline__ void raster(int tile, int num_m, int num_n, int group
   nt = local / gsz;
 }
 
+// Tile -> (block, M-tile, N-tile): the blocks' tiles are numbered one after the other.
+__device__ __forceinline__ const Blk& tile_of(const Blk* b, int tile, int group_m, int& mt, int& nt) {
+  const int bi = tile < b[0].tiles ? 0 : 1;
+  const Blk& k = b[bi];
+  raster(bi ? tile - b[0].tiles : tile, k.num_m, k.num_n, group_m, mt, nt);
+  return k;
+}
+
 template <int BK, int NPL, int NPASS, int FG>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_split(const __grid_constant__ TmapSet maps, TcParams p) {
@@ -227,7 +272,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tempty0 = tfull0 + 16;
   const uint32_t final_bar = tempty0 + 16;
 
+  __shared__ Blk blks[2];
+  __shared__ int s_total;
   if (threadIdx.x == 0) {
+    const int nb = load_blocks<BK>(p, blks);
+    s_total = blks[0].tiles + (nb > 1 ? blks[1].tiles : 0);
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
@@ -255,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int total = p.num_m * p.num_n;
+  const int total = s_total;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -265,15 +314,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
         int mt, nt;
-        raster(tile, p.num_m, p.num_n, p.group_m, mt, nt);
-        for (int kb = 0; kb < p.num_kb; ++kb) {
+        const Blk& bk = tile_of(blks, tile, p.group_m, mt, nt);
+        for (int kb = 0; kb < bk.num_kb; ++kb) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.timeout_ns)) { ok = false; break; }
           const uint32_t fb = full0 + 8 * stage;
           mbar_expect_tx(fb, STAGE_BYTES);
+          const int kx = bk.k0 + kb * TC_BK;
 #pragma unroll
           for (int pl = 0; pl < NPL; ++pl) {
-            tma_load_2d(smem_u32(a_tile(stage, pl)), &maps.a[pl], fb, kb * TC_BK, mt * TC_BM);
-            tma_load_2d(smem_u32(b_tile(stage, pl)), &maps.b[pl], fb, kb * TC_BK, nt * TC_BN);
+            tma_load_2d(smem_u32(a_tile(stage, pl)), &maps.a[pl], fb, kx, bk.m0 + mt * TC_BM);
+            tma_load_2d(smem_u32(b_tile(stage, pl)), &maps.b[pl], fb, kx, bk.n0 + nt * TC_BN);
           }
           ++issued;
           if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
@@ -294,6 +344,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t bphase = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+        int mt_, nt_;
+        const int num_kb = tile_of(blks, tile, p.group_m, mt_, nt_).num_kb;
         // Descriptors differ only in their start-address field (bits 0-13, address >> 4), so each
         // one is a base descriptor plus the tile's byte offset >> 4 (all offsets are multiples of
         // 16 bytes and the shared window is < 256 KB, so the field never carries over). Passes,
@@ -301,8 +353,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // issue code with constant offsets.
         const uint64_t desc_base = smem_desc<BK>(smem_u32(smem));
         constexpr uint32_t B_OFF = NPL * A_TILE;
-        for (int kb0 = 0; kb0 < p.num_kb && ok; kb0 += FG) {
-          const int g = min(FG, p.num_kb - kb0);  // k-blocks in this fold group
+        for (int kb0 = 0; kb0 < num_kb && ok; kb0 += FG) {
+          const int g = min(FG, num_kb - kb0);  // k-blocks in this fold group
           if (!mbar_wait(tempty0 + 8 * buf, bphase ^ 1, abort_flag, p.timeout_ns)) { ok = false; break; }
           uint32_t so[FG];  // byte offsets of the group's stages
           {
@@ -352,11 +404,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = true;
     for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
       int mt, nt;
-      raster(tile, p.num_m, p.num_n, p.group_m, mt, nt);
+      const Blk& bk = tile_of(blks, tile, p.group_m, mt, nt);
       float acc[128];
 #pragma unroll
       for (int j = 0; j < 128; ++j) acc[j] = 0.f;
-      for (int kb = 0; kb < p.num_kb; kb += FG) {
+      for (int kb = 0; kb < bk.num_kb; kb += FG) {
         // one lane waits for the fold group's MMAs, the warp follows it
         int w = 1;
         if (lane == 0) w = mbar_wait(tfull0 + 8 * buf, bphase, abort_flag, p.timeout_ns) ? 1 : 0;
@@ -382,18 +434,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (++buf == 2) { buf = 0; bphase ^= 1; }
       }
       if (!ok) break;
-      const long long row = (long long)mt * TC_BM + q * 32 + lane;
-      const long long col0 = (long long)nt * TC_BN + half * 128;
-      if (row < p.M && col0 < p.N) {
+      const long long row = (long long)bk.m0 + (long long)mt * TC_BM + q * 32 + lane;
+      const long long col0 = (long long)bk.n0 + (long long)nt * TC_BN + half * 128;
+      const long long row_end = (long long)bk.m0 + bk.mc, col_end = (long long)bk.n0 + bk.nc;
+      if (row < row_end && col0 < col_end) {
         float* dst = p.C + row * p.ldc + col0;
-        if (p.vec4 && col0 + 128 <= p.N) {
+        if (p.vec4 && (bk.n0 & 3) == 0 && col0 + 128 <= col_end) {
 #pragma unroll
           for (int j = 0; j < 128; j += 4)
             *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
         } else {
 #pragma unroll
           for (int j = 0; j < 128; ++j)
-            if (col0 + j < p.N) dst[j] = acc[j];
+            if (col0 + j < col_end) dst[j] = acc[j];
         }
       }
     }
@@ -490,7 +543,7 @@ int num_sms() {
 int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
                       int npass, int* status, double timeout_s, cudaStream_t s, int bk, int group_m,
-                      int fold_group) {
+                      int fold_group, const GemmBlocks* blk) {
   if (bk != 32 && bk != 64) return HOTRG_EINVAL;
   if (group_m < 1 || group_m > 64 || fold_group < 1) return HOTRG_EINVAL;
   if (M < TC_BM || N < TC_BN || K < 64 || (npass != 1 && npass != 3 && npass != 4 && npass != 6))
@@ -518,9 +571,11 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
   p.status = status;
   p.timeout_ns = (unsigned long long)(timeout_s * 1e9);
   p.vec4 = ((ldc % 4) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+  p.blk = blk;
   const long long tiles = (long long)p.num_m * p.num_n;
   if (tiles > 0x7fffffffLL) return HOTRG_EINVAL;
-  const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
+  // with device-side blocks the tile count is known only on the device: one CTA per SM
+  const int grid = blk ? num_sms() : (int)(tiles < num_sms() ? tiles : num_sms());
   // supported variants (fold groups beyond a variant's maximum are clamped to it)
   const int fg = std::max(1, std::min(fold_group, max_fold_group(npass, bk)));
   int rc = HOTRG_EINVAL;

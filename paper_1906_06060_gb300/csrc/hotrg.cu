@@ -62,6 +62,15 @@ struct hotrg_ctx {
   long long dg_stride = 0;
   void *Tt2 = nullptr, *dX1[2] = {nullptr, nullptr}, *dX2 = nullptr, *dO = nullptr;  // tangent squeeze scratch
   void *dR1 = nullptr, *dR2 = nullptr;
+  // zero-field block structure (z2.cu): even-value counts of every leg, before / after a step,
+  // the per-instance layouts, index tables and the current chunk's GEMM blocks and parity
+  bool z2 = false;
+  int *z2ev = nullptr, *z2ev_new = nullptr;
+  Z2Layout* z2L = nullptr;
+  int *z2rank = nullptr, *z2kcol = nullptr, *z2colpos = nullptr, *z2pi = nullptr;
+  double* z2flops = nullptr;  // [2] flops of the GEMM blocks since hotrg_timing_start
+  bool t_z2 = false;          // a parity-blocked squeeze ran while timing
+  GemmBlocks* z2blk = nullptr;
   // impure tensors (Eqs. (SS), (ST)): [0] the nearest-neighbour pair, [1] the single spin
   bool impure = false;
   double *SI = nullptr;       // [2][batch][Pmax^2], normalised by the pure flow's c_n
@@ -85,7 +94,7 @@ struct hotrg_ctx {
   int graph_dims[kMaxD][kMaxD] = {};
   int graph_planes[kMaxD] = {-1, -1, -1, -1};
   long long launch0 = 0, t_gemm_launches = 0, t_steps = 0;
-  double t_gemm_flops = 0, t_gemm_tflops = 0, t_step_flops = 0;
+  double t_gemm_flops = 0, t_gemm_tflops = 0, t_step_flops = 0, t_dense_step_flops = 0;
 };
 
 namespace {
@@ -126,7 +135,9 @@ StepNeeds needs_for(int d, const int* dims, int a, int Dcut, int planes) {
   const bool mixed = planes > 0;
   Geom g = make_geom(d, dims);
   const long long P = g.P;
-  const long long ldk = mixed ? round_up(P, 64) : P;
+  // operand rows: P rounded up to 64, plus one more 64-column block for the zero-field
+  // (parity-blocked) layout, whose two k classes start at 64-aligned columns
+  const long long ldk = mixed ? round_up(P, 64) + 64 : P;
   int chi[kMaxD];
   int trans[kMaxD], nt = 0;
   for (int b = 0; b < d; ++b) {
@@ -291,6 +302,17 @@ size_t carve(hotrg_ctx* c, char* base) {
     c->dg_stride = (long long)nmax * nmax;
     c->dG = k.take<double>(sizeof(double) * c->dg_stride * c->batch);
   }
+  if (c->z2) {
+    c->z2ev = k.take<int>(sizeof(int) * kMaxD * c->batch);
+    c->z2ev_new = k.take<int>(sizeof(int) * kMaxD * c->batch);
+    c->z2L = k.take<Z2Layout>(sizeof(Z2Layout) * c->batch);
+    c->z2rank = k.take<int>(sizeof(int) * Pmax);
+    c->z2kcol = k.take<int>(sizeof(int) * Pmax);
+    c->z2colpos = k.take<int>(sizeof(int) * Pmax * kMaxBond);
+    c->z2blk = k.take<GemmBlocks>(sizeof(GemmBlocks));
+    c->z2pi = k.take<int>(sizeof(int) * 32);
+    c->z2flops = k.take<double>(sizeof(double) * 4);
+  }
   if (c->impure) {
     c->SI = k.take<double>(sizeof(double) * 2 * P2 * c->batch);
     c->Stmp = k.take<double>(sizeof(double) * 2 * P2);
@@ -329,7 +351,7 @@ int cuda_err(hotrg_ctx* c) {
 int status_to_code(int bits) {
   if (bits & ST_TIMEOUT) return HOTRG_ETIMEOUT;
   if (bits & ST_NOCONV) return HOTRG_ENOCONV;
-  if (bits & ST_NUMERIC) return HOTRG_ENUMERIC;
+  if (bits & (ST_NUMERIC | ST_Z2)) return HOTRG_ENUMERIC;
   if (bits) return HOTRG_EDEVICE;
   return HOTRG_OK;
 }
@@ -358,6 +380,72 @@ struct Ax {
 };
 
 // Contract (m_b, n_b) with U_b into k'_b; output dense row-major unless out_strides given.
+// Output description of contracting (m_b, n_b) into k'_b: the output view without k' (rest),
+// the stride of k', the contracted input axes and the dense output axes.
+struct Contraction {
+  View rest;
+  long long sk;
+  int im, in_;
+  std::vector<Ax> out_axes;
+};
+
+Contraction plan_contraction(const std::vector<Ax>& axes, int b, int chi_b, const long long* final_out_stride) {
+  Contraction r;
+  int im = -1, in_ = -1;
+  for (int i = 0; i < (int)axes.size(); ++i) {
+    if (axes[i].kind == 0 && axes[i].slot == b) im = i;
+    if (axes[i].kind == 2 && axes[i].slot == b) in_ = i;
+  }
+  View v;
+  v.ndim = 0;
+  int kaxis = -1;
+  for (int i = 0; i < (int)axes.size(); ++i) {
+    if (i == im) continue;
+    Ax ax = axes[i];
+    if (i == in_) {
+      kaxis = v.ndim;
+      ax.dim = chi_b;
+      ax.stride = 0;
+    }
+    v.shape[v.ndim] = ax.dim;
+    v.in_stride[v.ndim] = ax.stride;
+    r.out_axes.push_back(ax);
+    ++v.ndim;
+  }
+  long long st = 1;
+  for (int i = v.ndim - 1; i >= 0; --i) {
+    v.out_stride[i] = final_out_stride ? final_out_stride[i] : st;
+    st *= v.shape[i];
+  }
+  r.rest.ndim = 0;
+  for (int i = 0; i < v.ndim; ++i) {
+    if (i == kaxis) continue;
+    r.rest.shape[r.rest.ndim] = v.shape[i];
+    r.rest.in_stride[r.rest.ndim] = v.in_stride[i];
+    r.rest.out_stride[r.rest.ndim] = v.out_stride[i];
+    ++r.rest.ndim;
+  }
+  r.sk = v.out_stride[kaxis];
+  r.im = im;
+  r.in_ = in_;
+  st = 1;
+  for (int i = v.ndim - 1; i >= 0; --i) {
+    r.out_axes[i].stride = st;
+    st *= r.out_axes[i].dim;
+  }
+  return r;
+}
+
+// The first contraction of a chunk's epilogue from the parity-blocked GEMM output (z2.cu).
+template <class Tout>
+void contract_axes_z2(std::vector<Ax>& axes, const float* O, long long ldO, Tout* out, int b, int chi_b,
+                      const double* Ub, const long long* final_out_stride, long long out_base,
+                      const Z2Layout* L, const int* pi, cudaStream_t s) {
+  Contraction r = plan_contraction(axes, b, chi_b, final_out_stride);
+  launch_epi_z2<Tout>(O, ldO, out, r.rest, r.sk, out_base, b, axes[r.im].dim, Ub, chi_b, L, pi, s);
+  axes = r.out_axes;
+}
+
 // With in2 (laid out like in), the same contraction of in2 with U2 is added.
 template <class Tin, class Tout>
 void contract_axes(std::vector<Ax>& axes, const Tin* in, Tout* out, int b, int chi_b, const double* Ub,
@@ -663,6 +751,114 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   return HOTRG_OK;
 }
 
+// The zero-field squeeze of T with itself on the tensor cores (z2.cu): parity-blocked operands,
+// two dense GEMM blocks per chunk, the first epilogue contraction reading the blocked output.
+// Same output as squeeze<float>(c, T, T, out, ...) up to the order of FP32 summation.
+int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const double* U, const Geom& g,
+               const Geom& gn, int a, const int* chi, const int* trans, int nt, int planes, int npass) {
+  using Op = __nv_bfloat16;
+  cudaStream_t s = c->stream;
+  const long long P = g.P;
+  const long long ldz = round_up(P, 64) + 64;
+  const int c3 = trans[nt - 1];
+  const int chi3 = chi[c3];
+  auto Ub = [&](int b) { return U + (long long)b * kMaxBond * kMaxGram; };
+  StepNeeds need = needs_for(c->d, g.D, a, c->Dcut, planes);
+  if (need.Tt > c->sz_Tt || need.Bt > c->sz_Bt || need.X > c->sz_X || need.Y > c->sz_Y || need.O > c->sz_O ||
+      need.R1 > c->sz_R1 || need.R2 > c->sz_R2 || P > c->Pmax)
+    return HOTRG_ENOMEM;
+  const int nparts = planes;
+  const long long bt_plane = (long long)chi3 * P * ldz, y_plane = P * ldz;
+  auto pl = [&](void* base, long long plane_elems) {
+    Planes<Op> q;
+    q.nparts = nparts;
+    for (int k = 0; k < 3; ++k) q.p[k] = static_cast<Op*>(base) + (size_t)(k < nparts ? k : 0) * plane_elems;
+    return q;
+  };
+  Z2Layout* L = c->z2L + inst;
+  const int* ev_new = c->z2ev_new + inst * kMaxD;
+  const long long ldO = (long long)chi3 * P;
+  PhaseScope* ops_scope = new PhaseScope(c, PH_OPERANDS);
+  launch_z2_layout(c->z2ev + inst * kMaxD, ev_new, 1, g, c3, chi3, L, s);
+  launch_z2_tables(L, P, chi3, c->z2rank, c->z2kcol, c->z2colpos, s);
+  // zeros between and after the k classes (the GEMM's k-blocks run over them)
+  cudaMemsetAsync(c->Bt, 0, sizeof(Op) * nparts * bt_plane, s);
+  cudaMemsetAsync(c->Y, 0, sizeof(Op) * nparts * y_plane, s);
+  float* Tt = static_cast<float*>(c->Tt);
+  launch_transpose<float>(T, Tt, P, s);
+  launch_build_bt_z2(Tt, pl(c->Bt, bt_plane), ldz, g, c3, Ub(c3), chi3, c->z2rank, c->z2kcol, c->z2colpos, L, s);
+  delete ops_scope;
+  float* O = static_cast<float*>(c->O);
+  const int no = nt - 1;
+  int kcnt[kMaxD] = {0, 0, 0, 0};
+  long long nchunks = 1;
+  for (int i = 0; i < no; ++i) nchunks *= chi[trans[i]];
+  int prev_k0 = -1;
+  for (long long ch = 0; ch < nchunks; ++ch) {
+    long long r = ch;
+    for (int i = no - 1; i >= 0; --i) {
+      kcnt[i] = (int)(r % chi[trans[i]]);
+      r /= chi[trans[i]];
+    }
+    ops_scope = new PhaseScope(c, PH_OPERANDS);
+    launch_z2_chunk(L, ev_new, no, no > 0 ? trans[0] : 0, kcnt[0], no > 1 ? trans[1] : 0, kcnt[1], ldO, c->z2blk,
+                    c->z2pi, c->z2flops, npass, s);
+    if (no == 0) {
+      launch_build_y_z2<double>(T, pl(c->Y, y_plane), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
+    } else {
+      float* X1 = static_cast<float*>(c->X1);
+      float* X2 = static_cast<float*>(c->X2);
+      if (kcnt[0] != prev_k0) {
+        launch_mode_unprimed<double, float>(T, X1, g, trans[0], Ub(trans[0]), kcnt[0], s);
+        prev_k0 = kcnt[0];
+      }
+      const float* X = X1;
+      if (no >= 2) {
+        launch_mode_unprimed<float, float>(X1, X2, g, trans[1], Ub(trans[1]), kcnt[1], s);
+        X = X2;
+      }
+      launch_build_y_z2<float>(X, pl(c->Y, y_plane), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
+    }
+    delete ops_scope;
+    {
+      PhaseScope gemm_scope(c, PH_GEMM);
+      const int rc = launch_gemm_split(pl(c->Y, y_plane), ldz, pl(c->Bt, bt_plane), ldz, O, ldO, P, ldO, ldz, npass,
+                                       c->status, c->timeout_s, s, c->kblock, c->group_m, fold_group_for(c, npass),
+                                       c->z2blk);
+      if (rc) return rc;
+      // the blocks' flops are counted on the device (k_z2_chunk)
+      if (c->timing) {
+        ++c->t_gemm_launches;
+        c->t_z2 = true;
+      }
+    }
+    PhaseScope epi_scope(c, PH_EPILOGUE);
+    std::vector<Ax> axes;
+    for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b] * ldO, 0, b});
+    axes.push_back({chi3, P, 1, -1});
+    for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
+    long long out_base = 0;
+    for (int i = 0; i < no; ++i) out_base += (long long)kcnt[i] * gn.Sn[trans[i]] * gn.P;
+    float* bufs[2] = {static_cast<float*>(c->R1), static_cast<float*>(c->R2)};
+    long long fs[kMaxAxes];
+    if (no == 0) {
+      final_strides(axes, c3, c3, gn, c3, fs);
+      contract_axes_z2<double>(axes, O, ldO, out, c3, chi3, Ub(c3), fs, out_base, L, c->z2pi, s);
+      continue;
+    }
+    contract_axes_z2<float>(axes, O, ldO, bufs[0], trans[0], chi[trans[0]], Ub(trans[0]), nullptr, 0, L, c->z2pi,
+                            s);
+    const float* cur = bufs[0];
+    for (int i = 1; i < no; ++i) {
+      contract_axes<float, float>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(trans[i]), nullptr, 0, s);
+      cur = bufs[i];
+    }
+    final_strides(axes, c3, c3, gn, c3, fs);
+    contract_axes<float, double>(axes, cur, out, c3, chi3, Ub(c3), fs, out_base, s);
+  }
+  return HOTRG_OK;
+}
+
 }  // namespace
 
 // ================================================================= C ABI
@@ -700,6 +896,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   c.deriv = opt->derivatives != 0;
   c.deriv_mode = opt->derivatives;
   c.impure = opt->impurities != 0;
+  c.z2 = opt->z2 != 0;
   *bytes = carve(&c, nullptr);
   return HOTRG_OK;
 }
@@ -718,7 +915,10 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
     vb[i] = opt->beta ? opt->beta[i] : beta;
     vh[i] = opt->h ? opt->h[i] : h;
     if (!(vb[i] > 0.0) || !std::isfinite(vb[i]) || !std::isfinite(vh[i])) return HOTRG_EINVAL;
+    // the block structure holds only at zero field, and not for tangents or impurities in h
+    if (opt->z2 && vh[i] != 0.0) return HOTRG_EINVAL;
   }
+  if (opt->z2 && (opt->derivatives || opt->impurities || d < 2)) return HOTRG_EINVAL;
   int dev = 0;
   cudaDeviceProp prop;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
@@ -743,6 +943,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->deriv = opt->derivatives != 0;
   c->deriv_mode = opt->derivatives;
   c->impure = opt->impurities != 0;
+  c->z2 = opt->z2 != 0;
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
@@ -764,6 +965,13 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   cudaMemcpyAsync(c->dbeta, vb.data(), sizeof(double) * c->batch, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(c->dh, vh.data(), sizeof(double) * c->batch, cudaMemcpyHostToDevice, s);
   const long long P2 = c->Pmax * c->Pmax;
+  if (c->z2) {
+    // every initial leg: index 0 even, index 1 odd
+    std::vector<int> ones((size_t)kMaxD * c->batch, 1);
+    cudaMemcpyAsync(c->z2ev, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->z2ev_new, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
   launch_init_tensor(c->T, P2, c->batch, d, c->dbeta, c->dh, s);
   if (c->impure)
     for (int w = 0; w < 2; ++w) launch_init_tensor(c->SI + w * P2 * c->batch, P2, c->batch, d, c->dbeta, c->dh, s, 1);
@@ -838,7 +1046,8 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
       launch_gram_combine(c->Q1, c->Q2, c->q_stride, c->batch, g.D[b], g.D[a], Gb, c->g_stride, s);
       EigOut eo{c->spec_log + (long long)b * kSpecCap, c->spec_stride, (long long)c->d * kSpecCap, c->dstep,
                 c->max_steps};
-      launch_eig(Gb, c->g_stride, c->batch, n, chi[b], eo, Ub, c->u_stride, c->ework, c->status, s);
+      launch_eig(Gb, c->g_stride, c->batch, n, chi[b], eo, Ub, c->u_stride, c->ework, c->status, s,
+                 c->z2 ? c->z2ev : nullptr, c->z2ev_new, b, g.D[b]);
       if (c->deriv_mode == 2)
         for (int w = 0; w < 2; ++w) {
           // dG from the half-Gram tangents, then dU from the eigensystem still in ework
@@ -865,8 +1074,10 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
         tg.dU[w] = c->deriv_mode == 2 ? c->dU + (w * c->batch + i) * c->u_stride : nullptr;
       }
     }
-    int rc = planes ? squeeze<float>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass, tg)
-                    : squeeze<double>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0, tg);
+    int rc = (planes && c->z2 && nt > 0)
+                 ? squeeze_z2(c, i, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass)
+             : planes ? squeeze<float>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass, tg)
+                      : squeeze<double>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0, tg);
     if (rc) return rc;
     // impure tensors with the pure flow's isometries: the pair merges with itself at step 1
     // (Eq. (SS)) and with a pure site after (Eq. (ST)); the single spin always with a pure site
@@ -897,6 +1108,11 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
   launch_trace_x(c->T, P2max, c->batch, gn, a, c->L, c->dstep, c->out3, s);
   for (int w = 0; c->impure && w < 2; ++w)
     launch_trace_ratio(c->SI + w * P2max * c->batch, c->T, P2max, c->batch, gn.P, c->imp_out + w * c->batch, s);
+  if (c->z2) {
+    unsigned mask = 0;
+    for (int t = 0; t < nt; ++t) mask |= 1u << trans[t];
+    launch_z2_advance(c->z2ev, c->z2ev_new, c->batch, mask, s);
+  }
   if (c->deriv)
     for (int w = 0; w < 2; ++w)
       launch_trace_tangent(c->T, c->dT + w * P2max * c->batch, P2max, c->batch, gn.P, c->dL + w * c->batch,
@@ -904,7 +1120,9 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
   if (c->timing) {
     double f = 2.0 * (double)g.P * (double)g.P * (double)g.P * c->batch;
     for (int t = 0; t < nt; ++t) f *= chi[trans[t]];
-    c->t_step_flops += f;
+    c->t_dense_step_flops += f;
+    // parity-blocked steps add what their GEMM blocks computed, counted on the device
+    if (!(planes && c->z2 && nt > 0)) c->t_step_flops += f;
     ++c->t_steps;
   }
   return HOTRG_OK;
@@ -1100,6 +1318,8 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
     if (cudaMemsetAsync(c->dT + (w * c->batch + instance) * c->Pmax * c->Pmax, 0, sizeof(double) * g.P * g.P,
                         c->stream) != cudaSuccess)
       return c->sticky = HOTRG_EDEVICE;
+  // an arbitrary tensor need not have the zero-field block structure: use the dense squeeze
+  c->z2 = false;
   // nor does it carry impurities: the impure estimates restart from zero
   for (int w = 0; c->impure && w < 2; ++w)
     if (cudaMemsetAsync(c->SI + (w * c->batch + instance) * c->Pmax * c->Pmax, 0, sizeof(double) * g.P * g.P,
@@ -1259,7 +1479,10 @@ int hotrg_timing_start(hotrg_ctx* c) {
   c->timing = true;
   c->launch0 = launches_total();
   c->t_gemm_launches = c->t_steps = 0;
-  c->t_gemm_flops = c->t_gemm_tflops = c->t_step_flops = 0;
+  c->t_gemm_flops = c->t_gemm_tflops = c->t_step_flops = c->t_dense_step_flops = 0;
+  c->t_z2 = false;
+  if (c->z2flops && cudaMemsetAsync(c->z2flops, 0, sizeof(double) * 2, c->stream) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
   return HOTRG_OK;
 }
 
@@ -1289,6 +1512,15 @@ int hotrg_timing_stop(hotrg_ctx* c, hotrg_timing* out) {
   out->gemm_flops = c->t_gemm_flops;
   out->gemm_tensor_flops = c->t_gemm_tflops;
   out->step_flops = c->t_step_flops;
+  out->dense_step_flops = c->t_dense_step_flops;
+  if (c->t_z2 && c->z2flops) {
+    double zf[2] = {0.0, 0.0};
+    if (cudaMemcpy(zf, c->z2flops, sizeof(zf), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return c->sticky = HOTRG_EDEVICE;
+    out->gemm_flops += zf[0];
+    out->gemm_tensor_flops += zf[1];
+    out->step_flops += zf[0];
+  }
   cudaGetLastError();
   return HOTRG_OK;
 }

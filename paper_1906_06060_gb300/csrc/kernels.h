@@ -107,8 +107,13 @@ struct EigOut {
 // Symmetric eigendecomposition of G (n x n, n <= 256) by cyclic Jacobi, one CTA per instance;
 // eigenvalues sorted descending, the leading chi eigenvectors, sign-fixed, into U[k][0..n).
 // work: batch * 2*n*n doubles. Sets ST_NOCONV on the sweep limit.
+// z2_ev (non-null): zero-field flow: [batch][kMaxD] even counts of the legs; the kept vectors of
+// axis z2_axis (Db x Db fused index) are written even-parity first (each group in descending
+// eigenvalue order), z2_ev_new[i][z2_axis] = number of even ones; a vector that is not
+// parity-pure sets ST_Z2.
 void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o,
-                double* U, long long u_stride, double* work, int* status, cudaStream_t s);
+                double* U, long long u_stride, double* work, int* status, cudaStream_t s,
+                const int* z2_ev = nullptr, int* z2_ev_new = nullptr, int z2_axis = 0, int Db = 0);
 // First-order change of the kept eigenvectors for a change dG of G, from the eigensystem that
 // launch_eig left in `work` (call before the next launch_eig reuses it):
 //   dU_k = sign_k sum_{j >= chi} V_j (V_j^T dG V_k) / (lambda_k - lambda_j),  k < chi,
@@ -132,13 +137,59 @@ void launch_gemm_f64(const double* A, long long lda, const double* Bt, long long
 // group_m: output tiles are visited in groups of group_m M-tiles (L2 reuse); fold_group: k-blocks
 // per accumulator fold (at most ring stages - 1 when > 1).
 // Returns 0 or a hotrg_status (tensor-map encode failure, bad alignment or sizes).
+// Block-sparse form (blk != null, device memory read by the kernel at start): only the output
+// blocks listed are computed. Block b: rows [m0, m0+mc) of A and C, rows [n0, n0+nc) of Bt
+// (columns of C), k range [k0, k0+kc), where both operands must hold zeros from k0+kc up to the
+// next multiple of bk. M, N, K are then the operands' extents (rows of A, rows of Bt, row
+// length) and bound every copy; nothing outside the blocks is written.
+struct GemmBlocks {
+  int nb;
+  int m0[2], mc[2], n0[2], nc[2], k0[2], kc[2];
+};
 int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
                       int npass, int* status, double timeout_s, cudaStream_t s, int bk = 64,
-                      int group_m = 16, int fold_group = 1);
+                      int group_m = 16, int fold_group = 1, const GemmBlocks* blk = nullptr);
 // Largest fold group the kernel variant for (npass, bk) accepts.
 int max_fold_group(int npass, int bk);
 void launch_split_rows(const float* X, long long ldx, long long rows, long long cols,
                        const Planes<__nv_bfloat16>& out, long long ld, cudaStream_t s);
+
+// ---- z2.cu ---------------------------------------------------------------------------------
+// Parity-blocked layout of the zero-field squeeze's operands for one instance (see z2.cu).
+struct Z2Layout {
+  int d;
+  int D[kMaxD], e[kMaxD];      // bond dimensions and even-value counts of the current legs
+  int ncls[2];                 // natural P-indices of even / odd total parity
+  int kstart[2];               // operand column where each parity class starts (64-aligned)
+  int patoff[16];              // rank of the first index of each leg-parity pattern
+  int bs[16][kMaxD];           // row-major strides inside each pattern's box
+  int chi3, e3;                // the new c3 index: range and number of even values
+  int goff[2];                 // first output column of each group (parity of (j, n))
+  int jstart[2][kMaxBond + 1]; // offset of new index j inside each group
+};
+// Layouts of every instance (ev, ev_new: [batch][kMaxD] even counts before / after the step).
+void launch_z2_layout(const int* ev, const int* ev_new, int batch, Geom g, int c3, int chi3, Z2Layout* out,
+                      cudaStream_t s);
+// rank_tab[P], kcol_tab[P], colpos_tab[chi3 * P] of one instance's layout.
+void launch_z2_tables(const Z2Layout* L, long long P, int chi3, int* rank_tab, int* kcol_tab, int* colpos_tab,
+                      cudaStream_t s);
+// The chunk's parity (fixed new indices k0 of axis b0, k1 of b1; nfix of them) and its two GEMM
+// blocks; flops[0] += their 2 M N K, flops[1] += that times npass.
+void launch_z2_chunk(const Z2Layout* L, const int* ev_new, int nfix, int b0, int k0, int b1, int k1, long long ldO,
+                     GemmBlocks* blk, int* pi, double* flops, int npass, cudaStream_t s);
+// ev[i][b] = ev_new[i][b] for the axes b in trans_mask (end of a step).
+void launch_z2_advance(int* ev, const int* ev_new, int batch, unsigned trans_mask, cudaStream_t s);
+template <class Tin>
+void launch_build_y_z2(const Tin* X, const Planes<__nv_bfloat16>& out, long long ld, Geom g, int a,
+                       const int* rank_tab, const int* kcol_tab, const Z2Layout* L, const int* pi, cudaStream_t s);
+void launch_build_bt_z2(const float* Tt, const Planes<__nv_bfloat16>& out, long long ld, Geom g, int c3,
+                        const double* U3, int chi3, const int* rank_tab, const int* kcol_tab, const int* colpos_tab,
+                        const Z2Layout* L, cudaStream_t s);
+// First epilogue contraction (over slot t0, Dt x Dt -> chi) from the parity-blocked GEMM output;
+// rest / sk / out_base as for launch_pair_contract_all.
+template <class Tout>
+void launch_epi_z2(const float* O, long long ldO, Tout* out, const View& rest, long long sk, long long out_base,
+                   int t0, int Dt, const double* U, int chi, const Z2Layout* L, const int* pi, cudaStream_t s);
 
 }  // namespace hotrg

@@ -1,0 +1,379 @@
+// Spin-flip (Z2) block structure of the zero-field flow, used to skip the squeeze's zero blocks.
+//
+// At h = 0 the site weight is even in the spin, so T^(0) vanishes unless an even number of its
+// legs carry the odd bond index (Sec. 2's T^(0): the odd-n1 terms of the sum over s cancel
+// exactly). Every step keeps this: the Gram matrices commute with the parity of the fused
+// index, the eigenvectors are parity-pure (Jacobi never rotates an entry that is exactly zero),
+// so every new bond index has a parity and every tensor entry whose legs' parities add up to
+// odd is exactly zero. Here each bond index is kept parity-sorted (even values first; a
+// relabelling of the bond, under which ln Z/N and the spectra are invariant), and the squeeze
+// works on parity-blocked operands:
+//   rows m and columns k of the A operand, and the columns n of B, are ordered by total parity
+//   (even class first), inside a class by the parity pattern of the legs and then row-major
+//   inside the pattern's box; the two k classes start at 64-aligned columns with zeros between;
+//   the rows (j, n) of B (columns of the GEMM output) are grouped by parity(j) + parity(n).
+// In a chunk with isometry-index parity pi, A[m][k] vanishes unless parity(m) + parity(k) = pi
+// and B[(j, n)][k] unless parity(j) + parity(n) = parity(k): the product is two dense blocks,
+// a quarter of the dense flops.
+#include "kernels.h"
+
+namespace hotrg {
+
+namespace {
+
+__device__ __forceinline__ int popc4(int x) { return __popc(x & 15); }
+
+// natural P-index -> digits (slot 0 slowest) and leg-parity pattern (bit b = digit_b >= e_b)
+__device__ __forceinline__ int z2_digits(const Z2Layout& L, int idx, int* dig) {
+  int pat = 0;
+  for (int b = L.d - 1; b >= 0; --b) {
+    dig[b] = idx % L.D[b];
+    idx /= L.D[b];
+    if (dig[b] >= L.e[b]) pat |= 1 << b;
+  }
+  return pat;
+}
+
+__device__ __forceinline__ int z2_rank(const Z2Layout& L, const int* dig, int pat) {
+  int r = L.patoff[pat];
+  for (int b = 0; b < L.d; ++b) r += (dig[b] - (((pat >> b) & 1) ? L.e[b] : 0)) * L.bs[pat][b];
+  return r;
+}
+
+__global__ void k_z2_layout(const int* ev, const int* ev_new, Geom g, int c3, int chi3, Z2Layout* out) {
+  if (threadIdx.x != 0) return;
+  const int inst = blockIdx.x;
+  ev += inst * kMaxD;
+  ev_new += inst * kMaxD;
+  Z2Layout L;
+  L.d = g.d;
+  for (int b = 0; b < kMaxD; ++b) {
+    L.D[b] = b < g.d ? g.D[b] : 1;
+    L.e[b] = b < g.d ? min(max(ev[b], 0), L.D[b]) : 1;
+  }
+  const int npat = 1 << g.d;
+  int off = 0;
+  L.ncls[0] = L.ncls[1] = 0;
+  for (int cls = 0; cls < 2; ++cls)
+    for (int pat = 0; pat < 16; ++pat) {
+      if (pat >= npat || (popc4(pat) & 1) != cls) {
+        if (cls == 0) {
+          L.patoff[pat] = 0;
+          for (int b = 0; b < kMaxD; ++b) L.bs[pat][b] = 0;
+        }
+        continue;
+      }
+      int box = 1;
+      for (int b = g.d - 1; b >= 0; --b) {
+        L.bs[pat][b] = box;
+        box *= ((pat >> b) & 1) ? L.D[b] - L.e[b] : L.e[b];
+      }
+      for (int b = g.d; b < kMaxD; ++b) L.bs[pat][b] = 0;
+      L.patoff[pat] = off;
+      off += box;
+      L.ncls[cls] += box;
+    }
+  L.kstart[0] = 0;
+  L.kstart[1] = (L.ncls[0] + 63) / 64 * 64;
+  L.chi3 = chi3;
+  L.e3 = c3 >= 0 ? min(max(ev_new[c3], 0), chi3) : chi3;
+  for (int t = 0; t < 2; ++t) {
+    int acc = 0;
+    for (int j = 0; j <= kMaxBond; ++j) {
+      L.jstart[t][j] = acc;
+      if (j < chi3) acc += L.ncls[t ^ (j >= L.e3 ? 1 : 0)];
+    }
+  }
+  L.goff[0] = 0;
+  L.goff[1] = L.jstart[0][chi3];
+  out[inst] = L;
+}
+
+// rank_tab[i] = rank of natural index i (even class first); kcol_tab[i] = its operand column;
+// colpos_tab[j * P + n] = GEMM-output column of (j, n).
+__global__ void k_z2_tables(const Z2Layout* Lp, int P, int chi3, int* rank_tab, int* kcol_tab, int* colpos_tab) {
+  const Z2Layout L = *Lp;
+  const long long total = (long long)chi3 * P;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / P), n = (int)(t % P);
+    int dig[kMaxD];
+    const int pat = z2_digits(L, n, dig);
+    const int par = popc4(pat) & 1;
+    const int r = z2_rank(L, dig, pat);
+    const int within = r - (par ? L.ncls[0] : 0);
+    if (j == 0) {
+      rank_tab[n] = r;
+      kcol_tab[n] = L.kstart[par] + within;
+    }
+    const int grp = par ^ (j >= L.e3 ? 1 : 0);
+    colpos_tab[t] = L.goff[grp] + L.jstart[grp][j] + within;
+  }
+}
+
+// pi = parity of the chunk's fixed new indices; the GEMM's two blocks (row class cm, k class
+// and column group cm ^ pi).
+__global__ void k_z2_chunk(const Z2Layout* Lp, const int* ev_new, int nfix, int b0, int k0, int b1, int k1,
+                           long long ldO, GemmBlocks* blk, int* pi_out, double* flops, int npass) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const Z2Layout& L = *Lp;
+  int pi = 0;
+  if (nfix > 0) pi ^= k0 >= ev_new[b0] ? 1 : 0;
+  if (nfix > 1) pi ^= k1 >= ev_new[b1] ? 1 : 0;
+  GemmBlocks g;
+  g.nb = 2;
+  for (int cm = 0; cm < 2; ++cm) {
+    const int ck = cm ^ pi;
+    g.m0[cm] = cm ? L.ncls[0] : 0;
+    g.mc[cm] = L.ncls[cm];
+    g.k0[cm] = L.kstart[ck];
+    g.kc[cm] = L.ncls[ck];
+    g.n0[cm] = L.goff[ck];
+    g.nc[cm] = ck ? (int)(ldO - L.goff[1]) : L.goff[1];
+  }
+  *blk = g;
+  *pi_out = pi;
+  // algorithmic flops of the two blocks: [0] 2 M N K, [1] times the split passes
+  double f = 0.0;
+  for (int b = 0; b < 2; ++b) f += 2.0 * g.mc[b] * (double)g.nc[b] * g.kc[b];
+  flops[0] += f;
+  flops[1] += f * npass;
+}
+
+__global__ void k_z2_advance(int* ev, const int* ev_new, int batch, unsigned trans_mask) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= batch * kMaxD) return;
+  if ((trans_mask >> (t % kMaxD)) & 1) ev[t] = ev_new[t];
+}
+
+// A operand of one chunk, parity-blocked: Y[rank(m)][kcol(k)] = X[R(k) + C(m)] where
+// parity(m) + parity(k) = pi (the other entries of X are zero and not stored).
+template <class Tin>
+__global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, Planes<__nv_bfloat16> out,
+                                                    long long ld, Geom g, int a, const int* __restrict__ rank_tab,
+                                                    const int* __restrict__ kcol_tab, const Z2Layout* Lp,
+                                                    const int* pi_ptr) {
+  __shared__ long long Rk[32], Cm[32];
+  __shared__ int rowr[32], colk[32], parm[32], park[32];
+  const long long P = g.P;
+  const int ncls0 = Lp->ncls[0];
+  const int pi = *pi_ptr;
+  const long long m0 = (long long)blockIdx.y * 32, k0 = (long long)blockIdx.x * 32;
+  if (threadIdx.y == 0) {
+    const long long k = k0 + threadIdx.x, m = m0 + threadIdx.x;
+    long long rk = 0, cm = 0;
+    for (int b = 0; b < g.d; ++b) {
+      const long long kb = (k / g.Sn[b]) % g.D[b];
+      const long long mb = (m / g.Sn[b]) % g.D[b];
+      if (b == a) { rk += kb * g.Sn[b]; cm += mb * g.Sn[b] * P; }
+      else        { rk += kb * g.Sn[b] * P; cm += mb * g.Sn[b]; }
+    }
+    Rk[threadIdx.x] = rk;
+    Cm[threadIdx.x] = cm;
+    const int rm = m < P ? rank_tab[m] : 0;
+    const int ck = k < P ? kcol_tab[k] : 0;
+    rowr[threadIdx.x] = rm;
+    parm[threadIdx.x] = rm >= ncls0 ? 1 : 0;
+    colk[threadIdx.x] = ck;
+    park[threadIdx.x] = k < P ? (rank_tab[k] >= ncls0 ? 1 : 0) : 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const long long m = m0 + r, k = k0 + threadIdx.x;
+    if (m < P && k < P && (parm[r] ^ park[threadIdx.x]) == pi)
+      store_planes(out, (long long)rowr[r] * ld + colk[threadIdx.x], (float)X[Rk[threadIdx.x] + Cm[r]]);
+  }
+}
+
+// B operand, parity-blocked: Bt[colpos(j, n)][kcol(k)] = sum_x U3[j][k_c3][x] Tt[n][k | c3 := x]
+// where parity(j) + parity(n) = parity(k).
+template <class Tin>
+__global__ void __launch_bounds__(256) k_build_bt_z2(const Tin* __restrict__ Tt, Planes<__nv_bfloat16> out,
+                                                     long long ld, long long P, long long Sc, int Dc,
+                                                     const double* __restrict__ U3, int chi3,
+                                                     const int* __restrict__ rank_tab, const int* __restrict__ kcol_tab,
+                                                     const int* __restrict__ colpos_tab, const Z2Layout* Lp) {
+  extern __shared__ float W[];  // [chi3][Dc][Dc]
+  const int nW = chi3 * Dc * Dc;
+  for (int t = threadIdx.x; t < nW; t += blockDim.x) W[t] = (float)U3[t];
+  __syncthreads();
+  const int ncls0 = Lp->ncls[0];
+  const int goff1 = Lp->goff[1];
+  const long long total = (long long)chi3 * P * P;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long k = idx % P;
+    const long long row = idx / P;  // j*P + n
+    const int cp = colpos_tab[row];
+    const int grp = cp >= goff1 ? 1 : 0;
+    const int park = rank_tab[k] >= ncls0 ? 1 : 0;
+    if (grp != park) continue;
+    const long long n = row % P;
+    const int j = (int)(row / P);
+    const int kc = (int)((k / Sc) % Dc);
+    const long long base = n * P + k - (long long)kc * Sc;
+    const float* w = W + ((long long)j * Dc + kc) * Dc;
+    float acc = 0.f;
+    for (int x = 0; x < Dc; ++x) acc += w[x] * (float)Tt[base + x * Sc];
+    store_planes(out, (long long)cp * ld + kcol_tab[k], acc);
+  }
+}
+
+// First epilogue contraction of a chunk from the parity-blocked GEMM output:
+//   R[rest, k'] = sum_{i, jj} U_t0[k'][i][jj] O[m = (rest_m, m_t0 = i)][(j, n = (rest_n, n_t0 = jj))]
+// with O stored as O[rank(m)][colpos(j, n)]. rest = (m_b for b != t0, j, n_b for b != t0) in that
+// order, shaped and strided by `rest` (out_stride) and sk (stride of k'). Only the (i, jj)
+// parity combinations of the chunk's two computed blocks are read; the rest of O is zero.
+template <class Tout>
+__global__ void __launch_bounds__(256) k_epi_z2(const float* __restrict__ O, long long ldO, Tout* __restrict__ out,
+                                                View rest, long long total, long long sk, long long out_base,
+                                                int t0, const double* __restrict__ U, int chi,
+                                                const Z2Layout* Lp, const int* pi_ptr) {
+  extern __shared__ float W[];  // [D*D][chi]
+  __shared__ Z2Layout L;
+  if (threadIdx.x == 0) L = *Lp;
+  const int Dt = Lp->D[t0];
+  const int nij = Dt * Dt;
+  for (int t = threadIdx.x; t < chi * nij; t += blockDim.x) {
+    const int k = t / nij, ij = t % nij;
+    W[ij * chi + k] = (float)U[t];
+  }
+  __syncthreads();
+  const int pi = *pi_ptr;
+  const int d = L.d, et = L.e[t0];
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    // decode rest coordinates: d-1 m digits, j, d-1 n digits
+    int c[2 * kMaxD + 1];
+    long long rem = idx, ooff = out_base;
+    for (int ax = rest.ndim - 1; ax >= 0; --ax) {
+      c[ax] = (int)(rem % rest.shape[ax]);
+      rem /= rest.shape[ax];
+      ooff += (long long)c[ax] * rest.out_stride[ax];
+    }
+    int dm[kMaxD], dn[kMaxD];
+    int pm = 0, pn = 0, q = 0;
+    for (int b = 0; b < d; ++b) {
+      dm[b] = 0;
+      if (b == t0) continue;
+      dm[b] = c[q++];
+      if (dm[b] >= L.e[b]) pm |= 1 << b;
+    }
+    const int j = c[q++];
+    for (int b = 0; b < d; ++b) {
+      dn[b] = 0;
+      if (b == t0) continue;
+      dn[b] = c[q++];
+      if (dn[b] >= L.e[b]) pn |= 1 << b;
+    }
+    const int pj = j >= L.e3 ? 1 : 0;
+    const int tau = pi ^ pj ^ (popc4(pm) & 1) ^ (popc4(pn) & 1);
+    float acc[kMaxBond];
+#pragma unroll
+    for (int k = 0; k < kMaxBond; ++k) acc[k] = 0.f;
+    for (int ci = 0; ci < 2; ++ci) {
+      const int cj = ci ^ tau;
+      const int patm = pm | (ci << t0), patn = pn | (cj << t0);
+      const int parn = popc4(patn) & 1;
+      long long rb = L.patoff[patm];
+      long long cb = L.patoff[patn] - (parn ? L.ncls[0] : 0);
+      for (int b = 0; b < d; ++b) {
+        if (b == t0) continue;
+        rb += (long long)(dm[b] - (((patm >> b) & 1) ? L.e[b] : 0)) * L.bs[patm][b];
+        cb += (long long)(dn[b] - (((patn >> b) & 1) ? L.e[b] : 0)) * L.bs[patn][b];
+      }
+      const int grp = parn ^ pj;
+      cb += L.goff[grp] + L.jstart[grp][j];
+      const long long rs = L.bs[patm][t0], cs = L.bs[patn][t0];
+      const int i0 = ci ? et : 0, i1 = ci ? Dt : et;
+      const int j0 = cj ? et : 0, j1 = cj ? Dt : et;
+      for (int i = i0; i < i1; ++i) {
+        const float* src = O + (rb + (long long)(i - i0) * rs) * ldO + cb;
+        float x[kMaxBond];
+#pragma unroll
+        for (int u = 0; u < kMaxBond; ++u) x[u] = (j0 + u < j1) ? src[(long long)u * cs] : 0.f;
+#pragma unroll
+        for (int u = 0; u < kMaxBond; ++u) {
+          if (j0 + u >= j1) break;
+          const float* w = W + (i * Dt + j0 + u) * chi;
+#pragma unroll
+          for (int k = 0; k < kMaxBond; ++k)
+            if (k < chi) acc[k] += w[k] * x[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxBond; ++k)
+      if (k < chi) out[ooff + k * sk] = (Tout)acc[k];
+  }
+}
+
+inline int grid_cap(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void launch_z2_layout(const int* ev, const int* ev_new, int batch, Geom g, int c3, int chi3, Z2Layout* out,
+                      cudaStream_t s) {
+  k_z2_layout<<<batch, 32, 0, s>>>(ev, ev_new, g, c3, chi3, out);
+  count_launches(1);
+}
+
+void launch_z2_tables(const Z2Layout* L, long long P, int chi3, int* rank_tab, int* kcol_tab, int* colpos_tab,
+                      cudaStream_t s) {
+  k_z2_tables<<<grid_cap((long long)chi3 * P), 256, 0, s>>>(L, (int)P, chi3, rank_tab, kcol_tab, colpos_tab);
+  count_launches(1);
+}
+
+void launch_z2_chunk(const Z2Layout* L, const int* ev_new, int nfix, int b0, int k0, int b1, int k1, long long ldO,
+                     GemmBlocks* blk, int* pi, double* flops, int npass, cudaStream_t s) {
+  k_z2_chunk<<<1, 32, 0, s>>>(L, ev_new, nfix, b0, k0, b1, k1, ldO, blk, pi, flops, npass);
+  count_launches(1);
+}
+
+void launch_z2_advance(int* ev, const int* ev_new, int batch, unsigned trans_mask, cudaStream_t s) {
+  k_z2_advance<<<(batch * kMaxD + 127) / 128, 128, 0, s>>>(ev, ev_new, batch, trans_mask);
+  count_launches(1);
+}
+
+template <class Tin>
+void launch_build_y_z2(const Tin* X, const Planes<__nv_bfloat16>& out, long long ld, Geom g, int a,
+                       const int* rank_tab, const int* kcol_tab, const Z2Layout* L, const int* pi, cudaStream_t s) {
+  dim3 grid((unsigned)((g.P + 31) / 32), (unsigned)((g.P + 31) / 32));
+  k_build_y_z2<Tin><<<grid, dim3(32, 8), 0, s>>>(X, out, ld, g, a, rank_tab, kcol_tab, L, pi);
+  count_launches(1);
+}
+
+void launch_build_bt_z2(const float* Tt, const Planes<__nv_bfloat16>& out, long long ld, Geom g, int c3,
+                        const double* U3, int chi3, const int* rank_tab, const int* kcol_tab, const int* colpos_tab,
+                        const Z2Layout* L, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (size_t)chi3 * g.D[c3] * g.D[c3];
+  const long long total = (long long)chi3 * g.P * g.P;
+  k_build_bt_z2<float><<<grid_cap(total), 256, smem, s>>>(Tt, out, ld, g.P, g.Sn[c3], g.D[c3], U3, chi3, rank_tab,
+                                                           kcol_tab, colpos_tab, L);
+  count_launches(1);
+}
+
+template <class Tout>
+void launch_epi_z2(const float* O, long long ldO, Tout* out, const View& rest, long long sk, long long out_base,
+                   int t0, int Dt, const double* U, int chi, const Z2Layout* L, const int* pi, cudaStream_t s) {
+  long long total = 1;
+  for (int i = 0; i < rest.ndim; ++i) total *= rest.shape[i];
+  const size_t smem = sizeof(float) * (size_t)chi * Dt * Dt;
+  k_epi_z2<Tout><<<grid_cap(total), 256, smem, s>>>(O, ldO, out, rest, total, sk, out_base, t0, U, chi, L, pi);
+  count_launches(1);
+}
+
+template void launch_build_y_z2<float>(const float*, const Planes<__nv_bfloat16>&, long long, Geom, int, const int*,
+                                       const int*, const Z2Layout*, const int*, cudaStream_t);
+template void launch_build_y_z2<double>(const double*, const Planes<__nv_bfloat16>&, long long, Geom, int,
+                                        const int*, const int*, const Z2Layout*, const int*, cudaStream_t);
+template void launch_epi_z2<float>(const float*, long long, float*, const View&, long long, long long, int, int,
+                                   const double*, int, const Z2Layout*, const int*, cudaStream_t);
+template void launch_epi_z2<double>(const float*, long long, double*, const View&, long long, long long, int, int,
+                                    const double*, int, const Z2Layout*, const int*, cudaStream_t);
+
+}  // namespace hotrg

@@ -1,0 +1,141 @@
+"""The zero-field block-sparse squeeze (opts.z2) against the dense path and the FP64 oracle.
+
+z2 relabels every bond index (even parity first), so tensors differ from the dense path by a
+permutation of each bond; the comparisons use gauge-invariant results (ln Z/N, ln c_n, Gram
+spectra, X^(n)). The blocked GEMM sums the same nonzero products as the dense one in another
+order, so agreement is to FP32 rounding of the split-precision path.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import hotrg_ref as R
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name + ".json")) as fh:
+        return json.load(fh)
+
+
+def hotrg(*a, **kw):
+    from paper_1906_06060_gb300 import HOTRG
+    return HOTRG(*a, **kw)
+
+
+def run(d, beta, Dcut, nsteps, **kw):
+    with hotrg(d, beta, 0.0, Dcut, max_steps=nsteps, **kw) as f:
+        lnz = []
+        for _ in range(nsteps):
+            f.step()
+            lnz.append(f.free_energy()[0][0])
+        spec = [f.spectra(n, ax) for n in range(1, nsteps + 1) for ax in range(d)
+                if len(f.spectra(n, ax))]
+        return np.array(lnz), f.ln_norms(), spec, f.observables()
+
+
+@pytest.mark.parametrize("precision,x6", [("bf16x3", 0), ("bf16x3", 8), ("bf16x6", 0)])
+def test_z2_matches_dense_path_dcut5(precision, x6):
+    kw = dict(precision=precision, fp64_steps=2, x6_steps=x6)
+    lz, cz, sz, oz = run(4, 0.1497, 5, 12, z2=True, **kw)
+    ld, cd, sd, od = run(4, 0.1497, 5, 12, **kw)
+    np.testing.assert_allclose(lz, ld, rtol=5e-8, atol=0)
+    np.testing.assert_allclose(cz, cd, rtol=0, atol=2e-6)
+    for a, b in zip(sz, sd):
+        np.testing.assert_allclose(a / a[0], b / b[0], rtol=0, atol=2e-6)
+    assert abs(oz["x_indicator"] - od["x_indicator"]) < 1e-5
+
+
+def test_z2_flow_matches_oracle_golden_dcut5():
+    g = golden("flow_d4_b0.1497_h0_D5_n16")
+    lz, _, _, _ = run(4, 0.1497, 5, 16, z2=True, precision="bf16x6", fp64_steps=0)
+    for st in g["steps"]:
+        n = st["step"]
+        assert abs(lz[n - 1] - st["lnz"]) < 2e-7 * abs(st["lnz"]), n
+
+
+def test_z2_2d_flow_matches_oracle_golden():
+    g = golden("flow_d2_b0.3_h0_D8_n40")
+    lz, _, _, _ = run(2, 0.3, 8, 40, z2=True, precision="bf16x3", fp64_steps=2, x6_steps=12)
+    assert abs(lz[-1] - g["lnz_final"]) < 3e-7 * abs(g["lnz_final"])
+
+
+def test_z2_3d_flow_matches_oracle():
+    # Dcut = 10: every cut of this flow is clear of degenerate multiplets (smallest gap 0.12)
+    ref = R.run(3, 0.22, 0.0, 10, 9)
+    lz, _, _, _ = run(3, 0.22, 10, 9, z2=True, precision="bf16x6", fp64_steps=1)
+    np.testing.assert_allclose(lz, np.array(ref.lnz[1:]), rtol=2e-7, atol=0)
+
+
+@pytest.mark.parametrize("x6", [0, 12])
+def test_z2_dcut10_steady_steps_match_dense(x6):
+    """The benchmark's shapes: bond dimensions 10^4 from step 3 on (BF16X3 k-block 64 or BF16X6)."""
+    kw = dict(precision="bf16x3", fp64_steps=2, x6_steps=x6)
+    lz, cz, sz, _ = run(4, 0.1497, 10, 5, z2=True, **kw)
+    ld, cd, sd, _ = run(4, 0.1497, 10, 5, **kw)
+    np.testing.assert_allclose(lz, ld, rtol=5e-8, atol=0)
+    np.testing.assert_allclose(cz, cd, rtol=0, atol=5e-6)
+    for a, b in zip(sz, sd):
+        n = min(10, len(a))
+        np.testing.assert_allclose(a[:n] / a[0], b[:n] / b[0], rtol=0, atol=5e-6)
+
+
+def test_z2_batched_instances_match_separate_runs():
+    """Each instance carries its own parity counts. Dcut = 5: no cut of these flows splits a
+    degenerate multiplet (at Dcut = 6 one does, and the Gram's batch-dependent summation order
+    then picks another kept subspace)."""
+    betas = [0.14, 0.1497, 0.16]
+    with hotrg(4, betas, 0.0, 5, precision="bf16x3", fp64_steps=2, z2=True, max_steps=8) as fb:
+        for _ in range(8):
+            fb.step()
+        lb = fb.free_energy()[0]
+    for i, b in enumerate(betas):
+        with hotrg(4, b, 0.0, 5, precision="bf16x3", fp64_steps=2, z2=True, max_steps=8) as f:
+            for _ in range(8):
+                f.step()
+            assert abs(f.free_energy()[0][0] - lb[i]) < 1e-8 * abs(lb[i])
+
+
+def test_z2_graph_replay_is_bitwise_and_counts_a_quarter_of_the_flops():
+    import torch
+    st = torch.cuda.Stream()
+    out = []
+    for graphs in (False, True):
+        with hotrg(4, [0.1497, 0.15], 0.0, 5, precision="bf16x3", fp64_steps=2, z2=True, graphs=graphs,
+                   stream=st, max_steps=10) as f:
+            for _ in range(10):
+                f.step()
+            out.append((f.free_energy()[0], f.ln_norms(1)))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    with hotrg(4, 0.1497, 0.0, 8, precision="bf16x3", fp64_steps=2, z2=True, max_steps=8) as f:
+        for _ in range(4):
+            f.step()
+        f.timing_start()
+        f.step()
+        t = f.timing_stop()
+    ratio = t["step_flops"] / t["dense_step_flops"]
+    assert 0.2 < ratio < 0.3, ratio
+
+
+def test_z2_argument_checks_and_set_tensor():
+    from paper_1906_06060_gb300 import HotrgError
+    from paper_1906_06060_gb300 import _lib
+    for kw in (dict(h=1e-6), dict(derivatives="fixed"), dict(impurities=True)):
+        h = kw.pop("h", 0.0)
+        with pytest.raises(HotrgError) as e:
+            hotrg(4, 0.1497, h, 4, z2=True, **kw)
+        assert e.value.code == _lib.HOTRG_EINVAL
+    # an arbitrary tensor switches the context to the dense squeeze
+    from tests.inputs import random_site_tensor
+    T = random_site_tensor((4, 4, 4, 4), seed=3)
+    ref, _ = R.coarse_grain(T, 2, 5)
+    with hotrg(4, 0.3, 0.0, 5, precision="bf16x3", fp64_steps=0, z2=True) as f:
+        f.set_tensor(T)
+        f.step(2)
+        got = f.get_tensor()
+    ref = ref / R.frobenius(ref)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-4 * np.abs(ref).max())
