@@ -8,6 +8,11 @@ the steady-state bond dimensions 10^4) run untimed, then K steady-state steps ar
 events on the library's stream. Metric: algorithmic TFLOP/s of the squeeze (2 prod(chi_b) P^3
 per step = 2 Dcut^15 at steady state; split-precision extra passes are not counted).
 
+At h = 0 the squeeze runs block-sparse by default (opts.z2: the spin-flip parity structure leaves
+two dense GEMM blocks per chunk, about a quarter of the flops; --no-z2 for the dense squeeze).
+"value" keeps the chi-rule count above as the unit of work in both cases; "executed_tflops" is
+what the kernels computed.
+
 Default precision schedule (the one whose free energy stays within 1e-7 of FP64): steps 1-3 in
 FP64, steps 4-12 in BF16X6, then BF16X3. With the default W = 12 the timed steps are BF16X3 steps
 of that schedule; with W = 3 they are BF16X6 steps.
@@ -61,6 +66,8 @@ def parse():
     ap.add_argument("--dcut", type=int, default=0)
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--h", type=float, default=0.0)
+    ap.add_argument("--no-z2", action="store_true",
+                    help="dense squeeze at h = 0 (default: the zero-field block-sparse squeeze)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=2)
@@ -83,6 +90,13 @@ def instances(a):
     return [a.beta], [a.h]
 
 
+def use_z2(a):
+    """The zero-field block-sparse squeeze applies when every instance has h = 0 and no
+    derivative in h is taken."""
+    _, hs = instances(a)
+    return (not a.no_z2) and a.workload != "deriv" and a.precision != "fp64" and all(h == 0.0 for h in hs)
+
+
 def workload_config(a):
     betas, hs = instances(a)
     if a.workload == "scan":
@@ -102,6 +116,7 @@ def workload_config(a):
             "h": a.h if len(hs) == 1 else sorted(set(hs)), "precision": a.precision,
             "timed_steps": [a.warmup + 1, a.warmup + a.steps],
             "fp64_steps": a.fp64_steps, "x6_steps": a.x6_steps, "kblock": a.kblock,
+            "z2_block_sparse": use_z2(a),
             "fold_group": a.fold_group,
             "l2": "inputs larger than L2 (T 800 MB fp64, GEMM operands several GB per step)",
             "parallelism": "replicas" if a.gpus > 1 else "single GPU"}
@@ -255,6 +270,7 @@ def run_ours(a, rank, world, dist):
     betas, hs = instances(a)
     if a.workload == "deriv":
         kw["derivatives"] = "eig"
+    kw["z2"] = use_z2(a)
     flow = HOTRG(4, betas, hs, a.dcut, **kw)
     for _ in range(a.warmup):
         flow.step()
@@ -278,17 +294,20 @@ def run_ours(a, rank, world, dist):
     lnz = flow.free_energy()[0][0]
     flow_obs = [flow.observables(i) for i in range(flow.batch)] if a.workload == "deriv" else []
     flow.close()
-    step_flops = t["step_flops"] * (5.0 if a.workload == "deriv" else 1.0)
+    # unit of work: the chi-rule count 2 prod(chi_b) P^3 per step and instance (also with the
+    # block-sparse squeeze, which computes about a quarter of it: reported as executed_*)
+    step_flops = t["dense_step_flops"] * (5.0 if a.workload == "deriv" else 1.0)
+    executed_flops = t["step_flops"] * (5.0 if a.workload == "deriv" else 1.0)
     # max time over ranks, total flops over ranks
     if dist:
-        buf = torch.tensor([ms, step_flops], dtype=torch.float64, device=dev)
+        buf = torch.tensor([ms, step_flops, executed_flops], dtype=torch.float64, device=dev)
         mx = buf.clone()
         dist.all_reduce(mx, op=dist.ReduceOp.MAX)
         sm = buf.clone()
         dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, flops_all = float(mx[0]), float(sm[1])
+        ms_max, flops_all, exec_all = float(mx[0]), float(sm[1]), float(sm[2])
     else:
-        ms_max, flops_all = ms, step_flops
+        ms_max, flops_all, exec_all = ms, step_flops, executed_flops
     if rank != 0:
         return None
     value = flops_all / (ms_max * 1e-3) / 1e12
@@ -304,8 +323,9 @@ def run_ours(a, rank, world, dist):
             "peak_source": f"{src} bf16 sustained (kernel timed inside long steps)",
             "kernel": "k_gemm_split (tcgen05 squeeze GEMM)" if a.precision != "fp64" else "k_gemm_f64",
             "tensor_pipe_tflops": (t["gemm_tensor_flops"] / max(1, t["gemm_launches"])) / (gemm_ms * 1e-3) / 1e12,
-            "note": "achieved counts algorithmic flops (2MNK) only; the split passes multiply tensor work "
-                    "by 3 (bf16x3) or 6 (bf16x6)"}
+            "note": "achieved counts the algorithmic flops the GEMM launches execute (2MNK; with the "
+                    "block-sparse squeeze only its two blocks per chunk); the split passes multiply tensor "
+                    "work by 3 (bf16x3) or 6 (bf16x6)"}
     if a.precision == "fp64":
         roof.update({"bound": "alu", "peak": 1.25, "peak_source": "nominal GB300 FP64 rate",
                      "frac": achieved / 1.25})
@@ -319,6 +339,8 @@ def run_ours(a, rank, world, dist):
            "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "bf16",
            "data": "synthetic", "config": workload_config(a),
            "steps_per_s": a.steps / (ms_max * 1e-3), "roofline": roof,
+           "executed_tflops": exec_all / (ms_max * 1e-3) / 1e12,
+           "executed_flops_fraction": exec_all / flops_all if flops_all else None,
            "phases_ms_per_step": {k[3:]: v / a.steps for k, v in t.items() if k.startswith("ms_")},
            "gpu_launches": int(t["kernel_launches"]), "lnz_per_site_after": lnz, **extra}
     out["clocks"] = clk.summary()
@@ -334,7 +356,7 @@ def e2e(a):
     nsteps = a.warmup + a.steps
     t0 = time.perf_counter()
     flow = HOTRG(4, a.beta, a.h, a.dcut, precision=a.precision, fp64_steps=a.fp64_steps, x6_steps=a.x6_steps,
-                 kblock=a.kblock, fold_group=a.fold_group)
+                 kblock=a.kblock, fold_group=a.fold_group, z2=use_z2(a))
     flops = 0.0
     dims = [2, 2, 2, 2]
     for n in range(nsteps):

@@ -252,6 +252,8 @@ __global__ void __launch_bounds__(256) k_trace_x(const double* __restrict__ T, l
 }
 
 // ---------------------------------------------------------------------------- mode product
+// One thread per "base" (an input index with digit b = 0): it reads the Db inputs along leg b
+// once and writes all Db outputs, so every input element is read from memory once.
 // TWO: out also accumulates the same product of a second input with a second matrix (the
 // tangent of a mode product: dX = M_U(dT) + M_dU(T)).
 template <class Tin, class Tout, bool TWO>
@@ -267,15 +269,27 @@ __global__ void __launch_bounds__(256) k_mode_unprimed(const Tin* __restrict__ i
     if (TWO) W2[t] = (Acc)U2[(long long)kk * Db * Db + t];
   }
   __syncthreads();
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)((idx / stride_b) % Db);
-    const long long base = idx - (long long)j * stride_b;
-    Acc acc = 0;
-    for (int i = 0; i < Db; ++i) acc += W[i * Db + j] * (Acc)in[base + i * stride_b];
-    if (TWO)
-      for (int i = 0; i < Db; ++i) acc += W2[i * Db + j] * (Acc)in2[base + i * stride_b];
-    out[idx] = (Tout)acc;
+  const long long nbase = total / Db;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nbase;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long base = (t / stride_b) * stride_b * Db + t % stride_b;
+    Acc x[kMaxBond], x2[TWO ? kMaxBond : 1];
+#pragma unroll
+    for (int i = 0; i < kMaxBond; ++i)
+      if (i < Db) {
+        x[i] = (Acc)in[base + i * stride_b];
+        if (TWO) x2[i] = (Acc)in2[base + i * stride_b];
+      }
+    for (int j = 0; j < Db; ++j) {
+      Acc acc = 0;
+#pragma unroll
+      for (int i = 0; i < kMaxBond; ++i)
+        if (i < Db) {
+          acc += W[i * Db + j] * x[i];
+          if (TWO) acc += W2[i * Db + j] * x2[i];
+        }
+      out[base + j * stride_b] = (Tout)acc;
+    }
   }
 }
 
@@ -550,11 +564,12 @@ template <class Tin, class Tout>
 void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double* U, int kk,
                           cudaStream_t s, const Tin* in2, const double* U2) {
   const long long total = g.P * g.P;
+  const long long nbase = total / g.D[b];
   if (in2)
-    k_mode_unprimed<Tin, Tout, true><<<grid_for(total, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
+    k_mode_unprimed<Tin, Tout, true><<<grid_for(nbase, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
                                                                            g.D[b], U, kk, in2, U2);
   else
-    k_mode_unprimed<Tin, Tout, false><<<grid_for(total, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
+    k_mode_unprimed<Tin, Tout, false><<<grid_for(nbase, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
                                                                             g.D[b], U, kk, nullptr, nullptr);
   count_launches(1);
 }

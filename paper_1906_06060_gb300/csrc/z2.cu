@@ -178,11 +178,20 @@ __global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, P
     park[threadIdx.x] = k < P ? (rank_tab[k] >= ncls0 ? 1 : 0) : 0;
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const long long m = m0 + r, k = k0 + threadIdx.x;
-    if (m < P && k < P && (parm[r] ^ park[threadIdx.x]) == pi)
-      store_planes(out, (long long)rowr[r] * ld + colk[threadIdx.x], (float)X[Rk[threadIdx.x] + Cm[r]]);
+  // the thread's four loads first, then the stores
+  float v[4];
+  bool w[4];
+  const long long k = k0 + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = threadIdx.y + 8 * q;
+    const long long m = m0 + r;
+    w[q] = m < P && k < P && (parm[r] ^ park[threadIdx.x]) == pi;
+    v[q] = w[q] ? (float)X[Rk[threadIdx.x] + Cm[r]] : 0.f;
   }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (w[q]) store_planes(out, (long long)rowr[threadIdx.y + 8 * q] * ld + colk[threadIdx.x], v[q]);
 }
 
 // B operand, parity-blocked: Bt[colpos(j, n)][kcol(k)] = sum_x U3[j][k_c3][x] Tt[n][k | c3 := x]
@@ -224,61 +233,82 @@ __global__ void __launch_bounds__(256) k_build_bt_z2(const Tin* __restrict__ Tt,
 // with O stored as O[rank(m)][colpos(j, n)]. rest = (m_b for b != t0, j, n_b for b != t0) in that
 // order, shaped and strided by `rest` (out_stride) and sk (stride of k'). Only the (i, jj)
 // parity combinations of the chunk's two computed blocks are read; the rest of O is zero.
-template <class Tout>
+// CHI = chi (compile-time: exact accumulator count, no predicated FMAs).
+template <class Tout, int CHI>
 __global__ void __launch_bounds__(256) k_epi_z2(const float* __restrict__ O, long long ldO, Tout* __restrict__ out,
-                                                View rest, long long total, long long sk, long long out_base,
-                                                int t0, const double* __restrict__ U, int chi,
+                                                View rest, int total, long long sk, long long out_base,
+                                                int t0, const double* __restrict__ U,
                                                 const Z2Layout* Lp, const int* pi_ptr) {
-  extern __shared__ float W[];  // [D*D][chi]
+  extern __shared__ float W[];  // [D*D][CHI]
   __shared__ Z2Layout L;
+  __shared__ int shape[2 * kMaxD + 1];
+  __shared__ long long ostr[2 * kMaxD + 1];
   if (threadIdx.x == 0) L = *Lp;
+  if (threadIdx.x < rest.ndim) {
+    shape[threadIdx.x] = rest.shape[threadIdx.x];
+    ostr[threadIdx.x] = rest.out_stride[threadIdx.x];
+  }
   const int Dt = Lp->D[t0];
   const int nij = Dt * Dt;
-  for (int t = threadIdx.x; t < chi * nij; t += blockDim.x) {
+  for (int t = threadIdx.x; t < CHI * nij; t += blockDim.x) {
     const int k = t / nij, ij = t % nij;
-    W[ij * chi + k] = (float)U[t];
+    W[ij * CHI + k] = (float)U[t];
   }
   __syncthreads();
   const int pi = *pi_ptr;
-  const int d = L.d, et = L.e[t0];
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    // decode rest coordinates: d-1 m digits, j, d-1 n digits
-    int c[2 * kMaxD + 1];
-    long long rem = idx, ooff = out_base;
-    for (int ax = rest.ndim - 1; ax >= 0; --ax) {
-      c[ax] = (int)(rem % rest.shape[ax]);
-      rem /= rest.shape[ax];
-      ooff += (long long)c[ax] * rest.out_stride[ax];
-    }
+  const int d = L.d, et = L.e[t0], nd = rest.ndim;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    // decode rest coordinates, last axis first: the d-1 n digits, j, the d-1 m digits (32-bit:
+    // rest has < 2^31 entries); unrolled over the slots so that the digits stay in registers
+    int rem = idx;
+    long long ooff = out_base;
+    int ax = nd - 1;
     int dm[kMaxD], dn[kMaxD];
-    int pm = 0, pn = 0, q = 0;
-    for (int b = 0; b < d; ++b) {
-      dm[b] = 0;
-      if (b == t0) continue;
-      dm[b] = c[q++];
-      if (dm[b] >= L.e[b]) pm |= 1 << b;
-    }
-    const int j = c[q++];
-    for (int b = 0; b < d; ++b) {
+    int pm = 0, pn = 0;
+#pragma unroll
+    for (int b = kMaxD - 1; b >= 0; --b) {
       dn[b] = 0;
-      if (b == t0) continue;
-      dn[b] = c[q++];
+      if (b >= d || b == t0) continue;
+      const int sh = shape[ax];
+      const int qq = rem / sh;
+      dn[b] = rem - qq * sh;
+      rem = qq;
+      ooff += (long long)dn[b] * ostr[ax--];
       if (dn[b] >= L.e[b]) pn |= 1 << b;
+    }
+    int j;
+    {
+      const int sh = shape[ax];
+      const int qq = rem / sh;
+      j = rem - qq * sh;
+      rem = qq;
+      ooff += (long long)j * ostr[ax--];
+    }
+#pragma unroll
+    for (int b = kMaxD - 1; b >= 0; --b) {
+      dm[b] = 0;
+      if (b >= d || b == t0) continue;
+      const int sh = shape[ax];
+      const int qq = rem / sh;
+      dm[b] = rem - qq * sh;
+      rem = qq;
+      ooff += (long long)dm[b] * ostr[ax--];
+      if (dm[b] >= L.e[b]) pm |= 1 << b;
     }
     const int pj = j >= L.e3 ? 1 : 0;
     const int tau = pi ^ pj ^ (popc4(pm) & 1) ^ (popc4(pn) & 1);
-    float acc[kMaxBond];
+    float acc[CHI];
 #pragma unroll
-    for (int k = 0; k < kMaxBond; ++k) acc[k] = 0.f;
+    for (int k = 0; k < CHI; ++k) acc[k] = 0.f;
     for (int ci = 0; ci < 2; ++ci) {
       const int cj = ci ^ tau;
       const int patm = pm | (ci << t0), patn = pn | (cj << t0);
       const int parn = popc4(patn) & 1;
       long long rb = L.patoff[patm];
       long long cb = L.patoff[patn] - (parn ? L.ncls[0] : 0);
-      for (int b = 0; b < d; ++b) {
-        if (b == t0) continue;
+#pragma unroll
+      for (int b = 0; b < kMaxD; ++b) {
+        if (b >= d || b == t0) continue;
         rb += (long long)(dm[b] - (((patm >> b) & 1) ? L.e[b] : 0)) * L.bs[patm][b];
         cb += (long long)(dn[b] - (((patn >> b) & 1) ? L.e[b] : 0)) * L.bs[patn][b];
       }
@@ -289,22 +319,24 @@ __global__ void __launch_bounds__(256) k_epi_z2(const float* __restrict__ O, lon
       const int j0 = cj ? et : 0, j1 = cj ? Dt : et;
       for (int i = i0; i < i1; ++i) {
         const float* src = O + (rb + (long long)(i - i0) * rs) * ldO + cb;
-        float x[kMaxBond];
+        const float* wrow = W + (i * Dt) * CHI;
+        // the row's loads in groups of four, issued before their FMAs
+        for (int u0 = j0; u0 < j1; u0 += 4) {
+          float x[4];
 #pragma unroll
-        for (int u = 0; u < kMaxBond; ++u) x[u] = (j0 + u < j1) ? src[(long long)u * cs] : 0.f;
+          for (int u = 0; u < 4; ++u) x[u] = (u0 + u < j1) ? src[(long long)(u0 + u - j0) * cs] : 0.f;
 #pragma unroll
-        for (int u = 0; u < kMaxBond; ++u) {
-          if (j0 + u >= j1) break;
-          const float* w = W + (i * Dt + j0 + u) * chi;
+          for (int u = 0; u < 4; ++u) {
+            if (u0 + u >= j1) break;
+            const float* w = wrow + (u0 + u) * CHI;
 #pragma unroll
-          for (int k = 0; k < kMaxBond; ++k)
-            if (k < chi) acc[k] += w[k] * x[u];
+            for (int k = 0; k < CHI; ++k) acc[k] += w[k] * x[u];
+          }
         }
       }
     }
 #pragma unroll
-    for (int k = 0; k < kMaxBond; ++k)
-      if (k < chi) out[ooff + k * sk] = (Tout)acc[k];
+    for (int k = 0; k < CHI; ++k) out[ooff + k * sk] = (Tout)acc[k];
   }
 }
 
@@ -363,7 +395,19 @@ void launch_epi_z2(const float* O, long long ldO, Tout* out, const View& rest, l
   long long total = 1;
   for (int i = 0; i < rest.ndim; ++i) total *= rest.shape[i];
   const size_t smem = sizeof(float) * (size_t)chi * Dt * Dt;
-  k_epi_z2<Tout><<<grid_cap(total), 256, smem, s>>>(O, ldO, out, rest, total, sk, out_base, t0, U, chi, L, pi);
+  const int n = (int)total;  // rest < 2^31 entries (P^2 chi3 / Dt^2 <= 2.3e9 / 4 for Dcut <= 14)
+  switch (chi) {
+#define HOTRG_EPI_Z2(C)                                                                                   \
+  case C:                                                                                                 \
+    k_epi_z2<Tout, C><<<grid_cap(total), 256, smem, s>>>(O, ldO, out, rest, n, sk, out_base, t0, U, L, pi); \
+    break;
+    HOTRG_EPI_Z2(1) HOTRG_EPI_Z2(2) HOTRG_EPI_Z2(3) HOTRG_EPI_Z2(4) HOTRG_EPI_Z2(5) HOTRG_EPI_Z2(6)
+    HOTRG_EPI_Z2(7) HOTRG_EPI_Z2(8) HOTRG_EPI_Z2(9) HOTRG_EPI_Z2(10) HOTRG_EPI_Z2(11) HOTRG_EPI_Z2(12)
+    HOTRG_EPI_Z2(13) HOTRG_EPI_Z2(14) HOTRG_EPI_Z2(15) HOTRG_EPI_Z2(16)
+#undef HOTRG_EPI_Z2
+    default:
+      return;
+  }
   count_launches(1);
 }
 
