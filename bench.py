@@ -47,7 +47,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "4D HOTRG TFLOP/s & % tensor peak at Dcut=10, mixed vs FP64, |Δf/f|≤1e-7"
 GEMM_SRC = os.path.join(ROOT, "paper_1906_06060_gb300", "csrc", "gemm_tc.cu")
-PROFILE = os.path.join(ROOT, "profiles", "ncu_squeeze_gemm_dcut10_summary.md")
+# committed ncu summaries of the Dcut = 10 BF16X3 squeeze GEMM: dense and block-sparse launches
+PROFILE = {False: os.path.join(ROOT, "profiles", "ncu_squeeze_gemm_dcut10_summary.md"),
+           True: os.path.join(ROOT, "profiles", "ncu_squeeze_gemm_z2_dcut10_summary.md")}
 
 
 def parse():
@@ -234,11 +236,11 @@ def run_reference(a, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def traffic_from_profile():
-    """Per-launch DRAM bytes of the squeeze GEMM from the committed ncu summary, valid only if
-    the kernel source is unchanged since the capture."""
+def traffic_from_profile(z2):
+    """Per-launch DRAM bytes of the squeeze GEMM (dense or block-sparse launch) from the
+    committed ncu summary, valid only if the kernel source is unchanged since the capture."""
     try:
-        text = open(PROFILE).read()
+        text = open(PROFILE[bool(z2)]).read()
     except OSError:
         return None
     sha = hashlib.sha256(open(GEMM_SRC, "rb").read()).hexdigest()[:16]
@@ -318,8 +320,8 @@ def run_ours(a, rank, world, dist):
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             # the committed ncu capture is of the Dcut = 10 BF16X3 steady-step GEMM
-            "traffic": (traffic_from_profile() if (a.workload == "flow" and a.dcut == 10 and a.precision == "bf16x3")
-                        else None),
+            "traffic": (traffic_from_profile(use_z2(a))
+                        if (a.workload == "flow" and a.dcut == 10 and a.precision == "bf16x3") else None),
             "peak_source": f"{src} bf16 sustained (kernel timed inside long steps)",
             "kernel": "k_gemm_split (tcgen05 squeeze GEMM)" if a.precision != "fp64" else "k_gemm_f64",
             "tensor_pipe_tflops": (t["gemm_tensor_flops"] / max(1, t["gemm_launches"])) / (gemm_ms * 1e-3) / 1e12,
