@@ -93,10 +93,23 @@ def instances(a):
 
 
 def use_z2(a):
-    """The zero-field block-sparse squeeze applies when every instance has h = 0 and no
-    derivative in h is taken."""
+    """The zero-field block-sparse squeeze applies to instances with h = 0 when no derivative in
+    h is taken (a scan puts its h = 0 instances into a block-sparse context of their own)."""
     _, hs = instances(a)
-    return (not a.no_z2) and a.workload != "deriv" and a.precision != "fp64" and all(h == 0.0 for h in hs)
+    return (not a.no_z2) and a.workload != "deriv" and a.precision != "fp64" and any(h == 0.0 for h in hs)
+
+
+def groups(a):
+    """(betas, hs, z2) of the contexts that run the workload's instances."""
+    betas, hs = instances(a)
+    if not use_z2(a):
+        return [(betas, hs, False)]
+    zero = [i for i, h in enumerate(hs) if h == 0.0]
+    rest = [i for i, h in enumerate(hs) if h != 0.0]
+    out = [([betas[i] for i in zero], [0.0] * len(zero), True)]
+    if rest:
+        out.append(([betas[i] for i in rest], [hs[i] for i in rest], False))
+    return out
 
 
 def workload_config(a):
@@ -119,6 +132,7 @@ def workload_config(a):
             "timed_steps": [a.warmup + 1, a.warmup + a.steps],
             "fp64_steps": a.fp64_steps, "x6_steps": a.x6_steps, "kblock": a.kblock,
             "z2_block_sparse": use_z2(a),
+            "contexts": [{"instances": len(g[0]), "z2": g[2]} for g in groups(a)],
             "fold_group": a.fold_group,
             "l2": "inputs larger than L2 (T 800 MB fp64, GEMM operands several GB per step)",
             "parallelism": "replicas" if a.gpus > 1 else "single GPU"}
@@ -269,33 +283,39 @@ def run_ours(a, rank, world, dist):
         if dist:
             dist.barrier()
 
-    betas, hs = instances(a)
     if a.workload == "deriv":
         kw["derivatives"] = "eig"
-    kw["z2"] = use_z2(a)
-    flow = HOTRG(4, betas, hs, a.dcut, **kw)
+    # one context per group (a scan's h = 0 instances run block-sparse in a context of their own);
+    # all contexts step on the same stream, one after the other
+    flows = [HOTRG(4, b, h, a.dcut, z2=z2, **kw) for b, h, z2 in groups(a)]
     for _ in range(a.warmup):
-        flow.step()
-    flow.free_energy()
+        for flow in flows:
+            flow.step()
+    for flow in flows:
+        flow.free_energy()
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    flow.timing_start()
+    for flow in flows:
+        flow.timing_start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev.index) as clk:
         ev0.record(stream)
         for _ in range(a.steps):
-            flow.step()
+            for flow in flows:
+                flow.step()
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    t = flow.timing_stop()
+    ts = [flow.timing_stop() for flow in flows]
+    t = {k: sum(x[k] for x in ts) for k in ts[0]}
     ms = ev0.elapsed_time(ev1)
-    lnz = flow.free_energy()[0][0]
-    flow_obs = [flow.observables(i) for i in range(flow.batch)] if a.workload == "deriv" else []
-    flow.close()
+    lnz = flows[0].free_energy()[0][0]
+    flow_obs = [flows[0].observables(i) for i in range(flows[0].batch)] if a.workload == "deriv" else []
+    for flow in flows:
+        flow.close()
     # unit of work: the chi-rule count 2 prod(chi_b) P^3 per step and instance (also with the
     # block-sparse squeeze, which computes about a quarter of it: reported as executed_*)
     step_flops = t["dense_step_flops"] * (5.0 if a.workload == "deriv" else 1.0)

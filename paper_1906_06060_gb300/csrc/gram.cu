@@ -5,16 +5,16 @@
 //                         = sum_{al, al~} Q1[(b1,al)][(b1~,al~)] Q2[(b2,al)][(b2~,al~)]
 // Q1 contracts site 1 over all legs except (u_b, p_a); Q2 site 2 over all except (u_b, u_a).
 // Both are X X^T of an unfolding of T with nr = D_b D_a rows and P^2 / nr columns, computed in
-// FP64 on the CUDA cores by split-K 64x64 tiles and a fixed-order reduction (deterministic).
+// FP64 on the CUDA cores by split-K tiles (edge chosen per nr to waste the least padding; only
+// the upper tiles of a symmetric product) and a fixed-order reduction (deterministic).
 #include "kernels.h"
 
 namespace hotrg {
 
 namespace {
 
-constexpr int GT = 64;           // output tile edge
-constexpr int GK = 16;           // column chunk
-constexpr int kGramCTAs = 304;   // 2 x 152 SMs
+constexpr int GK = 16;               // column chunk
+constexpr int kGramWarps = 152 * 24;  // warps the split-K grid aims at (latency hiding on the FP64 pipe)
 
 struct LegInfo {
   int nrest;                     // number of remaining legs (2d - 2)
@@ -22,13 +22,17 @@ struct LegInfo {
   long long stride[kMaxLegs];
 };
 
-// Rows of the output tile come from TA, columns from TB (both T for the Gram itself; the tangent
-// dT and T for its derivative).
-__global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ TA, const double* __restrict__ TB,
-                                                   long long t_stride, LegInfo li,
-                                                   long long S1, long long S2, int Da, int nr,
-                                                   long long K, int ntile, int nsplit,
-                                                   double* __restrict__ partial) {
+// Output tiles of edge GT ((GT/4)^2 threads, 4 x 4 outputs each). With sym (TA = TB: Q is
+// symmetric) only the tiles on and above the diagonal are computed; the reduction mirrors the
+// rest. Rows of a tile come from TA, columns from TB (both T for the Gram itself; the tangent dT
+// and T for its derivative).
+template <int GT>
+__global__ void __launch_bounds__((GT / 4) * (GT / 4)) k_half_gram(const double* __restrict__ TA,
+                                                                   const double* __restrict__ TB, long long t_stride,
+                                                                   LegInfo li, long long S1, long long S2, int Da,
+                                                                   int nr, long long K, int ntile, int sym,
+                                                                   int nsplit, double* __restrict__ partial) {
+  constexpr int NT = (GT / 4) * (GT / 4);
   TA += (long long)blockIdx.z * t_stride;
   TB += (long long)blockIdx.z * t_stride;
   partial += (long long)blockIdx.z * nsplit * nr * nr;
@@ -37,17 +41,26 @@ __global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ TA
   __shared__ long long coloff[GK];
   __shared__ long long rowoffA[GT], rowoffB[GT];
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x, split = blockIdx.y;
-  const int r0 = (tile / ntile) * GT, c0 = (tile % ntile) * GT;
+  const int split = blockIdx.y;
+  int tr = 0, tc = 0;
+  if (sym) {
+    int t = blockIdx.x;
+    while (t >= ntile - tr) { t -= ntile - tr; ++tr; }
+    tc = tr + t;
+  } else {
+    tr = blockIdx.x / ntile;
+    tc = blockIdx.x % ntile;
+  }
+  const int r0 = tr * GT, c0 = tc * GT;
   const long long kper = (K + nsplit - 1) / nsplit;
   const long long kb = (long long)split * kper;
   const long long ke = min(K, kb + kper);
-  if (tid < GT) {
-    const int ra = r0 + tid, rb = c0 + tid;
-    rowoffA[tid] = ra < nr ? (long long)(ra / Da) * S1 + (long long)(ra % Da) * S2 : -1;
-    rowoffB[tid] = rb < nr ? (long long)(rb / Da) * S1 + (long long)(rb % Da) * S2 : -1;
+  for (int t = tid; t < GT; t += NT) {
+    const int ra = r0 + t, rb = c0 + t;
+    rowoffA[t] = ra < nr ? (long long)(ra / Da) * S1 + (long long)(ra % Da) * S2 : -1;
+    rowoffB[t] = rb < nr ? (long long)(rb / Da) * S1 + (long long)(rb % Da) * S2 : -1;
   }
-  const int tx = tid % 16, ty = tid / 16;
+  const int tx = tid % (GT / 4), ty = tid / (GT / 4);
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -69,9 +82,7 @@ __global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ TA
       coloff[tid] = off;
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < (GT * GK) / 256; ++q) {
-      const int e = tid + 256 * q;
+    for (int e = tid; e < GT * GK; e += NT) {
       const int kk = e % GK, rr = e / GK;
       const long long co = coloff[kk];
       const long long ra = rowoffA[rr], rb = rowoffB[rr];
@@ -106,14 +117,19 @@ __global__ void __launch_bounds__(256) k_half_gram(const double* __restrict__ TA
   }
 }
 
-__global__ void k_reduce_splits(const double* __restrict__ partial, int nsplit, int nn,
+// Q[e] = sum over the splits in a fixed order; with sym, entries below the diagonal tiles read
+// their mirror.
+__global__ void k_reduce_splits(const double* __restrict__ partial, int nsplit, int nr, int gt, int sym,
                                 double* __restrict__ Q, long long q_stride) {
+  const int nn = nr * nr;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nn) return;
   partial += (long long)blockIdx.y * nsplit * nn;
   Q += (long long)blockIdx.y * q_stride;
+  const int r = e / nr, c = e % nr;
+  const int src = (sym && r / gt > c / gt) ? c * nr + r : e;
   double s = 0.0;
-  for (int k = 0; k < nsplit; ++k) s += partial[(long long)k * nn + e];
+  for (int k = 0; k < nsplit; ++k) s += partial[(long long)k * nn + src];
   Q[e] = s;
 }
 
@@ -165,12 +181,29 @@ __global__ void k_gram_combine_tangent(const double* __restrict__ Q1, const doub
 
 }  // namespace
 
-int gram_nsplit() { return kGramCTAs; }
+// Tile edge for nr x nr outputs: the candidate that computes the fewest padded entries.
+static int gram_tile(int nr, bool sym) {
+  const int cand[5] = {36, 44, 52, 60, 64};
+  int best = 64;
+  long long best_area = -1;
+  for (int gt : cand) {
+    const long long n = (nr + gt - 1) / gt;
+    const long long area = (sym ? n * (n + 1) / 2 : n * n) * gt * gt;
+    if (best_area < 0 || area < best_area) { best_area = area; best = gt; }
+  }
+  return best;
+}
 
-// split-K factor for nr x nr outputs over `batch` instances (about two waves of CTAs in total)
-static int nsplit_for(int nr, long long K, int batch) {
-  const int ntile = (nr + GT - 1) / GT;
-  int nsplit = kGramCTAs / (ntile * ntile * batch);
+static int gram_tiles(int nr, bool sym, int gt) {
+  const int n = (nr + gt - 1) / gt;
+  return sym ? n * (n + 1) / 2 : n * n;
+}
+
+// split-K factor for nr x nr outputs over `batch` instances (about kGramWarps warps in total)
+static int nsplit_for(int nr, long long K, int batch, bool sym) {
+  const int gt = gram_tile(nr, sym);
+  const int wpc = ((gt / 4) * (gt / 4) + 31) / 32;
+  int nsplit = kGramWarps / (gram_tiles(nr, sym, gt) * wpc * batch);
   if (nsplit < 1) nsplit = 1;
   if (nsplit > K) nsplit = (int)K;
   return nsplit;
@@ -178,10 +211,11 @@ static int nsplit_for(int nr, long long K, int batch) {
 
 size_t gram_partial_doubles(int nr_max, int batch) {
   size_t best = 0;
-  for (int nr = 1; nr <= nr_max; ++nr) {
-    const size_t v = (size_t)batch * nsplit_for(nr, 1LL << 40, batch) * nr * nr;
-    if (v > best) best = v;
-  }
+  for (int nr = 1; nr <= nr_max; ++nr)
+    for (int sym = 0; sym < 2; ++sym) {
+      const size_t v = (size_t)batch * nsplit_for(nr, 1LL << 40, batch, sym != 0) * nr * nr;
+      if (v > best) best = v;
+    }
   return best;
 }
 
@@ -201,15 +235,24 @@ void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, in
   const int Da = leg_dim(l2);
   const int nr = leg_dim(l1) * Da;
   const long long K = g.P * g.P / nr;
-  const int ntile = (nr + GT - 1) / GT;
-  const int tiles = ntile * ntile;
-  const int nsplit = nsplit_for(nr, K, batch);
-  dim3 grid(tiles, nsplit, batch);
-  k_half_gram<<<grid, 256, 0, s>>>(TA ? TA : T, T, t_stride, li, leg_stride(l1), leg_stride(l2), Da, nr, K, ntile,
-                                    nsplit, partial);
+  const bool sym = TA == nullptr || TA == T;
+  const int gt = gram_tile(nr, sym);
+  const int ntile = (nr + gt - 1) / gt;
+  const int nsplit = nsplit_for(nr, K, batch, sym);
+  dim3 grid(gram_tiles(nr, sym, gt), nsplit, batch);
+  const double* A = TA ? TA : T;
+  switch (gt) {
+#define HOTRG_GRAM(GT_)                                                                                        \
+  case GT_:                                                                                                    \
+    k_half_gram<GT_><<<grid, (GT_ / 4) * (GT_ / 4), 0, s>>>(A, T, t_stride, li, leg_stride(l1), leg_stride(l2), \
+                                                            Da, nr, K, ntile, sym ? 1 : 0, nsplit, partial);     \
+    break;
+    HOTRG_GRAM(36) HOTRG_GRAM(44) HOTRG_GRAM(52) HOTRG_GRAM(60) HOTRG_GRAM(64)
+#undef HOTRG_GRAM
+  }
   count_launches(1);
   const int nn = nr * nr;
-  k_reduce_splits<<<dim3((nn + 255) / 256, batch), 256, 0, s>>>(partial, nsplit, nn, Q, q_stride);
+  k_reduce_splits<<<dim3((nn + 255) / 256, batch), 256, 0, s>>>(partial, nsplit, nr, gt, sym ? 1 : 0, Q, q_stride);
   count_launches(1);
 }
 

@@ -81,7 +81,6 @@ void prepare_kernel_attributes();
 // Q[(i,al)][(i~,al~)] = sum over all other legs of T[..i..al..] T[..i~..al~..]; legs l1, l2 are
 // positions 0..2d-1 in the natural layout. partial: nsplit * nr^2 doubles scratch.
 // Instance i reads T + i*t_stride and writes Q + i*q_stride.
-int gram_nsplit();
 size_t gram_partial_doubles(int nr_max, int batch);  // scratch for `partial`
 // With TA: rows from TA (same layout and strides as T), columns from T: Q(TA, T).
 void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, int l1, int l2,
