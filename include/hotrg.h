@@ -175,6 +175,14 @@ int hotrg_get_tensor(hotrg_ctx *c, int instance, int *dims, double *host, size_t
  * opts.max_steps steps). */
 int hotrg_set_tensor(hotrg_ctx *c, int instance, const int *dims, const double *host);
 
+/* The same for a context created with opts.z2, keeping the block-sparse squeeze: the tensor
+ * must have the zero-field block structure (Sec. 2's T^(0) at h = 0 and every coarse-grained
+ * tensor of that flow), with the values of leg b ordered even-parity first and evens[b] of
+ * them even (d ints, 0..dims[b]): every entry whose legs' parities add up to odd must be exactly
+ * zero, which is checked on the host. Errors: EINVAL (bad sizes, structure violated), ESTATE
+ * (context created without opts.z2). Synchronises. */
+int hotrg_set_tensor_z2(hotrg_ctx *c, int instance, const int *dims, const int *evens, const double *host);
+
 /* Checkpoint: size of, save to and restore from a host buffer holding the full flow state
  * (tensors, dims, accumulators, step logs). load requires a context created with the same
  * d, Dcut, batch and precision. Synchronise. Errors: EINVAL (size/format mismatch). */

@@ -152,13 +152,20 @@ class HOTRG:
               "hotrg_get_tensor")
         return out
 
-    def set_tensor(self, T: np.ndarray, instance: int = 0) -> None:
+    def set_tensor(self, T: np.ndarray, instance: int = 0, evens=None) -> None:
+        """Replace an instance's tensor (natural layout). evens (one count per leg, values
+        ordered even-parity first) keeps the block-sparse squeeze of a context created with
+        z2=True; the tensor must then have the zero-field block structure."""
         T = np.ascontiguousarray(T, dtype=np.float64)
         if T.ndim != 2 * self.d:
             raise ValueError("tensor rank must be 2d")
         dims = (c_int * 4)(*T.shape[: self.d])
-        check(_lib.load().hotrg_set_tensor(self._ctx, instance, dims,
-                                           T.ctypes.data_as(ctypes.POINTER(c_double))), "hotrg_set_tensor")
+        ptr = T.ctypes.data_as(ctypes.POINTER(c_double))
+        if evens is None:
+            check(_lib.load().hotrg_set_tensor(self._ctx, instance, dims, ptr), "hotrg_set_tensor")
+        else:
+            ev = (c_int * 4)(*[int(x) for x in evens])
+            check(_lib.load().hotrg_set_tensor_z2(self._ctx, instance, dims, ev, ptr), "hotrg_set_tensor_z2")
 
     def state_save(self) -> bytes:
         lib = _lib.load()

@@ -52,6 +52,7 @@ _SIGS = {
     "hotrg_ln_norms": (c_int, [c_void_p, c_int, POINTER(c_double), c_int, POINTER(c_int)]),
     "hotrg_get_tensor": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double), c_size_t]),
     "hotrg_set_tensor": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double)]),
+    "hotrg_set_tensor_z2": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     "hotrg_state_size": (c_int, [c_void_p, POINTER(c_size_t)]),
     "hotrg_state_save": (c_int, [c_void_p, c_void_p, c_size_t]),
     "hotrg_state_load": (c_int, [c_void_p, c_void_p, c_size_t]),

@@ -64,7 +64,8 @@ struct hotrg_ctx {
   void *dR1 = nullptr, *dR2 = nullptr;
   // zero-field block structure (z2.cu): even-value counts of every leg, before / after a step,
   // the per-instance layouts, index tables and the current chunk's GEMM blocks and parity
-  bool z2 = false;
+  bool z2 = false;      // the block-sparse squeeze is in use
+  bool z2_opt = false;  // requested at init (set_tensor turns z2 off, set_tensor_z2 back on)
   int *z2ev = nullptr, *z2ev_new = nullptr;
   Z2Layout* z2L = nullptr;
   int *z2rank = nullptr, *z2kcol = nullptr, *z2colpos = nullptr, *z2pi = nullptr;
@@ -369,6 +370,17 @@ int sync_check(hotrg_ctx* c) {
   const int code = status_to_code(bits);
   if (code) c->sticky = code;
   return code;
+}
+
+// Forget the captured steady-state steps (after the tensor, its bond order or the squeeze
+// path changed from outside the flow).
+void drop_graphs(hotrg_ctx* c) {
+  for (int a = 0; a < kMaxD; ++a)
+    if (c->graph_exec[a]) {
+      cudaGraphExecDestroy(c->graph_exec[a]);
+      c->graph_exec[a] = nullptr;
+      c->graph_planes[a] = -1;
+    }
 }
 
 // ----------------------------------------------------------------- epilogue axis bookkeeping
@@ -944,6 +956,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->deriv_mode = opt->derivatives;
   c->impure = opt->impurities != 0;
   c->z2 = opt->z2 != 0;
+  c->z2_opt = c->z2;
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
@@ -1320,6 +1333,7 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
       return c->sticky = HOTRG_EDEVICE;
   // an arbitrary tensor need not have the zero-field block structure: use the dense squeeze
   c->z2 = false;
+  drop_graphs(c);
   // nor does it carry impurities: the impure estimates restart from zero
   for (int w = 0; c->impure && w < 2; ++w)
     if (cudaMemsetAsync(c->SI + (w * c->batch + instance) * c->Pmax * c->Pmax, 0, sizeof(double) * g.P * g.P,
@@ -1329,10 +1343,45 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
   return HOTRG_OK;
 }
 
+int hotrg_set_tensor_z2(hotrg_ctx* c, int instance, const int* dims, const int* evens, const double* host) {
+  if (!c || !dims || !evens || !host || instance < 0 || instance >= c->batch) return HOTRG_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->z2_opt) return HOTRG_ESTATE;
+  for (int b = 0; b < c->d; ++b)
+    if (dims[b] < 1 || dims[b] > c->Dcut || evens[b] < 0 || evens[b] > dims[b]) return HOTRG_EINVAL;
+  if (c->batch > 1)
+    for (int b = 0; b < c->d; ++b)
+      if (dims[b] != c->dims[b]) return HOTRG_EINVAL;
+  Geom g = make_geom(c->d, dims);
+  if (g.P > c->Pmax) return HOTRG_EINVAL;
+  // the block structure must hold exactly: every entry with odd total leg parity is zero
+  std::vector<int> upar(g.P);
+  for (long long u = 0; u < g.P; ++u) {
+    int par = 0;
+    for (int b = 0; b < c->d; ++b) par ^= ((u / g.Sn[b]) % g.D[b]) >= evens[b] ? 1 : 0;
+    upar[u] = par;
+  }
+  for (long long u = 0; u < g.P; ++u)
+    for (long long q = 0; q < g.P; ++q)
+      if ((upar[u] ^ upar[q]) && host[u * g.P + q] != 0.0) return HOTRG_EINVAL;
+  int ev[kMaxD] = {1, 1, 1, 1};
+  for (int b = 0; b < c->d; ++b) ev[b] = evens[b];
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemcpy(c->T + instance * c->Pmax * c->Pmax, host, sizeof(double) * g.P * g.P,
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->z2ev + instance * kMaxD, ev, sizeof(ev), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->z2ev_new + instance * kMaxD, ev, sizeof(ev), cudaMemcpyHostToDevice) != cudaSuccess)
+    return c->sticky = HOTRG_EDEVICE;
+  c->z2 = true;
+  drop_graphs(c);
+  for (int b = 0; b < c->d; ++b) c->dims[b] = dims[b];
+  return HOTRG_OK;
+}
+
 // ---- checkpoint format: header, then per instance T (P^2), L, lnc_log, spec_log, out3
 struct StateHeader {
   char magic[8];
-  int version, d, Dcut, batch, precision, max_steps, steps, last_axis, deriv, impure;
+  int version, d, Dcut, batch, precision, max_steps, steps, last_axis, deriv, impure, z2;
   int dims[kMaxD];
   long long P;
   int hist_dims[64][kMaxD];
@@ -1345,7 +1394,8 @@ size_t state_per_instance(const hotrg_ctx* c, long long P) {
   size_t n = (size_t)P * P + 1 + (c->max_steps + 1) + c->spec_stride + 3;
   if (c->deriv) n += 2 * ((size_t)P * P + 2);
   if (c->impure) n += 2 * ((size_t)P * P + 1);
-  return sizeof(double) * n;
+  // with the block-sparse squeeze: the legs' even-value counts
+  return sizeof(double) * n + (c->z2_opt ? sizeof(int) * kMaxD : 0);
 }
 
 int hotrg_state_size(hotrg_ctx* c, size_t* bytes) {
@@ -1363,7 +1413,8 @@ int hotrg_state_save(hotrg_ctx* c, void* host, size_t cap) {
   StateHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "HOTRGST", 8);
-  h.version = 2;
+  h.version = 3;
+  h.z2 = c->z2 ? 1 : 0;
   h.deriv = c->deriv ? c->deriv_mode : 0;
   h.impure = c->impure ? 1 : 0;
   h.d = c->d; h.Dcut = c->Dcut; h.batch = c->batch; h.precision = c->precision;
@@ -1407,6 +1458,10 @@ int hotrg_state_save(hotrg_ctx* c, void* host, size_t cap) {
       ok = ok && cudaMemcpy(p, c->imp_out + j, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess;
       p += sizeof(double);
     }
+    if (c->z2_opt) {
+      ok = ok && cudaMemcpy(p, c->z2ev + i * kMaxD, sizeof(int) * kMaxD, cudaMemcpyDeviceToHost) == cudaSuccess;
+      p += sizeof(int) * kMaxD;
+    }
     if (!ok) return c->sticky = HOTRG_EDEVICE;
   }
   return HOTRG_OK;
@@ -1416,9 +1471,9 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
   if (!c || !host || size < sizeof(StateHeader)) return HOTRG_EINVAL;
   StateHeader h;
   std::memcpy(&h, host, sizeof(h));
-  if (std::memcmp(h.magic, "HOTRGST", 8) || h.version != 2 || h.d != c->d || h.Dcut != c->Dcut ||
+  if (std::memcmp(h.magic, "HOTRGST", 8) || h.version != 3 || h.d != c->d || h.Dcut != c->Dcut ||
       h.batch != c->batch || h.precision != c->precision || h.max_steps != c->max_steps ||
-      h.deriv != (c->deriv ? c->deriv_mode : 0) || h.impure != (c->impure ? 1 : 0))
+      h.deriv != (c->deriv ? c->deriv_mode : 0) || h.impure != (c->impure ? 1 : 0) || (h.z2 && !c->z2_opt))
     return HOTRG_EINVAL;
   Geom g = make_geom(h.d, h.dims);
   if (g.P != h.P || g.P > c->Pmax) return HOTRG_EINVAL;
@@ -1456,6 +1511,11 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
       ok = ok && cudaMemcpy(c->imp_out + j, p, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
       p += sizeof(double);
     }
+    if (c->z2_opt) {
+      ok = ok && cudaMemcpy(c->z2ev + i * kMaxD, p, sizeof(int) * kMaxD, cudaMemcpyHostToDevice) == cudaSuccess;
+      ok = ok && cudaMemcpy(c->z2ev_new + i * kMaxD, p, sizeof(int) * kMaxD, cudaMemcpyHostToDevice) == cudaSuccess;
+      p += sizeof(int) * kMaxD;
+    }
     if (!ok) return c->sticky = HOTRG_EDEVICE;
   }
   if (cudaMemcpy(c->dstep, &h.steps, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1465,6 +1525,8 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
   std::memcpy(c->hist_axis, h.hist_axis, sizeof(h.hist_axis));
   c->steps = h.steps;
   c->last_axis = h.last_axis;
+  c->z2 = h.z2 != 0;
+  drop_graphs(c);
   return HOTRG_OK;
 }
 

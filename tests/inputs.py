@@ -31,3 +31,20 @@ def random_symmetric_psd(n: int, seed: int, rank: int | None = None) -> np.ndarr
 
 def beta_scan(lo: float, hi: float, n: int) -> np.ndarray:
     return np.linspace(lo, hi, n)
+
+
+def random_z2_site_tensor(dims, evens, seed: int) -> np.ndarray:
+    """Gaussian rank-2d tensor with the zero-field (spin-flip) block structure: the values of leg
+    b are ordered even-parity first, evens[b] of them even, and every entry whose legs' parities
+    add up to odd is set to zero."""
+    T = random_site_tensor(dims, seed)
+    d = len(dims)
+    par = np.zeros(T.shape, dtype=int)
+    for axis in range(2 * d):
+        b = axis % d
+        p = (np.arange(dims[b]) >= evens[b]).astype(int)
+        shape = [1] * (2 * d)
+        shape[axis] = dims[b]
+        par = par ^ p.reshape(shape)
+    T[par == 1] = 0.0
+    return T

@@ -53,3 +53,57 @@ def test_steady_dcut10_step_matches_oracle_on_sampled_slices(case, precision, kb
         np.testing.assert_allclose(have, want, rtol=0, atol=tol * scale)
     # the GPU's norm is the norm of the whole output: sampled slices carry part of it
     assert 0 < np.sum((ref[:, 0, 0, :SLICES] / c) ** 2) < 1.0
+
+
+# ------------------------------------------------------------------ the benchmark's default path
+def _kept_parities(U, par):
+    """Spin-flip parity of each kept vector of U (D x D x chi, fused index (x1, x2)) given the
+    parities of the old bond's values: the parity of its largest component."""
+    D = U.shape[0]
+    out = []
+    for k in range(U.shape[2]):
+        x1, x2 = np.unravel_index(np.argmax(np.abs(U[:, :, k])), (D, D))
+        out.append(par[x1] ^ par[x2])
+    return np.array(out, dtype=int)
+
+
+@pytest.mark.parametrize("precision,kblock,tol", [("bf16x3", 64, 2e-4), ("bf16x6", 32, 2e-6)])
+def test_steady_dcut10_block_sparse_step_matches_oracle_on_sampled_slices(precision, kblock, tol):
+    """The block-sparse squeeze (the benchmark's default at h = 0) at the benchmark's shapes, on
+    a seeded Gaussian tensor with the zero-field block structure (bond dimensions 10^4, uneven
+    parity classes). The library writes every new bond even-parity first (stable in the
+    eigenvalue order), so its indices are the oracle's permuted per new bond; the test derives
+    that permutation from the parities of the oracle's kept vectors and compares element by
+    element (generic spectra: unique isometries up to the common sign convention)."""
+    from paper_1906_06060_gb300 import HOTRG
+    from tests.inputs import random_z2_site_tensor
+    evens = (5, 4, 6, 5)
+    T = random_z2_site_tensor((D,) * 4, evens, seed=2020)
+    a = 0
+    trans = [1, 2, 3]
+    U = {b: R.isometry_from_gram(R.gram(T, a, b), D, D).U for b in trans}
+    ref = R.squeeze(T, T, a, U, max_slices=SLICES)
+    par = [(np.arange(D) >= evens[b]).astype(int) for b in range(4)]
+    sig = [np.arange(D)] + [None] * 3
+    for b in trans:
+        p = _kept_parities(U[b], par[b])
+        sig[b] = np.argsort(np.argsort(p, kind="stable"), kind="stable")  # oracle index -> library
+    with HOTRG(4, 0.1497, 0.0, D, precision=precision, fp64_steps=0, x6_steps=0, kblock=kblock, z2=True,
+               max_steps=8) as f:
+        f.set_tensor(T, evens=evens)
+        f.step(a)
+        got = f.get_tensor()
+        c = math.exp(f.ln_norms()[-1])
+        # a second step runs the block-sparse path on its own output
+        f.timing_start()
+        f.step(3)
+        t = f.timing_stop()
+        assert 0.2 < t["step_flops"] / t["dense_step_flops"] < 0.3
+    for s in range(SLICES):
+        k3 = s % D
+        want = ref[:, 0, 0, k3] / c                      # [u0 | p0, p1, p2, p3]
+        have = got[np.ix_(sig[0], [sig[1][0]], [sig[2][0]], [sig[3][k3]], sig[0], sig[1], sig[2], sig[3])]
+        have = have.reshape(want.shape)
+        scale = np.abs(want).max()
+        assert scale > 0
+        np.testing.assert_allclose(have, want, rtol=0, atol=tol * scale)

@@ -139,3 +139,41 @@ def test_z2_argument_checks_and_set_tensor():
         got = f.get_tensor()
     ref = ref / R.frobenius(ref)
     np.testing.assert_allclose(got, ref, rtol=0, atol=2e-4 * np.abs(ref).max())
+
+
+def test_set_tensor_z2_checks_the_structure_and_checkpoints_keep_the_parity_counts():
+    from paper_1906_06060_gb300 import HotrgError
+    from paper_1906_06060_gb300 import _lib
+    from tests.inputs import random_z2_site_tensor, random_site_tensor
+    evens = (2, 3, 2, 2)
+    T = random_z2_site_tensor((4, 5, 4, 4), evens, seed=7)
+    with hotrg(4, 0.3, 0.0, 6, precision="bf16x3", fp64_steps=0, z2=True, max_steps=6) as f:
+        bad = T.copy()
+        bad[0, 0, 0, 3, 0, 0, 0, 0] = 1e-3          # one leg odd, all others even: odd total
+        with pytest.raises(HotrgError) as e:
+            f.set_tensor(bad, evens=evens)
+        assert e.value.code == _lib.HOTRG_EINVAL
+        f.set_tensor(T, evens=evens)
+        f.step(0)
+        blob = f.state_save()
+        f.step(1)
+        f.step(2)
+        want = f.get_tensor()
+        f.state_load(blob)
+        f.step(1)
+        f.step(2)
+        assert np.array_equal(f.get_tensor(), want)
+    # the dense path on the same tensor gives the same free-energy increments
+    with hotrg(4, 0.3, 0.0, 6, precision="bf16x3", fp64_steps=0, max_steps=6) as g:
+        g.set_tensor(T)
+        for ax in (0, 1, 2):
+            g.step(ax)
+        with hotrg(4, 0.3, 0.0, 6, precision="bf16x3", fp64_steps=0, z2=True, max_steps=6) as f:
+            f.set_tensor(T, evens=evens)
+            for ax in (0, 1, 2):
+                f.step(ax)
+            np.testing.assert_allclose(f.ln_norms()[1:], g.ln_norms()[1:], rtol=0, atol=1e-6)
+    with hotrg(4, 0.3, 0.0, 6, max_steps=6) as h:          # created without z2
+        with pytest.raises(HotrgError) as e:
+            h.set_tensor(T, evens=evens)
+        assert e.value.code == _lib.HOTRG_ESTATE
