@@ -20,7 +20,28 @@ struct LegInfo {
   int nrest;                     // number of remaining legs (2d - 2)
   int dim[kMaxLegs];             // remaining legs, natural order
   long long stride[kMaxLegs];
+  int ax[kMaxLegs];              // lattice axis of each remaining leg
+  int ax1, ax2;                  // axes of the two row legs
 };
+
+// Zero-field block structure (ev: the instance's even-value counts per axis, values ordered
+// even-parity first): row r = (i1, i2) has parity [i1 >= e1] ^ [i2 >= e2], and a column the
+// parity of its legs. Q vanishes between rows of different parity, and a row meets only the
+// columns of its own parity: with the rows in parity order (even rows first) each of the two
+// diagonal blocks is tiled on its own and sums over its parity's columns only, a quarter of
+// the dense work. The class sizes are known on the device only: the grid holds enough tiles for
+// a class of nr rows, and tiles beyond the actual class exit at once.
+__device__ __forceinline__ int gram_row_par(int r, int Da, int e1, int e2) {
+  return ((r / Da) >= e1 ? 1 : 0) ^ ((r % Da) >= e2 ? 1 : 0);
+}
+// natural row of the s-th row in parity order
+__device__ int gram_row_sorted(int s, int nr, int Da, int e1, int e2, int neven) {
+  const int want = s < neven ? 0 : 1;
+  int k = s < neven ? s : s - neven;
+  for (int r = 0; r < nr; ++r)
+    if (gram_row_par(r, Da, e1, e2) == want && k-- == 0) return r;
+  return 0;
+}
 
 // Output tiles of edge GT ((GT/4)^2 threads, 4 x 4 outputs each). With sym (TA = TB: Q is
 // symmetric) only the tiles on and above the diagonal are computed; the reduction mirrors the
@@ -31,7 +52,8 @@ __global__ void __launch_bounds__((GT / 4) * (GT / 4)) k_half_gram(const double*
                                                                    const double* __restrict__ TB, long long t_stride,
                                                                    LegInfo li, long long S1, long long S2, int Da,
                                                                    int nr, long long K, int ntile, int sym,
-                                                                   int nsplit, double* __restrict__ partial) {
+                                                                   int nsplit, double* __restrict__ partial,
+                                                                   const int* __restrict__ ev) {
   constexpr int NT = (GT / 4) * (GT / 4);
   TA += (long long)blockIdx.z * t_stride;
   TB += (long long)blockIdx.z * t_stride;
@@ -40,25 +62,69 @@ __global__ void __launch_bounds__((GT / 4) * (GT / 4)) k_half_gram(const double*
   __shared__ double Bs[GK][GT + 1];
   __shared__ long long coloff[GK];
   __shared__ long long rowoffA[GT], rowoffB[GT];
+  // zero-field blocks: per-leg even counts and the column layout of each parity pattern
+  __shared__ int e_rest[kMaxLegs];
+  __shared__ long long patsz[64];
   const int tid = threadIdx.x;
+  int e1 = 0, e2 = 0, neven = nr;
+  long long K0 = K;
+  int cls = 0, base = 0, ncls = nr;   // parity class of this tile (zero-field) and its row range
+  if (ev) {
+    ev += blockIdx.z * kMaxD;
+    e1 = ev[li.ax1];
+    e2 = ev[li.ax2];
+    neven = 0;
+    for (int r = 0; r < nr; ++r) neven += gram_row_par(r, Da, e1, e2) == 0;
+    if (tid < li.nrest) e_rest[tid] = ev[li.ax[tid]];
+    __syncthreads();
+    const int npat = 1 << li.nrest;
+    for (int pat = tid; pat < npat; pat += NT) {
+      long long sz = 1;
+      for (int l = 0; l < li.nrest; ++l) sz *= ((pat >> l) & 1) ? li.dim[l] - e_rest[l] : e_rest[l];
+      patsz[pat] = sz;
+    }
+    __syncthreads();
+    K0 = 0;
+    for (int pat = 0; pat < npat; ++pat)
+      if ((__popc(pat) & 1) == 0) K0 += patsz[pat];
+  }
   const int split = blockIdx.y;
+  const int tiles_per_cls = sym ? ntile * (ntile + 1) / 2 : ntile * ntile;
+  int t = blockIdx.x;
+  if (ev) {
+    cls = t / tiles_per_cls;
+    t %= tiles_per_cls;
+    base = cls ? neven : 0;
+    ncls = cls ? nr - neven : neven;
+  }
   int tr = 0, tc = 0;
   if (sym) {
-    int t = blockIdx.x;
     while (t >= ntile - tr) { t -= ntile - tr; ++tr; }
     tc = tr + t;
   } else {
-    tr = blockIdx.x / ntile;
-    tc = blockIdx.x % ntile;
+    tr = t / ntile;
+    tc = t % ntile;
   }
+  // tile rows / columns in class-local sorted order (the whole range without the block structure)
   const int r0 = tr * GT, c0 = tc * GT;
-  const long long kper = (K + nsplit - 1) / nsplit;
-  const long long kb = (long long)split * kper;
-  const long long ke = min(K, kb + kper);
-  for (int t = tid; t < GT; t += NT) {
-    const int ra = r0 + t, rb = c0 + t;
-    rowoffA[t] = ra < nr ? (long long)(ra / Da) * S1 + (long long)(ra % Da) * S2 : -1;
-    rowoffB[t] = rb < nr ? (long long)(rb / Da) * S1 + (long long)(rb % Da) * S2 : -1;
+  if (r0 >= ncls || c0 >= ncls) return;  // beyond this instance's class: no output (uniform per CTA)
+  long long cs = 0, ce = K;
+  const int colcls = ev ? cls : -1;
+  if (ev) {
+    cs = cls ? K0 : 0;
+    ce = cls ? K : K0;
+  }
+  const long long kper = (ce - cs + nsplit - 1) / nsplit;
+  const long long kb = cs + (long long)split * kper;
+  const long long ke = min(ce, kb + kper);
+  for (int q = tid; q < GT; q += NT) {
+    int ra = r0 + q, rb = c0 + q;
+    if (ev) {
+      ra = ra < ncls ? gram_row_sorted(base + ra, nr, Da, e1, e2, neven) : nr;
+      rb = rb < ncls ? gram_row_sorted(base + rb, nr, Da, e1, e2, neven) : nr;
+    }
+    rowoffA[q] = ra < nr ? (long long)(ra / Da) * S1 + (long long)(ra % Da) * S2 : -1;
+    rowoffB[q] = rb < nr ? (long long)(rb / Da) * S1 + (long long)(rb % Da) * S2 : -1;
   }
   const int tx = tid % (GT / 4), ty = tid / (GT / 4);
   double acc[4][4];
@@ -73,10 +139,29 @@ __global__ void __launch_bounds__((GT / 4) * (GT / 4)) k_half_gram(const double*
       long long off = -1;
       if (col < ke) {
         off = 0;
-        for (int l = li.nrest - 1; l >= 0; --l) {
-          const long long c = col % li.dim[l];
-          col /= li.dim[l];
-          off += c * li.stride[l];
+        if (colcls < 0) {
+          for (int l = li.nrest - 1; l >= 0; --l) {
+            const long long c = col % li.dim[l];
+            col /= li.dim[l];
+            off += c * li.stride[l];
+          }
+        } else {
+          // blocked order inside the class: patterns of that parity in increasing order, then
+          // row-major inside the pattern's box
+          long long local = col - (colcls ? K0 : 0);
+          int pat = 0;
+          for (; pat < (1 << li.nrest); ++pat) {
+            if ((__popc(pat) & 1) != colcls) continue;
+            if (local < patsz[pat]) break;
+            local -= patsz[pat];
+          }
+          for (int l = li.nrest - 1; l >= 0; --l) {
+            const int bit = (pat >> l) & 1;
+            const int dl = bit ? li.dim[l] - e_rest[l] : e_rest[l];
+            const long long c = local % dl;
+            local /= dl;
+            off += (c + (bit ? e_rest[l] : 0)) * li.stride[l];
+          }
         }
       }
       coloff[tid] = off;
@@ -104,30 +189,52 @@ __global__ void __launch_bounds__((GT / 4) * (GT / 4)) k_half_gram(const double*
     }
     __syncthreads();
   }
+  // partial sums at the rows' positions in parity order (base + class-local index)
   double* out = partial + (long long)split * nr * nr;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = r0 + ty * 4 + i;
-    if (r >= nr) continue;
+    if (r >= ncls) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = c0 + tx * 4 + j;
-      if (c < nr) out[(long long)r * nr + c] = acc[i][j];
+      if (c < ncls) out[(long long)(base + r) * nr + base + c] = acc[i][j];
     }
   }
 }
 
 // Q[e] = sum over the splits in a fixed order; with sym, entries below the diagonal tiles read
-// their mirror.
+// their mirror; with ev, the partial sums are in parity row order.
 __global__ void k_reduce_splits(const double* __restrict__ partial, int nsplit, int nr, int gt, int sym,
-                                double* __restrict__ Q, long long q_stride) {
+                                double* __restrict__ Q, long long q_stride, const int* __restrict__ ev,
+                                int ax1, int ax2, int Da) {
   const int nn = nr * nr;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nn) return;
   partial += (long long)blockIdx.y * nsplit * nn;
   Q += (long long)blockIdx.y * q_stride;
-  const int r = e / nr, c = e % nr;
-  const int src = (sym && r / gt > c / gt) ? c * nr + r : e;
+  int r = e / nr, c = e % nr;
+  int base = 0;
+  if (ev) {
+    // rows of different parity: zero; otherwise the class-local positions in parity order
+    const int e1 = ev[blockIdx.y * kMaxD + ax1], e2 = ev[blockIdx.y * kMaxD + ax2];
+    int neven = 0, br = 0, bc = 0;
+    const int pr = gram_row_par(r, Da, e1, e2), pc = gram_row_par(c, Da, e1, e2);
+    if (pr != pc) {
+      Q[e] = 0.0;
+      return;
+    }
+    for (int q = 0; q < nr; ++q) {
+      const int pq = gram_row_par(q, Da, e1, e2);
+      neven += pq == 0;
+      if (q < r && pq == pr) ++br;
+      if (q < c && pq == pc) ++bc;
+    }
+    base = pr ? neven : 0;
+    r = br;
+    c = bc;
+  }
+  const int src = (sym && r / gt > c / gt) ? (base + c) * nr + base + r : (base + r) * nr + base + c;
   double s = 0.0;
   for (int k = 0; k < nsplit; ++k) s += partial[(long long)k * nn + src];
   Q[e] = s;
@@ -212,15 +319,19 @@ static int nsplit_for(int nr, long long K, int batch, bool sym) {
 size_t gram_partial_doubles(int nr_max, int batch) {
   size_t best = 0;
   for (int nr = 1; nr <= nr_max; ++nr)
-    for (int sym = 0; sym < 2; ++sym) {
-      const size_t v = (size_t)batch * nsplit_for(nr, 1LL << 40, batch, sym != 0) * nr * nr;
-      if (v > best) best = v;
-    }
+    for (int sym = 0; sym < 2; ++sym)
+      for (int z2 = 0; z2 < 2; ++z2) {
+        // the zero-field launch splits as for half the rows but writes at full nr x nr positions
+        const int ns = z2 ? nsplit_for((nr + 1) / 2, 1LL << 40, batch, sym != 0)
+                          : nsplit_for(nr, 1LL << 40, batch, sym != 0);
+        const size_t v = (size_t)batch * ns * nr * nr;
+        if (v > best) best = v;
+      }
   return best;
 }
 
 void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, int l1, int l2, double* partial,
-                      double* Q, long long q_stride, cudaStream_t s, const double* TA) {
+                      double* Q, long long q_stride, cudaStream_t s, const double* TA, const int* z2ev) {
   const int d = g.d;
   auto leg_dim = [&](int l) { return g.D[l % d]; };
   auto leg_stride = [&](int l) { return l < d ? g.Sn[l] * g.P : g.Sn[l - d]; };
@@ -230,29 +341,36 @@ void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, in
     if (l == l1 || l == l2) continue;
     li.dim[li.nrest] = leg_dim(l);
     li.stride[li.nrest] = leg_stride(l);
+    li.ax[li.nrest] = l % d;
     ++li.nrest;
   }
+  li.ax1 = l1 % d;
+  li.ax2 = l2 % d;
   const int Da = leg_dim(l2);
   const int nr = leg_dim(l1) * Da;
   const long long K = g.P * g.P / nr;
   const bool sym = TA == nullptr || TA == T;
-  const int gt = gram_tile(nr, sym);
+  // zero-field: each parity class is tiled on its own, for about half the rows (a class may
+  // hold up to nr rows: ntile covers that, the tiles beyond the actual class exit)
+  const int gt = z2ev ? gram_tile((nr + 1) / 2, sym) : gram_tile(nr, sym);
   const int ntile = (nr + gt - 1) / gt;
-  const int nsplit = nsplit_for(nr, K, batch, sym);
-  dim3 grid(gram_tiles(nr, sym, gt), nsplit, batch);
+  const int nsplit = z2ev ? nsplit_for((nr + 1) / 2, K / 2, batch, sym) : nsplit_for(nr, K, batch, sym);
+  dim3 grid((z2ev ? 2 : 1) * (sym ? ntile * (ntile + 1) / 2 : ntile * ntile), nsplit, batch);
   const double* A = TA ? TA : T;
   switch (gt) {
 #define HOTRG_GRAM(GT_)                                                                                        \
   case GT_:                                                                                                    \
     k_half_gram<GT_><<<grid, (GT_ / 4) * (GT_ / 4), 0, s>>>(A, T, t_stride, li, leg_stride(l1), leg_stride(l2), \
-                                                            Da, nr, K, ntile, sym ? 1 : 0, nsplit, partial);     \
+                                                            Da, nr, K, ntile, sym ? 1 : 0, nsplit, partial,      \
+                                                            z2ev);                                               \
     break;
     HOTRG_GRAM(36) HOTRG_GRAM(44) HOTRG_GRAM(52) HOTRG_GRAM(60) HOTRG_GRAM(64)
 #undef HOTRG_GRAM
   }
   count_launches(1);
   const int nn = nr * nr;
-  k_reduce_splits<<<dim3((nn + 255) / 256, batch), 256, 0, s>>>(partial, nsplit, nr, gt, sym ? 1 : 0, Q, q_stride);
+  k_reduce_splits<<<dim3((nn + 255) / 256, batch), 256, 0, s>>>(partial, nsplit, nr, gt, sym ? 1 : 0, Q, q_stride,
+                                                                 z2ev, li.ax1, li.ax2, Da);
   count_launches(1);
 }
 

@@ -1054,8 +1054,9 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
       const int n = g.D[b] * g.D[b];
       double* Gb = c->G + (long long)b * (c->g_stride / kMaxD);
       double* Ub = c->U + (long long)b * kMaxBond * kMaxGram;
-      launch_half_gram(c->T, P2max, c->batch, g, b, c->d + a, c->gpartial, c->Q1, c->q_stride, s);
-      launch_half_gram(c->T, P2max, c->batch, g, b, a, c->gpartial, c->Q2, c->q_stride, s);
+      const int* zev = c->z2 ? c->z2ev : nullptr;
+      launch_half_gram(c->T, P2max, c->batch, g, b, c->d + a, c->gpartial, c->Q1, c->q_stride, s, nullptr, zev);
+      launch_half_gram(c->T, P2max, c->batch, g, b, a, c->gpartial, c->Q2, c->q_stride, s, nullptr, zev);
       launch_gram_combine(c->Q1, c->Q2, c->q_stride, c->batch, g.D[b], g.D[a], Gb, c->g_stride, s);
       EigOut eo{c->spec_log + (long long)b * kSpecCap, c->spec_stride, (long long)c->d * kSpecCap, c->dstep,
                 c->max_steps};

@@ -83,9 +83,11 @@ void prepare_kernel_attributes();
 // Instance i reads T + i*t_stride and writes Q + i*q_stride.
 size_t gram_partial_doubles(int nr_max, int batch);  // scratch for `partial`
 // With TA: rows from TA (same layout and strides as T), columns from T: Q(TA, T).
+// With z2ev ([batch][kMaxD] even-value counts, values ordered even-parity first), the zero-field
+// block structure is used: a quarter of the work (see gram.cu).
 void launch_half_gram(const double* T, long long t_stride, int batch, Geom g, int l1, int l2,
                       double* partial, double* Q, long long q_stride, cudaStream_t s,
-                      const double* TA = nullptr);
+                      const double* TA = nullptr, const int* z2ev = nullptr);
 // G[(b1 b2)][(b1~ b2~)] = sum_{al,al~} Q1[(b1,al)][(b1~,al~)] Q2[(b2,al)][(b2~,al~)] per instance
 void launch_gram_combine(const double* Q1, const double* Q2, long long q_stride, int batch, int Db,
                          int Da, double* G, long long g_stride, cudaStream_t s);

@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, P
     park[threadIdx.x] = k < P ? (rank_tab[k] >= ncls0 ? 1 : 0) : 0;
   }
   __syncthreads();
-  // the thread's four loads first, then the stores
+  // the thread's four loads first, then the stores (reads along m share L1 sectors between the
+  // tile's rows when X is contiguous along m)
   float v[4];
   bool w[4];
   const long long k = k0 + threadIdx.x;
