@@ -28,19 +28,20 @@ __device__ void sm_red_sum(double* sred, double v, int tid) {
   }
 }
 
-__global__ void __launch_bounds__(kEigThreads) k_jacobi(const double* __restrict__ G, long long g_stride, int n,
-                                                        int chi, EigOut o, double* __restrict__ Uout,
-                                                        long long u_stride, double* __restrict__ work,
-                                                        int* status, const int* z2_ev, int* z2_ev_new,
-                                                        int z2_axis, int Db) {
+// One CTA per (instance = blockIdx.x, axis = blockIdx.y): the Gram matrices of all transverse
+// axes of a step are diagonalised in one launch.
+__global__ void __launch_bounds__(kEigThreads) k_jacobi(EigAxes ea, int* status, const int* z2_ev, int* z2_ev_new) {
   extern __shared__ double sm[];
-  G += (long long)blockIdx.x * g_stride;
-  Uout += (long long)blockIdx.x * u_stride;
-  work += (long long)blockIdx.x * 2 * n * n;
+  const EigAxis& ax = ea.ax[blockIdx.y];
+  const int n = ax.n, chi = ax.chi, z2_axis = ax.z2_axis, Db = ax.Db > 0 ? ax.Db : 1;
+  const double* G = ax.G + (long long)blockIdx.x * ea.g_stride;
+  double* Uout = ax.U + (long long)blockIdx.x * ea.u_stride;
+  double* work = ax.work + (long long)blockIdx.x * 2 * n * n;
+  const EigOut& o = ea.out;
   // eigenvalue log slot of this instance for the current step (device step counter, 1-based)
   const int step = o.step ? *o.step : 1;
   double* evals = (step >= 1 && step <= o.max_steps)
-                      ? o.base + (long long)blockIdx.x * o.inst_stride + (long long)(step - 1) * o.step_stride
+                      ? ax.evals + (long long)blockIdx.x * o.inst_stride + (long long)(step - 1) * o.step_stride
                       : nullptr;
   const int tid = threadIdx.x;
   const int np = n + (n & 1);          // padded to even (index n is a dummy)
@@ -293,12 +294,24 @@ void prepare_eig_attributes() {
   cudaFuncSetAttribute(k_eig_tangent, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
+void launch_eig_axes(const EigAxes& ea, int batch, int* status, cudaStream_t s, const int* z2_ev, int* z2_ev_new) {
+  if (ea.nt < 1) return;
+  const size_t smem = sizeof(double) * (128 + 128 + 128 + 128 + kEigThreads);
+  k_jacobi<<<dim3(batch, ea.nt), kEigThreads, smem, s>>>(ea, status, z2_ev, z2_ev_new);
+  count_launches(1);
+}
+
 void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o, double* U,
                 long long u_stride, double* work, int* status, cudaStream_t s, const int* z2_ev, int* z2_ev_new,
                 int z2_axis, int Db) {
+  EigAxes ea;
+  ea.nt = 1;
+  ea.g_stride = g_stride;
+  ea.u_stride = u_stride;
+  ea.out = o;
+  ea.ax[0] = EigAxis{G, n, chi, z2_axis, Db, o.base, U, work};
   const size_t smem = sizeof(double) * (128 + 128 + 128 + 128 + kEigThreads);
-  k_jacobi<<<batch, kEigThreads, smem, s>>>(G, g_stride, n, chi, o, U, u_stride, work, status, z2_ev, z2_ev_new,
-                                            z2_axis, Db > 0 ? Db : 1);
+  k_jacobi<<<dim3(batch, 1), kEigThreads, smem, s>>>(ea, status, z2_ev, z2_ev_new);
   count_launches(1);
 }
 

@@ -48,6 +48,7 @@ struct hotrg_ctx {
   double *lnc_log = nullptr, *spec_log = nullptr, *out3 = nullptr, *cval = nullptr;
   double *norm_partial = nullptr, *gpartial = nullptr, *Q1 = nullptr, *Q2 = nullptr;
   double *G = nullptr, *U = nullptr, *ework = nullptr;
+  long long ework_axis = 0;  // doubles of ework per axis (batch x 2 n_max^2)
   int* status = nullptr;
   int* dstep = nullptr;       // device-side step counter (steps done)
   // tangents d/d beta (0) and d/d h (1) of the flow: deriv_mode 1 holds the isometries fixed,
@@ -286,7 +287,8 @@ size_t carve(hotrg_ctx* c, char* base) {
   c->Q2 = k.take<double>(sizeof(double) * c->q_stride * c->batch);
   c->G = k.take<double>(sizeof(double) * c->g_stride * c->batch);
   c->U = k.take<double>(sizeof(double) * c->u_stride * c->batch);
-  c->ework = k.take<double>(sizeof(double) * 2 * nmax * nmax * c->batch);
+  c->ework_axis = 2LL * nmax * nmax * c->batch;
+  c->ework = k.take<double>(sizeof(double) * c->ework_axis * kMaxD);  // one area per axis
   (void)nr_max;
   if (c->deriv) {
     c->dT = k.take<double>(sizeof(double) * 2 * P2 * c->batch);
@@ -1049,12 +1051,30 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
   // 1. isometries of every instance (batched launches: one CTA group per instance)
   {
     PhaseScope iso_scope(c, PH_ISO);
-    for (int t = 0; t < nt; ++t) {
+    const int* zev = c->z2 ? c->z2ev : nullptr;
+    if (c->deriv_mode != 2 && nt > 0) {
+      // every transverse axis' Gram matrix, then one eigensolver launch for all of them
+      EigAxes ea;
+      ea.nt = nt;
+      ea.g_stride = c->g_stride;
+      ea.u_stride = c->u_stride;
+      ea.out = EigOut{nullptr, c->spec_stride, (long long)c->d * kSpecCap, c->dstep, c->max_steps};
+      for (int t = 0; t < nt; ++t) {
+        const int b = trans[t];
+        double* Gb = c->G + (long long)b * (c->g_stride / kMaxD);
+        launch_half_gram(c->T, P2max, c->batch, g, b, c->d + a, c->gpartial, c->Q1, c->q_stride, s, nullptr, zev);
+        launch_half_gram(c->T, P2max, c->batch, g, b, a, c->gpartial, c->Q2, c->q_stride, s, nullptr, zev);
+        launch_gram_combine(c->Q1, c->Q2, c->q_stride, c->batch, g.D[b], g.D[a], Gb, c->g_stride, s);
+        ea.ax[t] = EigAxis{Gb, g.D[b] * g.D[b], chi[b], b, g.D[b], c->spec_log + (long long)b * kSpecCap,
+                           c->U + (long long)b * kMaxBond * kMaxGram, c->ework + t * c->ework_axis};
+      }
+      launch_eig_axes(ea, c->batch, c->status, s, zev, c->z2ev_new);
+    }
+    for (int t = 0; t < nt && c->deriv_mode == 2; ++t) {
       const int b = trans[t];
       const int n = g.D[b] * g.D[b];
       double* Gb = c->G + (long long)b * (c->g_stride / kMaxD);
       double* Ub = c->U + (long long)b * kMaxBond * kMaxGram;
-      const int* zev = c->z2 ? c->z2ev : nullptr;
       launch_half_gram(c->T, P2max, c->batch, g, b, c->d + a, c->gpartial, c->Q1, c->q_stride, s, nullptr, zev);
       launch_half_gram(c->T, P2max, c->batch, g, b, a, c->gpartial, c->Q2, c->q_stride, s, nullptr, zev);
       launch_gram_combine(c->Q1, c->Q2, c->q_stride, c->batch, g.D[b], g.D[a], Gb, c->g_stride, s);

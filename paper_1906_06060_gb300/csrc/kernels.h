@@ -108,6 +108,25 @@ struct EigOut {
 // Symmetric eigendecomposition of G (n x n, n <= 256) by cyclic Jacobi, one CTA per instance;
 // eigenvalues sorted descending, the leading chi eigenvectors, sign-fixed, into U[k][0..n).
 // work: batch * 2*n*n doubles. Sets ST_NOCONV on the sweep limit.
+// Several axes in one launch (blockIdx.y = axis): per axis its Gram matrices G (+ instance x
+// g_stride), size n, kept count chi, the axis and Db for the zero-field ordering, the eigenvalue
+// log base (+ instance x out.inst_stride + (step - 1) x out.step_stride), U (+ instance x u_stride)
+// and a work area of batch x 2 n^2 doubles.
+struct EigAxis {
+  const double* G;
+  int n, chi, z2_axis, Db;
+  double* evals;
+  double* U;
+  double* work;
+};
+struct EigAxes {
+  int nt;
+  long long g_stride, u_stride;
+  EigOut out;  // strides, step counter and step limit (its base is unused here)
+  EigAxis ax[kMaxD];
+};
+void launch_eig_axes(const EigAxes& ea, int batch, int* status, cudaStream_t s, const int* z2_ev = nullptr,
+                     int* z2_ev_new = nullptr);
 // z2_ev (non-null): zero-field flow: [batch][kMaxD] even counts of the legs; the kept vectors of
 // axis z2_axis (Db x Db fused index) are written even-parity first (each group in descending
 // eigenvalue order), z2_ev_new[i][z2_axis] = number of even ones; a vector that is not
