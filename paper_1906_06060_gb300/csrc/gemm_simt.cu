@@ -9,21 +9,38 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
+// With blk (block-sparse product), blockIdx.z picks the block: its rows [m0, m0+mc), columns
+// [n0, n0+nc) and k range [k0, k0+kc); CTAs whose tile lies outside the block return at once.
 __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, long long lda,
                                                   const double* __restrict__ Bt, long long ldb,
                                                   double* __restrict__ C, long long ldc, long long M,
-                                                  long long N, long long K) {
+                                                  long long N, long long K, const GemmBlocks* __restrict__ blk) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
-  const long long m0 = (long long)blockIdx.y * BM, n0 = (long long)blockIdx.x * BN;
+  long long mb = 0, nb = 0, kb = 0;
+  if (blk) {
+    const int b = blockIdx.z;
+    if (b >= blk->nb) return;
+    mb = min((long long)max(blk->m0[b], 0), M);
+    nb = min((long long)max(blk->n0[b], 0), N);
+    kb = min((long long)max(blk->k0[b], 0), K);
+    const long long mc = min((long long)max(blk->mc[b], 0), M - mb);
+    const long long nc = min((long long)max(blk->nc[b], 0), N - nb);
+    const long long kc = min((long long)max(blk->kc[b], 0), K - kb);
+    if ((long long)blockIdx.y * BM >= mc || (long long)blockIdx.x * BN >= nc) return;
+    M = mb + mc;
+    N = nb + nc;
+    K = kb + kc;
+  }
+  const long long m0 = mb + (long long)blockIdx.y * BM, n0 = nb + (long long)blockIdx.x * BN;
   const int tx = tid % 16, ty = tid / 16;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (long long k0 = 0; k0 < K; k0 += BK) {
+  for (long long k0 = kb; k0 < K; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < (BM * BK) / 256; ++q) {
       const int e = tid + 256 * q;
@@ -63,9 +80,10 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, 
 }  // namespace
 
 void launch_gemm_f64(const double* A, long long lda, const double* Bt, long long ldb, double* C,
-                     long long ldc, long long M, long long N, long long K, cudaStream_t s) {
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
-  k_gemm_f64<<<grid, 256, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K);
+                     long long ldc, long long M, long long N, long long K, cudaStream_t s, const GemmBlocks* blk) {
+  // block-sparse: enough tiles for a block as large as the whole product, two blocks
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), blk ? 2 : 1);
+  k_gemm_f64<<<grid, 256, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, blk);
   count_launches(1);
 }
 

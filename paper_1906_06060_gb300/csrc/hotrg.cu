@@ -139,7 +139,7 @@ StepNeeds needs_for(int d, const int* dims, int a, int Dcut, int planes) {
   const long long P = g.P;
   // operand rows: P rounded up to 64, plus one more 64-column block for the zero-field
   // (parity-blocked) layout, whose two k classes start at 64-aligned columns
-  const long long ldk = mixed ? round_up(P, 64) + 64 : P;
+  const long long ldk = round_up(P, 64) + 64;
   int chi[kMaxD];
   int trans[kMaxD], nt = 0;
   for (int b = 0; b < d; ++b) {
@@ -451,12 +451,12 @@ Contraction plan_contraction(const std::vector<Ax>& axes, int b, int chi_b, cons
 }
 
 // The first contraction of a chunk's epilogue from the parity-blocked GEMM output (z2.cu).
-template <class Tout>
-void contract_axes_z2(std::vector<Ax>& axes, const float* O, long long ldO, Tout* out, int b, int chi_b,
+template <class Tin, class Tout>
+void contract_axes_z2(std::vector<Ax>& axes, const Tin* O, long long ldO, Tout* out, int b, int chi_b,
                       const double* Ub, const long long* final_out_stride, long long out_base,
                       const Z2Layout* L, const int* pi, cudaStream_t s) {
   Contraction r = plan_contraction(axes, b, chi_b, final_out_stride);
-  launch_epi_z2<Tout>(O, ldO, out, r.rest, r.sk, out_base, b, axes[r.im].dim, Ub, chi_b, L, pi, s);
+  launch_epi_z2<Tin, Tout>(O, ldO, out, r.rest, r.sk, out_base, b, axes[r.im].dim, Ub, chi_b, L, pi, s);
   axes = r.out_axes;
 }
 
@@ -765,12 +765,15 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   return HOTRG_OK;
 }
 
-// The zero-field squeeze of T with itself on the tensor cores (z2.cu): parity-blocked operands,
-// two dense GEMM blocks per chunk, the first epilogue contraction reading the blocked output.
-// Same output as squeeze<float>(c, T, T, out, ...) up to the order of FP32 summation.
+// The zero-field squeeze of T with itself (z2.cu): parity-blocked operands, two dense GEMM
+// blocks per chunk, the first epilogue contraction reading the blocked output. TC = float: the
+// tensor-core path (bf16 planes, npass split products); TC = double: the FP64 path. Same output
+// as squeeze<TC>(c, T, T, out, ...) up to the order of summation.
+template <class TC>
 int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const double* U, const Geom& g,
                const Geom& gn, int a, const int* chi, const int* trans, int nt, int planes, int npass) {
-  using Op = __nv_bfloat16;
+  using Op = typename Ops<TC>::Op;
+  constexpr bool mixed = std::is_same<TC, float>::value;
   cudaStream_t s = c->stream;
   const long long P = g.P;
   const long long ldz = round_up(P, 64) + 64;
@@ -781,7 +784,7 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
   if (need.Tt > c->sz_Tt || need.Bt > c->sz_Bt || need.X > c->sz_X || need.Y > c->sz_Y || need.O > c->sz_O ||
       need.R1 > c->sz_R1 || need.R2 > c->sz_R2 || P > c->Pmax)
     return HOTRG_ENOMEM;
-  const int nparts = planes;
+  const int nparts = mixed ? planes : 1;
   const long long bt_plane = (long long)chi3 * P * ldz, y_plane = P * ldz;
   auto pl = [&](void* base, long long plane_elems) {
     Planes<Op> q;
@@ -798,11 +801,12 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
   // zeros between and after the k classes (the GEMM's k-blocks run over them)
   cudaMemsetAsync(c->Bt, 0, sizeof(Op) * nparts * bt_plane, s);
   cudaMemsetAsync(c->Y, 0, sizeof(Op) * nparts * y_plane, s);
-  float* Tt = static_cast<float*>(c->Tt);
-  launch_transpose<float>(T, Tt, P, s);
-  launch_build_bt_z2(Tt, pl(c->Bt, bt_plane), ldz, g, c3, Ub(c3), chi3, c->z2rank, c->z2kcol, c->z2colpos, L, s);
+  TC* Tt = static_cast<TC*>(c->Tt);
+  launch_transpose<TC>(T, Tt, P, s);
+  launch_build_bt_z2<TC, Op>(Tt, pl(c->Bt, bt_plane), ldz, g, c3, Ub(c3), chi3, c->z2rank, c->z2kcol, c->z2colpos,
+                             L, s);
   delete ops_scope;
-  float* O = static_cast<float*>(c->O);
+  TC* O = static_cast<TC*>(c->O);
   const int no = nt - 1;
   int kcnt[kMaxD] = {0, 0, 0, 0};
   long long nchunks = 1;
@@ -816,30 +820,35 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
     }
     ops_scope = new PhaseScope(c, PH_OPERANDS);
     launch_z2_chunk(L, ev_new, no, no > 0 ? trans[0] : 0, kcnt[0], no > 1 ? trans[1] : 0, kcnt[1], ldO, c->z2blk,
-                    c->z2pi, c->z2flops, npass, s);
+                    c->z2pi, c->z2flops, mixed ? npass : 1, s);
     if (no == 0) {
-      launch_build_y_z2<double>(T, pl(c->Y, y_plane), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
+      launch_build_y_z2<double, Op>(T, pl(c->Y, y_plane), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
     } else {
-      float* X1 = static_cast<float*>(c->X1);
-      float* X2 = static_cast<float*>(c->X2);
+      TC* X1 = static_cast<TC*>(c->X1);
+      TC* X2 = static_cast<TC*>(c->X2);
       if (kcnt[0] != prev_k0) {
-        launch_mode_unprimed<double, float>(T, X1, g, trans[0], Ub(trans[0]), kcnt[0], s);
+        launch_mode_unprimed<double, TC>(T, X1, g, trans[0], Ub(trans[0]), kcnt[0], s);
         prev_k0 = kcnt[0];
       }
-      const float* X = X1;
+      const TC* X = X1;
       if (no >= 2) {
-        launch_mode_unprimed<float, float>(X1, X2, g, trans[1], Ub(trans[1]), kcnt[1], s);
+        launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(trans[1]), kcnt[1], s);
         X = X2;
       }
-      launch_build_y_z2<float>(X, pl(c->Y, y_plane), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
+      launch_build_y_z2<TC, Op>(X, pl(c->Y, y_plane), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
     }
     delete ops_scope;
     {
       PhaseScope gemm_scope(c, PH_GEMM);
-      const int rc = launch_gemm_split(pl(c->Y, y_plane), ldz, pl(c->Bt, bt_plane), ldz, O, ldO, P, ldO, ldz, npass,
-                                       c->status, c->timeout_s, s, c->kblock, c->group_m, fold_group_for(c, npass),
-                                       c->z2blk);
-      if (rc) return rc;
+      if constexpr (mixed) {
+        const int rc = launch_gemm_split(pl(c->Y, y_plane), ldz, pl(c->Bt, bt_plane), ldz, O, ldO, P, ldO, ldz,
+                                         npass, c->status, c->timeout_s, s, c->kblock, c->group_m,
+                                         fold_group_for(c, npass), c->z2blk);
+        if (rc) return rc;
+      } else {
+        launch_gemm_f64(pl(c->Y, y_plane).p[0], ldz, pl(c->Bt, bt_plane).p[0], ldz, O, ldO, P, ldO, ldz, s,
+                        c->z2blk);
+      }
       // the blocks' flops are counted on the device (k_z2_chunk)
       if (c->timing) {
         ++c->t_gemm_launches;
@@ -853,22 +862,22 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
     for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
     long long out_base = 0;
     for (int i = 0; i < no; ++i) out_base += (long long)kcnt[i] * gn.Sn[trans[i]] * gn.P;
-    float* bufs[2] = {static_cast<float*>(c->R1), static_cast<float*>(c->R2)};
+    TC* bufs[2] = {static_cast<TC*>(c->R1), static_cast<TC*>(c->R2)};
     long long fs[kMaxAxes];
     if (no == 0) {
       final_strides(axes, c3, c3, gn, c3, fs);
-      contract_axes_z2<double>(axes, O, ldO, out, c3, chi3, Ub(c3), fs, out_base, L, c->z2pi, s);
+      contract_axes_z2<TC, double>(axes, O, ldO, out, c3, chi3, Ub(c3), fs, out_base, L, c->z2pi, s);
       continue;
     }
-    contract_axes_z2<float>(axes, O, ldO, bufs[0], trans[0], chi[trans[0]], Ub(trans[0]), nullptr, 0, L, c->z2pi,
-                            s);
-    const float* cur = bufs[0];
+    contract_axes_z2<TC, TC>(axes, O, ldO, bufs[0], trans[0], chi[trans[0]], Ub(trans[0]), nullptr, 0, L, c->z2pi,
+                             s);
+    const TC* cur = bufs[0];
     for (int i = 1; i < no; ++i) {
-      contract_axes<float, float>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(trans[i]), nullptr, 0, s);
+      contract_axes<TC, TC>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(trans[i]), nullptr, 0, s);
       cur = bufs[i];
     }
     final_strides(axes, c3, c3, gn, c3, fs);
-    contract_axes<float, double>(axes, cur, out, c3, chi3, Ub(c3), fs, out_base, s);
+    contract_axes<TC, double>(axes, cur, out, c3, chi3, Ub(c3), fs, out_base, s);
   }
   return HOTRG_OK;
 }
@@ -1108,8 +1117,9 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
         tg.dU[w] = c->deriv_mode == 2 ? c->dU + (w * c->batch + i) * c->u_stride : nullptr;
       }
     }
-    int rc = (planes && c->z2 && nt > 0)
-                 ? squeeze_z2(c, i, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass)
+    int rc = (c->z2 && nt > 0)
+                 ? (planes ? squeeze_z2<float>(c, i, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass)
+                           : squeeze_z2<double>(c, i, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0))
              : planes ? squeeze<float>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass, tg)
                       : squeeze<double>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0, tg);
     if (rc) return rc;
@@ -1156,7 +1166,7 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
     for (int t = 0; t < nt; ++t) f *= chi[trans[t]];
     c->t_dense_step_flops += f;
     // parity-blocked steps add what their GEMM blocks computed, counted on the device
-    if (!(planes && c->z2 && nt > 0)) c->t_step_flops += f;
+    if (!(c->z2 && nt > 0)) c->t_step_flops += f;
     ++c->t_steps;
   }
   return HOTRG_OK;

@@ -146,8 +146,12 @@ void prepare_eig_attributes();  // shared-memory limit of the tangent kernel (on
 
 // ---- gemm_simt.cu --------------------------------------------------------------------------
 // C[m][n] = sum_k A[m][k] Bt[n][k] in FP64 (CUDA cores).
+// With blk (device memory, see GemmBlocks below), only the listed output blocks are computed, each
+// over its own k range; M, N are then the extents of A's and Bt's rows.
+struct GemmBlocks;
 void launch_gemm_f64(const double* A, long long lda, const double* Bt, long long ldb, double* C,
-                     long long ldc, long long M, long long N, long long K, cudaStream_t s);
+                     long long ldc, long long M, long long N, long long K, cudaStream_t s,
+                     const GemmBlocks* blk = nullptr);
 
 // ---- gemm_tc.cu ----------------------------------------------------------------------------
 // C[m][n] = sum over passes p of sum_k A_{a(p)}[m][k] Bt_{b(p)}[n][k], bf16 operand planes on
@@ -200,16 +204,17 @@ void launch_z2_chunk(const Z2Layout* L, const int* ev_new, int nfix, int b0, int
                      GemmBlocks* blk, int* pi, double* flops, int npass, cudaStream_t s);
 // ev[i][b] = ev_new[i][b] for the axes b in trans_mask (end of a step).
 void launch_z2_advance(int* ev, const int* ev_new, int batch, unsigned trans_mask, cudaStream_t s);
-template <class Tin>
-void launch_build_y_z2(const Tin* X, const Planes<__nv_bfloat16>& out, long long ld, Geom g, int a,
+template <class Tin, class Tout>
+void launch_build_y_z2(const Tin* X, const Planes<Tout>& out, long long ld, Geom g, int a,
                        const int* rank_tab, const int* kcol_tab, const Z2Layout* L, const int* pi, cudaStream_t s);
-void launch_build_bt_z2(const float* Tt, const Planes<__nv_bfloat16>& out, long long ld, Geom g, int c3,
-                        const double* U3, int chi3, const int* rank_tab, const int* kcol_tab, const int* colpos_tab,
-                        const Z2Layout* L, cudaStream_t s);
+template <class Tin, class Tout>
+void launch_build_bt_z2(const Tin* Tt, const Planes<Tout>& out, long long ld, Geom g, int c3, const double* U3,
+                        int chi3, const int* rank_tab, const int* kcol_tab, const int* colpos_tab, const Z2Layout* L,
+                        cudaStream_t s);
 // First epilogue contraction (over slot t0, Dt x Dt -> chi) from the parity-blocked GEMM output;
 // rest / sk / out_base as for launch_pair_contract_all.
-template <class Tout>
-void launch_epi_z2(const float* O, long long ldO, Tout* out, const View& rest, long long sk, long long out_base,
+template <class Tin, class Tout>
+void launch_epi_z2(const Tin* O, long long ldO, Tout* out, const View& rest, long long sk, long long out_base,
                    int t0, int Dt, const double* U, int chi, const Z2Layout* L, const int* pi, cudaStream_t s);
 
 }  // namespace hotrg

@@ -23,6 +23,10 @@ namespace {
 
 __device__ __forceinline__ int popc4(int x) { return __popc(x & 15); }
 
+// arithmetic type of a path: FP64 path in double, tensor-core path (bf16 planes, FP32 output) in float
+template <class T>
+using ZAcc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+
 // natural P-index -> digits (slot 0 slowest) and leg-parity pattern (bit b = digit_b >= e_b)
 __device__ __forceinline__ int z2_digits(const Z2Layout& L, int idx, int* dig) {
   int pat = 0;
@@ -148,8 +152,8 @@ __global__ void k_z2_advance(int* ev, const int* ev_new, int batch, unsigned tra
 
 // A operand of one chunk, parity-blocked: Y[rank(m)][kcol(k)] = X[R(k) + C(m)] where
 // parity(m) + parity(k) = pi (the other entries of X are zero and not stored).
-template <class Tin>
-__global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, Planes<__nv_bfloat16> out,
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, Planes<Tout> out,
                                                     long long ld, Geom g, int a, const int* __restrict__ rank_tab,
                                                     const int* __restrict__ kcol_tab, const Z2Layout* Lp,
                                                     const int* pi_ptr) {
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, P
   __syncthreads();
   // the thread's four loads first, then the stores (reads along m share L1 sectors between the
   // tile's rows when X is contiguous along m)
-  float v[4];
+  ZAcc<Tout> v[4];
   bool w[4];
   const long long k = k0 + threadIdx.x;
 #pragma unroll
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, P
     const int r = threadIdx.y + 8 * q;
     const long long m = m0 + r;
     w[q] = m < P && k < P && (parm[r] ^ park[threadIdx.x]) == pi;
-    v[q] = w[q] ? (float)X[Rk[threadIdx.x] + Cm[r]] : 0.f;
+    v[q] = w[q] ? (ZAcc<Tout>)X[Rk[threadIdx.x] + Cm[r]] : (ZAcc<Tout>)0;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -197,15 +201,17 @@ __global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, P
 
 // B operand, parity-blocked: Bt[colpos(j, n)][kcol(k)] = sum_x U3[j][k_c3][x] Tt[n][k | c3 := x]
 // where parity(j) + parity(n) = parity(k).
-template <class Tin>
-__global__ void __launch_bounds__(256) k_build_bt_z2(const Tin* __restrict__ Tt, Planes<__nv_bfloat16> out,
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(256) k_build_bt_z2(const Tin* __restrict__ Tt, Planes<Tout> out,
                                                      long long ld, long long P, long long Sc, int Dc,
                                                      const double* __restrict__ U3, int chi3,
                                                      const int* __restrict__ rank_tab, const int* __restrict__ kcol_tab,
                                                      const int* __restrict__ colpos_tab, const Z2Layout* Lp) {
-  extern __shared__ float W[];  // [chi3][Dc][Dc]
+  using Acc = ZAcc<Tout>;
+  extern __shared__ unsigned char smraw_bt[];
+  Acc* W = reinterpret_cast<Acc*>(smraw_bt);  // [chi3][Dc][Dc]
   const int nW = chi3 * Dc * Dc;
-  for (int t = threadIdx.x; t < nW; t += blockDim.x) W[t] = (float)U3[t];
+  for (int t = threadIdx.x; t < nW; t += blockDim.x) W[t] = (Acc)U3[t];
   __syncthreads();
   const int ncls0 = Lp->ncls[0];
   const int goff1 = Lp->goff[1];
@@ -222,9 +228,9 @@ __global__ void __launch_bounds__(256) k_build_bt_z2(const Tin* __restrict__ Tt,
     const int j = (int)(row / P);
     const int kc = (int)((k / Sc) % Dc);
     const long long base = n * P + k - (long long)kc * Sc;
-    const float* w = W + ((long long)j * Dc + kc) * Dc;
-    float acc = 0.f;
-    for (int x = 0; x < Dc; ++x) acc += w[x] * (float)Tt[base + x * Sc];
+    const Acc* w = W + ((long long)j * Dc + kc) * Dc;
+    Acc acc = 0;
+    for (int x = 0; x < Dc; ++x) acc += w[x] * (Acc)Tt[base + x * Sc];
     store_planes(out, (long long)cp * ld + kcol_tab[k], acc);
   }
 }
@@ -235,12 +241,14 @@ __global__ void __launch_bounds__(256) k_build_bt_z2(const Tin* __restrict__ Tt,
 // order, shaped and strided by `rest` (out_stride) and sk (stride of k'). Only the (i, jj)
 // parity combinations of the chunk's two computed blocks are read; the rest of O is zero.
 // CHI = chi (compile-time: exact accumulator count, no predicated FMAs).
-template <class Tout, int CHI>
-__global__ void __launch_bounds__(256) k_epi_z2(const float* __restrict__ O, long long ldO, Tout* __restrict__ out,
+template <class Tin, class Tout, int CHI>
+__global__ void __launch_bounds__(256) k_epi_z2(const Tin* __restrict__ O, long long ldO, Tout* __restrict__ out,
                                                 View rest, int total, long long sk, long long out_base,
                                                 int t0, const double* __restrict__ U,
                                                 const Z2Layout* Lp, const int* pi_ptr) {
-  extern __shared__ float W[];  // [D*D][CHI]
+  using Acc = ZAcc<Tin>;
+  extern __shared__ unsigned char smraw_epi[];
+  Acc* W = reinterpret_cast<Acc*>(smraw_epi);  // [D*D][CHI]
   __shared__ Z2Layout L;
   __shared__ int shape[2 * kMaxD + 1];
   __shared__ long long ostr[2 * kMaxD + 1];
@@ -253,7 +261,7 @@ __global__ void __launch_bounds__(256) k_epi_z2(const float* __restrict__ O, lon
   const int nij = Dt * Dt;
   for (int t = threadIdx.x; t < CHI * nij; t += blockDim.x) {
     const int k = t / nij, ij = t % nij;
-    W[ij * CHI + k] = (float)U[t];
+    W[ij * CHI + k] = (Acc)U[t];
   }
   __syncthreads();
   const int pi = *pi_ptr;
@@ -298,9 +306,9 @@ __global__ void __launch_bounds__(256) k_epi_z2(const float* __restrict__ O, lon
     }
     const int pj = j >= L.e3 ? 1 : 0;
     const int tau = pi ^ pj ^ (popc4(pm) & 1) ^ (popc4(pn) & 1);
-    float acc[CHI];
+    Acc acc[CHI];
 #pragma unroll
-    for (int k = 0; k < CHI; ++k) acc[k] = 0.f;
+    for (int k = 0; k < CHI; ++k) acc[k] = 0;
     for (int ci = 0; ci < 2; ++ci) {
       const int cj = ci ^ tau;
       const int patm = pm | (ci << t0), patn = pn | (cj << t0);
@@ -318,20 +326,30 @@ __global__ void __launch_bounds__(256) k_epi_z2(const float* __restrict__ O, lon
       const long long rs = L.bs[patm][t0], cs = L.bs[patn][t0];
       const int i0 = ci ? et : 0, i1 = ci ? Dt : et;
       const int j0 = cj ? et : 0, j1 = cj ? Dt : et;
-      for (int i = i0; i < i1; ++i) {
-        const float* src = O + (rb + (long long)(i - i0) * rs) * ldO + cb;
-        const float* wrow = W + (i * Dt) * CHI;
-        // the row's loads in groups of four, issued before their FMAs
-        for (int u0 = j0; u0 < j1; u0 += 4) {
-          float x[4];
+      // two rows at a time, each row's loads (up to 8) issued before the FMAs
+      for (int i = i0; i < i1; i += 2) {
+        const bool two = i + 1 < i1;
+        const Tin* src0 = O + (rb + (long long)(i - i0) * rs) * ldO + cb;
+        const Tin* src1 = src0 + rs * ldO;
+        for (int u0 = j0; u0 < j1; u0 += 8) {
+          Acc x0[8], x1[8];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) x[u] = (u0 + u < j1) ? src[(long long)(u0 + u - j0) * cs] : 0.f;
+          for (int u = 0; u < 8; ++u) {
+            const bool ok = u0 + u < j1;
+            x0[u] = ok ? (Acc)src0[(long long)(u0 + u - j0) * cs] : (Acc)0;
+            x1[u] = (ok && two) ? (Acc)src1[(long long)(u0 + u - j0) * cs] : (Acc)0;
+          }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 8; ++u) {
             if (u0 + u >= j1) break;
-            const float* w = wrow + (u0 + u) * CHI;
+            const Acc* w0 = W + (i * Dt + u0 + u) * CHI;
+            const Acc* w1 = w0 + Dt * CHI;
 #pragma unroll
-            for (int k = 0; k < CHI; ++k) acc[k] += w[k] * x[u];
+            for (int k = 0; k < CHI; ++k) acc[k] += w0[k] * x0[u];
+            if (two) {
+#pragma unroll
+              for (int k = 0; k < CHI; ++k) acc[k] += w1[k] * x1[u];
+            }
           }
         }
       }
@@ -372,35 +390,36 @@ void launch_z2_advance(int* ev, const int* ev_new, int batch, unsigned trans_mas
   count_launches(1);
 }
 
-template <class Tin>
-void launch_build_y_z2(const Tin* X, const Planes<__nv_bfloat16>& out, long long ld, Geom g, int a,
+template <class Tin, class Tout>
+void launch_build_y_z2(const Tin* X, const Planes<Tout>& out, long long ld, Geom g, int a,
                        const int* rank_tab, const int* kcol_tab, const Z2Layout* L, const int* pi, cudaStream_t s) {
   dim3 grid((unsigned)((g.P + 31) / 32), (unsigned)((g.P + 31) / 32));
-  k_build_y_z2<Tin><<<grid, dim3(32, 8), 0, s>>>(X, out, ld, g, a, rank_tab, kcol_tab, L, pi);
+  k_build_y_z2<Tin, Tout><<<grid, dim3(32, 8), 0, s>>>(X, out, ld, g, a, rank_tab, kcol_tab, L, pi);
   count_launches(1);
 }
 
-void launch_build_bt_z2(const float* Tt, const Planes<__nv_bfloat16>& out, long long ld, Geom g, int c3,
-                        const double* U3, int chi3, const int* rank_tab, const int* kcol_tab, const int* colpos_tab,
-                        const Z2Layout* L, cudaStream_t s) {
-  const size_t smem = sizeof(float) * (size_t)chi3 * g.D[c3] * g.D[c3];
+template <class Tin, class Tout>
+void launch_build_bt_z2(const Tin* Tt, const Planes<Tout>& out, long long ld, Geom g, int c3, const double* U3,
+                        int chi3, const int* rank_tab, const int* kcol_tab, const int* colpos_tab, const Z2Layout* L,
+                        cudaStream_t s) {
+  const size_t smem = sizeof(ZAcc<Tout>) * (size_t)chi3 * g.D[c3] * g.D[c3];
   const long long total = (long long)chi3 * g.P * g.P;
-  k_build_bt_z2<float><<<grid_cap(total), 256, smem, s>>>(Tt, out, ld, g.P, g.Sn[c3], g.D[c3], U3, chi3, rank_tab,
-                                                           kcol_tab, colpos_tab, L);
+  k_build_bt_z2<Tin, Tout><<<grid_cap(total), 256, smem, s>>>(Tt, out, ld, g.P, g.Sn[c3], g.D[c3], U3, chi3, rank_tab,
+                                                               kcol_tab, colpos_tab, L);
   count_launches(1);
 }
 
-template <class Tout>
-void launch_epi_z2(const float* O, long long ldO, Tout* out, const View& rest, long long sk, long long out_base,
+template <class Tin, class Tout>
+void launch_epi_z2(const Tin* O, long long ldO, Tout* out, const View& rest, long long sk, long long out_base,
                    int t0, int Dt, const double* U, int chi, const Z2Layout* L, const int* pi, cudaStream_t s) {
   long long total = 1;
   for (int i = 0; i < rest.ndim; ++i) total *= rest.shape[i];
-  const size_t smem = sizeof(float) * (size_t)chi * Dt * Dt;
+  const size_t smem = sizeof(ZAcc<Tin>) * (size_t)chi * Dt * Dt;
   const int n = (int)total;  // rest < 2^31 entries (P^2 chi3 / Dt^2 <= 2.3e9 / 4 for Dcut <= 14)
   switch (chi) {
-#define HOTRG_EPI_Z2(C)                                                                                   \
-  case C:                                                                                                 \
-    k_epi_z2<Tout, C><<<grid_cap(total), 256, smem, s>>>(O, ldO, out, rest, n, sk, out_base, t0, U, L, pi); \
+#define HOTRG_EPI_Z2(C)                                                                                        \
+  case C:                                                                                                      \
+    k_epi_z2<Tin, Tout, C><<<grid_cap(total), 256, smem, s>>>(O, ldO, out, rest, n, sk, out_base, t0, U, L, pi); \
     break;
     HOTRG_EPI_Z2(1) HOTRG_EPI_Z2(2) HOTRG_EPI_Z2(3) HOTRG_EPI_Z2(4) HOTRG_EPI_Z2(5) HOTRG_EPI_Z2(6)
     HOTRG_EPI_Z2(7) HOTRG_EPI_Z2(8) HOTRG_EPI_Z2(9) HOTRG_EPI_Z2(10) HOTRG_EPI_Z2(11) HOTRG_EPI_Z2(12)
@@ -412,13 +431,23 @@ void launch_epi_z2(const float* O, long long ldO, Tout* out, const View& rest, l
   count_launches(1);
 }
 
-template void launch_build_y_z2<float>(const float*, const Planes<__nv_bfloat16>&, long long, Geom, int, const int*,
-                                       const int*, const Z2Layout*, const int*, cudaStream_t);
-template void launch_build_y_z2<double>(const double*, const Planes<__nv_bfloat16>&, long long, Geom, int,
-                                        const int*, const int*, const Z2Layout*, const int*, cudaStream_t);
-template void launch_epi_z2<float>(const float*, long long, float*, const View&, long long, long long, int, int,
-                                   const double*, int, const Z2Layout*, const int*, cudaStream_t);
-template void launch_epi_z2<double>(const float*, long long, double*, const View&, long long, long long, int, int,
-                                    const double*, int, const Z2Layout*, const int*, cudaStream_t);
+using bf16 = __nv_bfloat16;
+template void launch_build_y_z2<float, bf16>(const float*, const Planes<bf16>&, long long, Geom, int, const int*,
+                                             const int*, const Z2Layout*, const int*, cudaStream_t);
+template void launch_build_y_z2<double, bf16>(const double*, const Planes<bf16>&, long long, Geom, int, const int*,
+                                              const int*, const Z2Layout*, const int*, cudaStream_t);
+template void launch_build_y_z2<double, double>(const double*, const Planes<double>&, long long, Geom, int,
+                                                const int*, const int*, const Z2Layout*, const int*, cudaStream_t);
+template void launch_build_bt_z2<float, bf16>(const float*, const Planes<bf16>&, long long, Geom, int, const double*,
+                                              int, const int*, const int*, const int*, const Z2Layout*, cudaStream_t);
+template void launch_build_bt_z2<double, double>(const double*, const Planes<double>&, long long, Geom, int,
+                                                 const double*, int, const int*, const int*, const int*,
+                                                 const Z2Layout*, cudaStream_t);
+template void launch_epi_z2<float, float>(const float*, long long, float*, const View&, long long, long long, int,
+                                          int, const double*, int, const Z2Layout*, const int*, cudaStream_t);
+template void launch_epi_z2<float, double>(const float*, long long, double*, const View&, long long, long long, int,
+                                           int, const double*, int, const Z2Layout*, const int*, cudaStream_t);
+template void launch_epi_z2<double, double>(const double*, long long, double*, const View&, long long, long long,
+                                            int, int, const double*, int, const Z2Layout*, const int*, cudaStream_t);
 
 }  // namespace hotrg

@@ -58,6 +58,38 @@ def test_z2_flow_matches_oracle_golden_dcut5():
         assert abs(lz[n - 1] - st["lnz"]) < 2e-7 * abs(st["lnz"]), n
 
 
+def test_z2_fp64_flow_matches_oracle_golden_dcut5():
+    """Every step in FP64 through the blocked FP64 GEMM: the oracle's ln Z/N, ln c_n and Gram
+    spectra to reassociation of FP64 sums."""
+    g = golden("flow_d4_b0.1497_h0_D5_n16")
+    with hotrg(4, 0.1497, 0.0, 5, precision="fp64", z2=True, max_steps=16) as f:
+        for st in g["steps"]:
+            f.step()
+            n = st["step"]
+            assert abs(f.free_energy()[0][0] - st["lnz"]) < 1e-12 * abs(st["lnz"]), n
+            assert abs(f.observables()["x_indicator"] - st["x"]) < 1e-9, n
+            lnc = f.ln_norms()
+            assert abs(lnc[n] - st["ln_c"]) < 1e-12 * max(1.0, abs(st["ln_c"])), n
+            for b, spec in st["spectra"].items():
+                lam = f.spectra(n, int(b))
+                lam = lam[: len(spec)] / lam[0]
+                keep = np.array(spec) > 1e-10
+                np.testing.assert_allclose(lam[keep], np.array(spec)[keep], rtol=1e-9, atol=1e-12)
+
+
+def test_z2_fp64_dcut10_steps_match_dense_fp64():
+    """The FP64 steps of the benchmark's flow, blocked against dense: the same products summed
+    in another order. Step 3 takes bond dimensions (4, 4, 10, 10) to 10^4, the largest FP64
+    squeeze of the flow (a fourth step at P = 10^4 would cost ~2e15 FP64 flops)."""
+    lz, cz, sz, _ = run(4, 0.1497, 10, 3, z2=True, precision="fp64")
+    ld, cd, sd, _ = run(4, 0.1497, 10, 3, precision="fp64")
+    np.testing.assert_allclose(lz, ld, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(cz, cd, rtol=0, atol=1e-12)
+    for a, b in zip(sz, sd):
+        n = min(10, len(a))
+        np.testing.assert_allclose(a[:n] / a[0], b[:n] / b[0], rtol=0, atol=1e-11)
+
+
 def test_z2_2d_flow_matches_oracle_golden():
     g = golden("flow_d2_b0.3_h0_D8_n40")
     lz, _, _, _ = run(2, 0.3, 8, 40, z2=True, precision="bf16x3", fp64_steps=2, x6_steps=12)
