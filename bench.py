@@ -96,7 +96,7 @@ def use_z2(a):
     """The zero-field block-sparse squeeze applies to instances with h = 0 when no derivative in
     h is taken (a scan puts its h = 0 instances into a block-sparse context of their own)."""
     _, hs = instances(a)
-    return (not a.no_z2) and a.workload != "deriv" and a.precision != "fp64" and any(h == 0.0 for h in hs)
+    return (not a.no_z2) and a.workload != "deriv" and any(h == 0.0 for h in hs)
 
 
 def groups(a):
