@@ -241,14 +241,84 @@ __global__ void __launch_bounds__(256) k_build_bt_z2(const Tin* __restrict__ Tt,
 // order, shaped and strided by `rest` (out_stride) and sk (stride of k'). Only the (i, jj)
 // parity combinations of the chunk's two computed blocks are read; the rest of O is zero.
 // CHI = chi (compile-time: exact accumulator count, no predicated FMAs).
+// W rows padded to a multiple of 4 entries (16-byte shared-memory loads)
+template <int CHI>
+constexpr int chi_pad() {
+  return (CHI + 3) / 4 * 4;
+}
+
+// Rows of one parity class with a compile-time column count NC: acc[k] += sum over the nrow
+// rows r and the NC columns u of w[r * wrow + u * CHIP + k] * src[r * rstep + u * cs]. Up to
+// 16 loads are issued before their FMAs.
+template <class Tin, class Acc, int CHI, int NC>
+__device__ __forceinline__ void epi_class_rows(const Tin* __restrict__ src, long long rstep, long long cs,
+                                               int nrow, const Acc* __restrict__ w, int wrow, Acc* acc) {
+  constexpr int CHIP = chi_pad<CHI>();
+  constexpr int R = NC >= 16 ? 1 : 16 / NC;
+  for (int r0 = 0; r0 < nrow; r0 += R) {
+    Acc x[R][NC];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const bool ok = r0 + r < nrow;
+      const Tin* p = src + (long long)(r0 + r) * rstep;
+#pragma unroll
+      for (int u = 0; u < NC; ++u) x[r][u] = ok ? (Acc)p[u * cs] : (Acc)0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r0 + r >= nrow) break;
+      const Acc* wr = w + (r0 + r) * wrow;
+#pragma unroll
+      for (int u = 0; u < NC; ++u)
+#pragma unroll
+        for (int k = 0; k < CHI; ++k) acc[k] += wr[u * CHIP + k] * x[r][u];
+    }
+  }
+}
+
+// Same for any column count (runtime ncol), two rows' loads (up to 8 each) before the FMAs.
+template <class Tin, class Acc, int CHI>
+__device__ __forceinline__ void epi_class_rows_any(const Tin* __restrict__ src, long long rstep, long long cs,
+                                                   int nrow, int ncol, const Acc* __restrict__ w, int wrow,
+                                                   Acc* acc) {
+  constexpr int CHIP = chi_pad<CHI>();
+  for (int i = 0; i < nrow; i += 2) {
+    const bool two = i + 1 < nrow;
+    const Tin* src0 = src + (long long)i * rstep;
+    const Tin* src1 = src0 + rstep;
+    for (int u0 = 0; u0 < ncol; u0 += 8) {
+      Acc x0[8], x1[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool ok = u0 + u < ncol;
+        x0[u] = ok ? (Acc)src0[(long long)(u0 + u) * cs] : (Acc)0;
+        x1[u] = (ok && two) ? (Acc)src1[(long long)(u0 + u) * cs] : (Acc)0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (u0 + u >= ncol) break;
+        const Acc* w0 = w + i * wrow + (u0 + u) * CHIP;
+        const Acc* w1 = w0 + wrow;
+#pragma unroll
+        for (int k = 0; k < CHI; ++k) acc[k] += w0[k] * x0[u];
+        if (two) {
+#pragma unroll
+          for (int k = 0; k < CHI; ++k) acc[k] += w1[k] * x1[u];
+        }
+      }
+    }
+  }
+}
+
 template <class Tin, class Tout, int CHI>
-__global__ void __launch_bounds__(256) k_epi_z2(const Tin* __restrict__ O, long long ldO, Tout* __restrict__ out,
+__global__ void __launch_bounds__(256, 3) k_epi_z2(const Tin* __restrict__ O, long long ldO, Tout* __restrict__ out,
                                                 View rest, int total, long long sk, long long out_base,
                                                 int t0, const double* __restrict__ U,
                                                 const Z2Layout* Lp, const int* pi_ptr) {
   using Acc = ZAcc<Tin>;
-  extern __shared__ unsigned char smraw_epi[];
-  Acc* W = reinterpret_cast<Acc*>(smraw_epi);  // [D*D][CHI]
+  constexpr int CHIP = chi_pad<CHI>();
+  extern __shared__ __align__(16) unsigned char smraw_epi[];
+  Acc* W = reinterpret_cast<Acc*>(smraw_epi);  // [D*D][CHIP]
   __shared__ Z2Layout L;
   __shared__ int shape[2 * kMaxD + 1];
   __shared__ long long ostr[2 * kMaxD + 1];
@@ -259,9 +329,9 @@ __global__ void __launch_bounds__(256) k_epi_z2(const Tin* __restrict__ O, long 
   }
   const int Dt = Lp->D[t0];
   const int nij = Dt * Dt;
-  for (int t = threadIdx.x; t < CHI * nij; t += blockDim.x) {
+  for (int t = threadIdx.x; t < CHIP * nij; t += blockDim.x) {
     const int k = t / nij, ij = t % nij;
-    W[ij * CHI + k] = (Acc)U[t];
+    W[ij * CHIP + k] = k < CHI ? (Acc)U[t] : (Acc)0;
   }
   __syncthreads();
   const int pi = *pi_ptr;
@@ -309,8 +379,10 @@ __global__ void __launch_bounds__(256) k_epi_z2(const Tin* __restrict__ O, long 
     Acc acc[CHI];
 #pragma unroll
     for (int k = 0; k < CHI; ++k) acc[k] = 0;
-    for (int ci = 0; ci < 2; ++ci) {
-      const int cj = ci ^ tau;
+    // loop over the column class: its width is the same in every lane of a warp (the row class
+    // ci = cj ^ tau varies with the lane's parities, only as a row count)
+    for (int cj = 0; cj < 2; ++cj) {
+      const int ci = cj ^ tau;
       const int patm = pm | (ci << t0), patn = pn | (cj << t0);
       const int parn = popc4(patn) & 1;
       long long rb = L.patoff[patm];
@@ -323,35 +395,26 @@ __global__ void __launch_bounds__(256) k_epi_z2(const Tin* __restrict__ O, long 
       }
       const int grp = parn ^ pj;
       cb += L.goff[grp] + L.jstart[grp][j];
-      const long long rs = L.bs[patm][t0], cs = L.bs[patn][t0];
-      const int i0 = ci ? et : 0, i1 = ci ? Dt : et;
-      const int j0 = cj ? et : 0, j1 = cj ? Dt : et;
-      // two rows at a time, each row's loads (up to 8) issued before the FMAs
-      for (int i = i0; i < i1; i += 2) {
-        const bool two = i + 1 < i1;
-        const Tin* src0 = O + (rb + (long long)(i - i0) * rs) * ldO + cb;
-        const Tin* src1 = src0 + rs * ldO;
-        for (int u0 = j0; u0 < j1; u0 += 8) {
-          Acc x0[8], x1[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const bool ok = u0 + u < j1;
-            x0[u] = ok ? (Acc)src0[(long long)(u0 + u - j0) * cs] : (Acc)0;
-            x1[u] = (ok && two) ? (Acc)src1[(long long)(u0 + u - j0) * cs] : (Acc)0;
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if (u0 + u >= j1) break;
-            const Acc* w0 = W + (i * Dt + u0 + u) * CHI;
-            const Acc* w1 = w0 + Dt * CHI;
-#pragma unroll
-            for (int k = 0; k < CHI; ++k) acc[k] += w0[k] * x0[u];
-            if (two) {
-#pragma unroll
-              for (int k = 0; k < CHI; ++k) acc[k] += w1[k] * x1[u];
-            }
-          }
+      const long long rstep = L.bs[patm][t0] * ldO, cs = L.bs[patn][t0];
+      const int i0 = ci ? et : 0, nrow = ci ? Dt - et : et;
+      const int j0 = cj ? et : 0, ncol = cj ? Dt - et : et;
+      const Tin* src = O + rb * ldO + cb;
+      const Acc* w = W + (i0 * Dt + j0) * CHIP;
+      const int wrow = Dt * CHIP;
+      if constexpr (std::is_same<Tin, float>::value && CHI >= 6) {
+        switch (ncol) {
+#define HOTRG_EPI_NC(NC) \
+  case NC:               \
+    epi_class_rows<Tin, Acc, CHI, NC>(src, rstep, cs, nrow, w, wrow, acc); \
+    break;
+          HOTRG_EPI_NC(1) HOTRG_EPI_NC(2) HOTRG_EPI_NC(3) HOTRG_EPI_NC(4)
+          HOTRG_EPI_NC(5) HOTRG_EPI_NC(6) HOTRG_EPI_NC(7) HOTRG_EPI_NC(8)
+#undef HOTRG_EPI_NC
+          default:
+            epi_class_rows_any<Tin, Acc, CHI>(src, rstep, cs, nrow, ncol, w, wrow, acc);
         }
+      } else {
+        epi_class_rows_any<Tin, Acc, CHI>(src, rstep, cs, nrow, ncol, w, wrow, acc);
       }
     }
 #pragma unroll
@@ -414,7 +477,7 @@ void launch_epi_z2(const Tin* O, long long ldO, Tout* out, const View& rest, lon
                    int t0, int Dt, const double* U, int chi, const Z2Layout* L, const int* pi, cudaStream_t s) {
   long long total = 1;
   for (int i = 0; i < rest.ndim; ++i) total *= rest.shape[i];
-  const size_t smem = sizeof(ZAcc<Tin>) * (size_t)chi * Dt * Dt;
+  const size_t smem = sizeof(ZAcc<Tin>) * (size_t)((chi + 3) / 4 * 4) * Dt * Dt;
   const int n = (int)total;  // rest < 2^31 entries (P^2 chi3 / Dt^2 <= 2.3e9 / 4 for Dcut <= 14)
   switch (chi) {
 #define HOTRG_EPI_Z2(C)                                                                                        \
