@@ -248,13 +248,14 @@ constexpr int chi_pad() {
 }
 
 // Rows of one parity class with a compile-time column count NC: acc[k] += sum over the nrow
-// rows r and the NC columns u of w[r * wrow + u * CHIP + k] * src[r * rstep + u * cs]. Up to
-// 16 loads are issued before their FMAs.
+// rows r and the NC columns u of w[r * wrow + u * CHIP + k] * src[r * rstep + u * cs]. The
+// loads of max(1, 8 / NC) rows are issued before their FMAs (few registers: the kernel is
+// latency-bound and gains more from resident warps than from loads in flight per thread).
 template <class Tin, class Acc, int CHI, int NC>
 __device__ __forceinline__ void epi_class_rows(const Tin* __restrict__ src, long long rstep, long long cs,
                                                int nrow, const Acc* __restrict__ w, int wrow, Acc* acc) {
   constexpr int CHIP = chi_pad<CHI>();
-  constexpr int R = NC >= 16 ? 1 : 16 / NC;
+  constexpr int R = NC >= 8 ? 1 : 8 / NC;
   for (int r0 = 0; r0 < nrow; r0 += R) {
     Acc x[R][NC];
 #pragma unroll
@@ -310,8 +311,15 @@ __device__ __forceinline__ void epi_class_rows_any(const Tin* __restrict__ src, 
   }
 }
 
+// CTAs per SM the register budget targets: four for the FP32 path; two for FP64 (its
+// accumulators take twice the registers)
+template <class Tin>
+constexpr int epi_min_blocks() {
+  return std::is_same<Tin, float>::value ? 4 : 2;
+}
+
 template <class Tin, class Tout, int CHI>
-__global__ void __launch_bounds__(256, 3) k_epi_z2(const Tin* __restrict__ O, long long ldO, Tout* __restrict__ out,
+__global__ void __launch_bounds__(256, epi_min_blocks<Tin>()) k_epi_z2(const Tin* __restrict__ O, long long ldO, Tout* __restrict__ out,
                                                 View rest, int total, long long sk, long long out_base,
                                                 int t0, const double* __restrict__ U,
                                                 const Z2Layout* Lp, const int* pi_ptr) {
