@@ -271,6 +271,20 @@ def traffic_from_profile(z2):
         return None
 
 
+def over_ranks(dist, ms, flops, executed, device):
+    """Whole-job figures of a replica run: the slowest rank's time and every rank's flops summed
+    (the replicas run independent flows; this is the only collective, outside the timed region)."""
+    if dist is None:
+        return ms, flops, executed
+    import torch
+    buf = torch.tensor([ms, flops, executed], dtype=torch.float64, device=device)
+    mx = buf.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = buf.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(sm[2])
+
+
 def run_ours(a, rank, world, dist):
     import torch
     from paper_1906_06060_gb300 import HOTRG
@@ -320,16 +334,7 @@ def run_ours(a, rank, world, dist):
     # block-sparse squeeze, which computes about a quarter of it: reported as executed_*)
     step_flops = t["dense_step_flops"] * (5.0 if a.workload == "deriv" else 1.0)
     executed_flops = t["step_flops"] * (5.0 if a.workload == "deriv" else 1.0)
-    # max time over ranks, total flops over ranks
-    if dist:
-        buf = torch.tensor([ms, step_flops, executed_flops], dtype=torch.float64, device=dev)
-        mx = buf.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = buf.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, flops_all, exec_all = float(mx[0]), float(sm[1]), float(sm[2])
-    else:
-        ms_max, flops_all, exec_all = ms, step_flops, executed_flops
+    ms_max, flops_all, exec_all = over_ranks(dist, ms, step_flops, executed_flops, dev)
     if rank != 0:
         return None
     value = flops_all / (ms_max * 1e-3) / 1e12
@@ -404,7 +409,9 @@ def main():
     if world > 1:
         import torch
         import torch.distributed as td
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        if a.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        # the reference arm (the CPU oracle) needs no GPU: its ranks meet over gloo
         td.init_process_group("nccl" if a.impl == "ours" else "gloo")
         dist = td
     if a.impl == "reference":

@@ -85,12 +85,12 @@ typedef struct hotrg_opts {
                              (SS), (ST)) with the pure flow's isometries and report the
                              estimates of Eqs. (energy) and (spin): two extra squeezes per step */
   int z2;                 /* 1: zero-field block-sparse squeeze: at h = 0 every tensor entry whose
-                             legs' spin-flip parities add up to odd vanishes, and the split-
-                             precision squeeze computes only the two nonzero GEMM blocks per
-                             chunk (a quarter of the dense flops); bond indices are then
-                             ordered even-parity first. Needs h = 0 for every instance, d >= 2,
-                             no derivatives and no impurities (EINVAL otherwise); set_tensor
-                             turns it off. */
+                             legs' spin-flip parities add up to odd vanishes, and the squeeze
+                             (split-precision and FP64 steps alike) computes only the two
+                             nonzero GEMM blocks per chunk (a quarter of the dense flops); bond
+                             indices are then ordered even-parity first. Needs h = 0 for every
+                             instance, d >= 2, no derivatives and no impurities (EINVAL
+                             otherwise); set_tensor turns it off, set_tensor_z2 keeps it. */
   int graphs;             /* 1: capture a steady-state step (bond dimensions unchanged) once per
                              axis as a CUDA graph and replay it (default 1; off while timing and
                              on the legacy default stream, which cannot be captured) */
