@@ -438,7 +438,9 @@ __global__ void __launch_bounds__(256) k_pair_contract(const Tin* __restrict__ i
 // once; W is held in shared memory as [i][j][k'] so a warp reads it by broadcast.
 // TWO: out also accumulates the same contraction of in2 with U2 (the tangent of an epilogue
 // contraction: dR' = C_U(dR) + C_dU(R)).
-template <class Tin, class Tout, bool TWO>
+// N > 0: chi = Dj = N at compile time (the steady-state shape: no predicated-off loads or FMAs,
+// W rows padded to 16-byte shared-memory loads); N = 0: any chi <= 16 and Dj <= 16.
+template <class Tin, class Tout, bool TWO, int N>
 __global__ void __launch_bounds__(256) k_pair_contract_all(const Tin* __restrict__ in, Tout* __restrict__ out,
                                                            View v, long long total, int Di, int Dj,
                                                            long long si, long long sj, long long sk,
@@ -447,15 +449,18 @@ __global__ void __launch_bounds__(256) k_pair_contract_all(const Tin* __restrict
                                                            const Tin* __restrict__ in2,
                                                            const double* __restrict__ U2) {
   using Acc = AccT<Tout>;
-  constexpr int kMaxChi = kMaxBond;
-  extern __shared__ unsigned char smraw[];
-  Acc* W = reinterpret_cast<Acc*>(smraw);  // [Di*Dj][chi], then the same for U2
+  constexpr int kMaxChi = N > 0 ? N : kMaxBond;
+  constexpr int kMaxJ = N > 0 ? N : kMaxBond;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  // W row stride: chi, or N padded to a multiple of 4
+  const int ws = N > 0 ? (N + 3) / 4 * 4 : chi;
+  Acc* W = reinterpret_cast<Acc*>(smraw);  // [Di*Dj][ws], then the same for U2
   const int nij = Di * Dj;
-  Acc* W2 = W + (long long)chi * nij;
-  for (int t = threadIdx.x; t < chi * nij; t += blockDim.x) {
+  Acc* W2 = W + (long long)ws * nij;
+  for (int t = threadIdx.x; t < ws * nij; t += blockDim.x) {
     const int k = t / nij, ij = t % nij;
-    W[ij * chi + k] = U ? (Acc)U[t] : (Acc)1;
-    if (TWO) W2[ij * chi + k] = (Acc)U2[t];
+    W[ij * ws + k] = k < chi ? (U ? (Acc)U[t] : (Acc)1) : (Acc)0;
+    if (TWO) W2[ij * ws + k] = k < chi ? (Acc)U2[t] : (Acc)0;
   }
   __syncthreads();
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -476,22 +481,22 @@ __global__ void __launch_bounds__(256) k_pair_contract_all(const Tin* __restrict
       const Acc* Wp = pass ? W2 : W;
       for (int i = 0; i < Di; ++i) {
         const Tin* src = base_in + ioff + i * si;
-        Acc x[kMaxBond];
+        Acc x[kMaxJ];
 #pragma unroll
-        for (int j = 0; j < kMaxBond; ++j) x[j] = j < Dj ? (Acc)src[j * sj] : (Acc)0;
+        for (int j = 0; j < kMaxJ; ++j) x[j] = (N > 0 || j < Dj) ? (Acc)src[j * sj] : (Acc)0;
 #pragma unroll
-        for (int j = 0; j < kMaxBond; ++j) {
-          if (j >= Dj) break;
-          const Acc* w = Wp + (i * Dj + j) * chi;
+        for (int j = 0; j < kMaxJ; ++j) {
+          if (N == 0 && j >= Dj) break;
+          const Acc* w = Wp + (i * Dj + j) * ws;
 #pragma unroll
           for (int k = 0; k < kMaxChi; ++k)
-            if (k < chi) acc[k] += w[k] * x[j];
+            if (N > 0 || k < chi) acc[k] += w[k] * x[j];
         }
       }
     }
 #pragma unroll
     for (int k = 0; k < kMaxChi; ++k)
-      if (k < chi) out[ooff + k * sk] = (Tout)acc[k];
+      if (N > 0 || k < chi) out[ooff + k * sk] = (Tout)acc[k];
   }
 }
 
@@ -631,12 +636,33 @@ void launch_pair_contract_all(const Tin* in, Tout* out, const View& rest, int Di
   long long total = 1;
   for (int i = 0; i < rest.ndim; ++i) total *= rest.shape[i];
   const size_t smem = sizeof(Acc) * (size_t)chi * Di * Dj * (in2 ? 2 : 1);
-  if (in2)
-    k_pair_contract_all<Tin, Tout, true><<<grid_for(total, 256), 256, smem, s>>>(
-        in, out, rest, total, Di, Dj, si, sj, sk, U, chi, in_base, out_base, in2, U2);
-  else
-    k_pair_contract_all<Tin, Tout, false><<<grid_for(total, 256), 256, smem, s>>>(
-        in, out, rest, total, Di, Dj, si, sj, sk, U, chi, in_base, out_base, nullptr, nullptr);
+  const size_t smem_pad = sizeof(Acc) * (size_t)((chi + 3) / 4 * 4) * Di * Dj;
+  const int grid = grid_for(total, 256);
+  if (in2) {
+    k_pair_contract_all<Tin, Tout, true, 0><<<grid, 256, smem, s>>>(in, out, rest, total, Di, Dj, si, sj, sk, U,
+                                                                     chi, in_base, out_base, in2, U2);
+    count_launches(1);
+    return;
+  }
+  // the steady-state FP32 shape (chi = Dj) with compile-time extents
+  if constexpr (std::is_same<Tin, float>::value) {
+    if (U && chi == Dj && chi >= 6) switch (chi) {
+#define HOTRG_PCA(NN)                                                                                      \
+  case NN:                                                                                                 \
+    k_pair_contract_all<Tin, Tout, false, NN><<<grid, 256, smem_pad, s>>>(in, out, rest, total, Di, Dj, si, sj, \
+                                                                          sk, U, chi, in_base, out_base,      \
+                                                                          nullptr, nullptr);                  \
+    count_launches(1);                                                                                     \
+    return;
+      HOTRG_PCA(6) HOTRG_PCA(7) HOTRG_PCA(8) HOTRG_PCA(9) HOTRG_PCA(10) HOTRG_PCA(11)
+      HOTRG_PCA(12) HOTRG_PCA(13) HOTRG_PCA(14) HOTRG_PCA(15) HOTRG_PCA(16)
+#undef HOTRG_PCA
+        default:
+          break;
+      }
+  }
+  k_pair_contract_all<Tin, Tout, false, 0><<<grid, 256, smem, s>>>(in, out, rest, total, Di, Dj, si, sj, sk, U,
+                                                                    chi, in_base, out_base, nullptr, nullptr);
   count_launches(1);
 }
 
@@ -644,9 +670,11 @@ void launch_pair_contract_all(const Tin* in, Tout* out, const View& rest, int Di
 // of dynamic shared memory (2 x 16 x 256 doubles): raise the limit once, outside any capture.
 void prepare_kernel_attributes() {
   const int big = (int)(2 * sizeof(double) * kMaxBond * kMaxGram);
-  cudaFuncSetAttribute(k_pair_contract_all<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_pair_contract_all<float, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_pair_contract_all<float, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_pair_contract_all<double, double, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       big);
+  cudaFuncSetAttribute(k_pair_contract_all<float, float, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_pair_contract_all<float, double, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       big);
   cudaFuncSetAttribute(k_build_bt<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_build_bt<float, __nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
