@@ -1,0 +1,75 @@
+"""bench.py's host logic on CPU: argument defaults, which contexts run block-sparse, the
+workload description, and the committed-profile lookup that feeds roofline.traffic."""
+import hashlib
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def args(monkeypatch, *argv):
+    monkeypatch.setattr(sys, "argv", ["bench.py", *argv])
+    return bench.parse()
+
+
+def test_defaults_name_the_dcut10_flow(monkeypatch):
+    a = args(monkeypatch)
+    assert (a.dcut, a.precision, a.fp64_steps, a.x6_steps, a.warmup, a.steps) == (10, "bf16x3", 3, 12, 12, 4)
+    assert args(monkeypatch, "--workload", "scan").dcut == 8
+    assert bench.steady_flops(10) == 2.0e15
+
+
+def test_block_sparse_only_where_the_structure_holds(monkeypatch):
+    assert bench.use_z2(args(monkeypatch))                              # h = 0 flow
+    assert bench.use_z2(args(monkeypatch, "--precision", "fp64"))       # FP64 steps too
+    assert not bench.use_z2(args(monkeypatch, "--no-z2"))
+    assert not bench.use_z2(args(monkeypatch, "--h", "1e-6"))           # field breaks the symmetry
+    assert not bench.use_z2(args(monkeypatch, "--workload", "deriv"))   # h-tangent is odd
+
+
+def test_scan_splits_into_a_block_sparse_and_a_dense_context(monkeypatch):
+    a = args(monkeypatch, "--workload", "scan", "--instances", "3")
+    betas, hs = bench.instances(a)
+    assert len(betas) == 6 and hs == [0.0] * 3 + [1e-5] * 3
+    g = bench.groups(a)
+    assert [(len(b), z) for b, _, z in g] == [(3, True), (3, False)]
+    assert g[0][1] == [0.0] * 3 and g[1][1] == [1e-5] * 3
+    assert sorted(g[0][0] + g[1][0]) == sorted(betas)
+    cfg = bench.workload_config(a)
+    assert cfg["contexts"] == [{"instances": 3, "z2": True}, {"instances": 3, "z2": False}]
+    assert cfg["instances"] == 6 and cfg["h"] == [0.0, 1e-5]
+
+
+def test_workload_config_records_the_timed_steps(monkeypatch):
+    cfg = bench.workload_config(args(monkeypatch, "--warmup", "5", "--steps", "2"))
+    assert cfg["timed_steps"] == [6, 7] and cfg["Dcut"] == 10 and cfg["z2_block_sparse"]
+    assert cfg["parallelism"] == "single GPU" and "workload" in cfg
+
+
+def _profile(tmp_path, sha, traffic):
+    p = tmp_path / "prof.md"
+    p.write_text(f"# summary\n\n- gemm_tc_sha={sha}\n- traffic_bytes_per_launch_full={traffic}\n")
+    return str(p)
+
+
+def test_traffic_is_read_only_while_the_kernel_source_is_unchanged(tmp_path, monkeypatch):
+    src = tmp_path / "gemm_tc.cu"
+    src.write_bytes(b"// kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    monkeypatch.setattr(bench, "GEMM_SRC", str(src))
+    monkeypatch.setattr(bench, "PROFILE", {True: _profile(tmp_path, sha, "1.2300e+10"),
+                                           False: str(tmp_path / "missing.md")})
+    assert bench.traffic_from_profile(True) == pytest.approx(1.23e10)
+    assert bench.traffic_from_profile(False) is None          # no summary
+    src.write_bytes(b"// kernel source, changed\n")
+    assert bench.traffic_from_profile(True) is None           # counters taken on another kernel
+
+
+def test_committed_profiles_parse():
+    for z2, path in bench.PROFILE.items():
+        text = open(path).read()
+        assert "gemm_tc_sha=" in text and "traffic_bytes_per_launch_full=" in text, path
