@@ -202,6 +202,49 @@ def test_dims_schedule_reaches_dcut_at_step_3():
     assert R.squeeze_flops([10] * 4, 0, 10) == pytest.approx(2e15)
 
 
+# ------------------------------------------------------------------ zero-field spin-flip structure
+def _odd_entries_max(T, par):
+    """Largest |T| over entries whose legs' parities (par[b][index], both copies of leg b) add
+    up to odd."""
+    d = T.ndim // 2
+    tot = np.zeros(T.shape, dtype=int)
+    for slot in range(2 * d):
+        shape = [1] * (2 * d)
+        shape[slot] = T.shape[slot]
+        tot = tot + par[slot % d].reshape(shape)
+    odd = (tot % 2) == 1
+    return np.abs(T[odd]).max() if odd.any() else 0.0
+
+
+@pytest.mark.parametrize("d,Dcut,nsteps", [(2, 8, 8), (3, 6, 6), (4, 5, 6)])
+def test_zero_field_flow_keeps_the_spin_flip_block_structure(d, Dcut, nsteps):
+    """Sec. 2's T^(0) at h = 0: the site weight is even in s, so entries with an odd number of
+    odd legs vanish; Gram matrices then commute with the fused parity and every kept
+    eigenvector lies in one parity sector, so the structure survives each step with the new
+    bond's parities read off the isometry. This is what the block-sparse squeeze relies on. At
+    h != 0 the odd entries are present from the start."""
+    beta = {2: 0.4, 3: 0.22, 4: 0.1497}[d]
+    T = R.initial_tensor(d, beta, 0.0)
+    assert _odd_entries_max(R.initial_tensor(d, beta, 0.05), [np.array([0, 1])] * d) > 1e-3
+    par = [np.array([0, 1]) for _ in range(d)]
+    order = R.default_order(d)
+    for n in range(nsteps):
+        assert _odd_entries_max(T, par) <= 1e-13 * np.abs(T).max(), n
+        a = order[n % d]
+        T, info = R.coarse_grain(T, a, Dcut)
+        T = T / R.frobenius(T)
+        for b, iso in info.isometries.items():
+            U = iso.U
+            fused = (par[b][:, None] ^ par[b][None, :]).astype(bool)
+            w_odd = (U ** 2)[fused].sum(axis=0)
+            w_even = (U ** 2)[~fused].sum(axis=0)
+            assert np.all(np.minimum(w_odd, w_even) < 1e-20), (n, b)
+            par[b] = (w_odd > w_even).astype(int)
+    assert _odd_entries_max(T, par) <= 1e-13 * np.abs(T).max()
+    # both sectors are kept on a truncated bond
+    assert any(0 < p.sum() < p.size for p in par)
+
+
 # ------------------------------------------------------------------ planted mistakes
 def test_planted_mistakes_are_caught(monkeypatch):
     """A dropped weight, a transposed operand or a wrong leg must fail one of the pins above."""
