@@ -410,8 +410,7 @@ Contraction plan_contraction(const std::vector<Ax>& axes, int b, int chi_b, cons
     if (axes[i].kind == 0 && axes[i].slot == b) im = i;
     if (axes[i].kind == 2 && axes[i].slot == b) in_ = i;
   }
-  View v;
-  v.ndim = 0;
+  View v{};
   int kaxis = -1;
   for (int i = 0; i < (int)axes.size(); ++i) {
     if (i == im) continue;
@@ -471,8 +470,7 @@ void contract_axes(std::vector<Ax>& axes, const Tin* in, Tout* out, int b, int c
     if (axes[i].kind == 2 && axes[i].slot == b) in_ = i;
   }
   std::vector<Ax> out_axes;
-  View v;
-  v.ndim = 0;
+  View v{};
   int kaxis = -1;
   for (int i = 0; i < (int)axes.size(); ++i) {
     if (i == im) continue;
