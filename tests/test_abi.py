@@ -88,6 +88,31 @@ def test_strerror_and_null_context(lib):
     assert lib.hotrg_gemm_scratch_bytes(128, 256, 64) > 2 * (128 + 256) * 64 * 2
 
 
+def test_every_context_call_rejects_a_null_context(lib):
+    """No entry point dereferences a null context or null output pointers (no device needed)."""
+    from paper_1906_06060_gb300 import _lib
+    E = _lib.HOTRG_EINVAL
+    d, n, sz = ctypes.c_double(), ctypes.c_int(), ctypes.c_size_t()
+    dims = (ctypes.c_int * 4)(2, 2, 2, 2)
+    buf = (ctypes.c_double * 16)()
+    assert lib.hotrg_free_energy(None, ctypes.byref(d), ctypes.byref(d)) == E
+    assert lib.hotrg_observables(None, 0, ctypes.byref(_lib.Obs())) == E
+    assert lib.hotrg_spectra(None, 1, 0, 0, buf, 16, ctypes.byref(n)) == E
+    assert lib.hotrg_ln_norms(None, 0, buf, 16, ctypes.byref(n)) == E
+    assert lib.hotrg_get_tensor(None, 0, dims, buf, 16) == E
+    assert lib.hotrg_set_tensor(None, 0, dims, buf) == E
+    assert lib.hotrg_set_tensor_z2(None, 0, dims, dims, buf) == E
+    assert lib.hotrg_state_size(None, ctypes.byref(sz)) == E
+    assert lib.hotrg_state_save(None, buf, 16) == E
+    assert lib.hotrg_state_load(None, buf, 16) == E
+    assert lib.hotrg_timing_start(None) == E
+    assert lib.hotrg_timing_stop(None, ctypes.byref(_lib.Timing())) == E
+    assert lib.hotrg_autotune(None, ctypes.byref(_lib.Tuning())) == E
+    assert lib.hotrg_gemm_split(None, 64, None, 64, None, 64, 128, 256, 64, 3, 64, 1, None, 0, None) == E
+    assert lib.hotrg_gemm_status(None, None) == E
+    assert lib.hotrg_gemm_split_noalloc(None, 64, None, 64, None, 64, 128, 256, 64, 3, None) == E
+
+
 def test_product_path_fails_loudly_without_a_device():
     import torch
     if torch.cuda.is_available():
