@@ -254,10 +254,12 @@ def traffic_from_profile(z2):
     """Per-launch DRAM bytes of the squeeze GEMM (dense or block-sparse launch) from the
     committed ncu summary, valid only if the kernel source is unchanged since the capture."""
     try:
-        text = open(PROFILE[bool(z2)]).read()
+        with open(PROFILE[bool(z2)]) as fh:
+            text = fh.read()
     except OSError:
         return None
-    sha = hashlib.sha256(open(GEMM_SRC, "rb").read()).hexdigest()[:16]
+    with open(GEMM_SRC, "rb") as fh:
+        sha = hashlib.sha256(fh.read()).hexdigest()[:16]
     kv = {}
     for line in text.splitlines():
         if "=" in line and line.strip().startswith("- "):

@@ -18,7 +18,8 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "hotrg.h")).read()
+    with open(os.path.join(ROOT, "include", "hotrg.h")) as fh:
+        src = fh.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(hotrg_[a-z0-9_]+)\s*\(", src)))
 

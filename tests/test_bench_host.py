@@ -71,5 +71,6 @@ def test_traffic_is_read_only_while_the_kernel_source_is_unchanged(tmp_path, mon
 
 def test_committed_profiles_parse():
     for z2, path in bench.PROFILE.items():
-        text = open(path).read()
+        with open(path) as fh:
+            text = fh.read()
         assert "gemm_tc_sha=" in text and "traffic_bytes_per_launch_full=" in text, path
