@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle for HOTRG on the d-dimensional Ising model (arXiv:1906.06060, Sec. 2).
 
-TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT. Only ``tests/``, ``__graft_entry__.smoke()`` and
-the CPU-baseline leg of ``bench.py`` may import anything from this package. The CUDA library
+TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT. Only ``tests/``, ``__graft_entry__.smoke()``, and
+the CPU-baseline leg and reference arm of ``bench.py`` may import anything from this package. The CUDA library
 shares no code, table or helper with it.
 
 Modules

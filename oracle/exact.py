@@ -1,7 +1,7 @@
 """Independent exact references that pin the HOTRG oracle (arXiv:1906.06060, Sec. 2).
 
 TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT: only tests/, __graft_entry__.smoke() and
-bench.py's CPU-baseline leg may use it.
+bench.py's CPU-baseline leg and reference arm may use it.
 
 None of these functions uses the tensor network: they evaluate the partition function of
 Eq. (pf) by other means (enumeration, textbook closed forms), or restate the closed form of

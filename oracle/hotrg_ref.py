@@ -1,7 +1,7 @@
 """HOTRG for the d-dimensional Ising model, plain FP64 NumPy (arXiv:1906.06060, Sec. 2).
 
 TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT: only tests/, __graft_entry__.smoke() and
-bench.py's CPU-baseline leg may use it. It shares no code with the CUDA library.
+bench.py's CPU-baseline leg and reference arm may use it. It shares no code with the CUDA library.
 
 Everything here follows the paper's order of operations; NumPy/LAPACK primitives (tensordot,
 einsum, eigh) serve as single steps. Where the paper is silent, the reading used is stated at
