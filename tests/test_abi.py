@@ -68,6 +68,22 @@ def test_workspace_size_and_argument_checks(lib):
     assert lib.hotrg_workspace_size(4, 4, ctypes.byref(o), ctypes.byref(n)) == _lib.HOTRG_EINVAL
 
 
+def test_workspace_covers_the_block_sparse_operands(lib):
+    """The block-sparse squeeze pads every operand row to round_up(P, 64) + 64 columns (its two
+    k classes start at 64-aligned columns), in FP64 as in split precision: at Dcut = 10 the B
+    operand alone is chi P rows of that length."""
+    from paper_1906_06060_gb300 import workspace_bytes
+    P, chi = 10 ** 4, 10
+    ld = (P + 63) // 64 * 64 + 64
+    fp64 = workspace_bytes(4, 10, "fp64", z2=True)
+    bf16x3 = workspace_bytes(4, 10, "bf16x3", fp64_steps=3, z2=True)
+    assert fp64 >= chi * P * ld * 8 + P * ld * 8            # Bt and Y in FP64
+    assert bf16x3 >= chi * P * ld * 2 * 2 + P * ld * 2 * 2   # two bf16 planes each
+    # the layout tables of the block-sparse path come on top of the dense path's needs
+    assert workspace_bytes(4, 10, "bf16x3", fp64_steps=3, z2=True) >= workspace_bytes(4, 10, "bf16x3",
+                                                                                       fp64_steps=3)
+
+
 def test_init_rejects_bad_arguments_before_touching_a_device(lib):
     from paper_1906_06060_gb300 import _lib
     o = _lib.Opts()
