@@ -170,8 +170,10 @@ int hotrg_get_tensor(hotrg_ctx *c, int instance, int *dims, double *host, size_t
 /* Replace the tensor of `instance` by a host array in natural layout with bond dimensions
  * dims[0..d) (each 1..Dcut). Used to coarse-grain arbitrary tensors. It does not normalise and
  * does not touch the ln Z accumulator; with opts.derivatives it zeroes the instance's tangents
- * (the supplied tensor does not depend on beta or h), with opts.impurities its impure tensors. Errors: EINVAL (also when prod dims
- * exceeds the largest P of the workspace plan, i.e. of the states reachable from T^(0) within
+ * (the supplied tensor does not depend on beta or h), with opts.impurities its impure tensors.
+ * With opts.z2 it switches the context to the dense squeeze (the tensor's block structure is
+ * unknown; hotrg_set_tensor_z2 keeps it). Errors: EINVAL (also when prod dims exceeds the
+ * largest P of the workspace plan, i.e. of the states reachable from T^(0) within
  * opts.max_steps steps). */
 int hotrg_set_tensor(hotrg_ctx *c, int instance, const int *dims, const double *host);
 
