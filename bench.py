@@ -26,6 +26,9 @@ Other workloads of the same path (same JSON line; e2e and the CPU baseline only 
     --workload deriv   d lnZ/d beta and d lnZ/d h through the eigendecomposition: beta in
                        linspace(0.1494, 0.1500, n) (default n = 16), h = 1e-6, Dcut = 10
     --instances n      fewer instances of a scan / deriv workload (a bounded sample of it)
+    --workload accuracy  per-step |delta(lnZ/N)| / |lnZ/N| of split-precision schedules against the
+                       FP64 GPU flow (--ref-steps of it, timed step by step) and the oracle's golden
+    --workload gemm    the tcgen05 squeeze GEMM alone (--gemm-shape M,N,K --npass)
 
 Multi-GPU (torchrun, one process per GPU): the single-flow workload does not shard, so each rank
 runs an independent replica; value = total flops of all ranks / max time over ranks.
@@ -63,7 +66,15 @@ def parse():
     ap.add_argument("--kblock", type=int, default=64)
     ap.add_argument("--fold-group", type=int, default=0)
     ap.add_argument("--x6-steps", type=int, default=12)
-    ap.add_argument("--workload", default="flow", choices=["flow", "scan", "deriv"])
+    ap.add_argument("--workload", default="flow", choices=["flow", "scan", "deriv", "accuracy", "gemm"])
+    ap.add_argument("--gemm-shape", default="10000,40000,10000",
+                    help="gemm workload: M,N,K of the squeeze GEMM alone (default: a quarter of one Dcut=10 chunk)")
+    ap.add_argument("--npass", type=int, default=3, help="gemm workload: split products (1, 3, 4 or 6)")
+    ap.add_argument("--ref-steps", type=int, default=8,
+                    help="accuracy workload: steps of the FP64 GPU reference flow (0: read the committed one)")
+    ap.add_argument("--flow-steps", type=int, default=40, help="accuracy workload: steps of each split flow")
+    ap.add_argument("--schedules", default="bf16x3:3:12,bf16x3:3:0,bf16x6:3:0",
+                    help="accuracy workload: precision:fp64_steps:x6_steps of each split flow")
     ap.add_argument("--instances", type=int, default=0)
     ap.add_argument("--dcut", type=int, default=0)
     ap.add_argument("--beta", type=float, default=0.1497)
@@ -376,6 +387,139 @@ def run_ours(a, rank, world, dist):
     return out
 
 
+
+# ----------------------------------------------------------------------------- accuracy workload
+ACCURACY_PROFILE = os.path.join(ROOT, "profiles", "accuracy_fp64_vs_split_dcut10.md")
+ORACLE_GOLDEN_D10 = os.path.join(ROOT, "tests", "golden", "flow_d4_b0.1497_h0_D10_n4.json")
+
+
+def stored_fp64_reference(path=ACCURACY_PROFILE):
+    """Per-step ln Z/N of the FP64 GPU flow recorded in the committed accuracy summary
+    ("- fp64_lnz_step_<n> = <value>" lines), or {} if there is none."""
+    out = {}
+    try:
+        with open(path) as fh:
+            for line in fh:
+                line = line.strip()
+                if line.startswith("- fp64_lnz_step_") and "=" in line:
+                    k, v = line[2:].split("=", 1)
+                    out[int(k.strip()[len("fp64_lnz_step_"):])] = float(v)
+    except (OSError, ValueError):
+        return {}
+    return out
+
+
+def oracle_golden_lnz(path=ORACLE_GOLDEN_D10):
+    """Per-step ln Z/N of the FP64 oracle's Dcut = 10 flow (tests/golden, written by the oracle)."""
+    try:
+        with open(path) as fh:
+            g = json.load(fh)
+    except (OSError, ValueError):
+        return {}
+    return {st["step"]: st["lnz"] for st in g["steps"]}
+
+
+def run_accuracy(a):
+    """|delta(ln Z/N)| / |ln Z/N| of split-precision schedules against the FP64 GPU path after every
+    step (4D, h = 0, both block-sparse; --no-z2 for dense), with the FP64 steps timed one by one."""
+    import torch
+    from paper_1906_06060_gb300 import HOTRG, fp64_fma_tflops
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    z2 = use_z2(a)
+    out = {"workload": "accuracy", "d": 4, "beta": a.beta, "h": a.h, "Dcut": a.dcut, "z2_block_sparse": z2}
+    out["fp64_fma_tflops"] = fp64_fma_tflops(stream=stream)
+    ref, ref_src = {}, None
+    if a.ref_steps > 0:
+        steps = []
+        with HOTRG(4, a.beta, a.h, a.dcut, precision="fp64", z2=z2, stream=stream, graphs=False) as f:
+            for n in range(1, a.ref_steps + 1):
+                f.timing_start()
+                f.step()
+                t = f.timing_stop()
+                lnz = float(f.free_energy()[0][0])
+                ob = f.observables()
+                ref[n] = lnz
+                steps.append({"step": n, "lnz": lnz, "ln_c": ob["last_ln_c"], "x": ob["x_indicator"],
+                              "ms": t["ms_step"], "ms_gemm": t["ms_gemm"], "gemm_flops": t["gemm_flops"],
+                              "dense_flops": t["dense_step_flops"]})
+                print(json.dumps({"fp64_step": steps[-1]}), file=sys.stderr, flush=True)
+        out["fp64_steps"] = steps
+        ref_src = "FP64 GPU flow of this run"
+    else:
+        ref = stored_fp64_reference()
+        ref_src = f"FP64 GPU flow recorded in {os.path.relpath(ACCURACY_PROFILE, ROOT)}"
+    oracle = oracle_golden_lnz() if (a.dcut == 10 and a.beta == 0.1497 and a.h == 0.0) else {}
+    out["reference"] = ref_src
+    out["fp64_vs_oracle"] = {str(n): abs(ref[n] - v) / abs(v) for n, v in oracle.items() if n in ref}
+    sched = []
+    for spec in [x for x in a.schedules.split(",") if x]:
+        prec, f64, x6 = spec.split(":")
+        lnzs = []
+        t0 = time.perf_counter()
+        with HOTRG(4, a.beta, a.h, a.dcut, precision=prec, fp64_steps=int(f64), x6_steps=int(x6), z2=z2,
+                   stream=stream) as f:
+            for _ in range(a.flow_steps):
+                f.step()
+                lnzs.append(float(f.free_energy()[0][0]))
+            lnc = [float(x) for x in f.ln_norms()]
+        wall = time.perf_counter() - t0
+        rel = {str(n): abs(lnzs[n - 1] - v) / abs(v) for n, v in ref.items() if n <= len(lnzs)}
+        rel_o = {str(n): abs(lnzs[n - 1] - v) / abs(v) for n, v in oracle.items() if n <= len(lnzs)}
+        sched.append({"precision": prec, "fp64_steps": int(f64), "x6_steps": int(x6), "wall_s": wall,
+                      "lnz": lnzs, "ln_c": lnc, "rel_err_vs_fp64": rel, "rel_err_vs_oracle": rel_o})
+        print(json.dumps({"schedule": spec, "rel_err_vs_fp64": rel, "wall_s": wall}), file=sys.stderr, flush=True)
+    out["schedules"] = sched
+    return out
+
+
+# ----------------------------------------------------------------------------- GEMM alone
+def run_gemm(a):
+    """The tcgen05 squeeze GEMM alone through the C ABI (hotrg_gemm_split) on seeded Gaussian
+    operands: one warm-up launch (it also splits the FP32 operands into bf16 planes), then K timed
+    launches with CUDA events. The default shape is a quarter of one Dcut = 10 chunk's N range
+    (M = P = 10^4, N = 4 x 10^4, K = 10^4: 3.6 GB of operands and output, larger than L2)."""
+    import torch
+    from ctypes import c_void_p
+    from paper_1906_06060_gb300 import _lib
+    from paper_1906_06060_gb300._lib import check
+    M, N, K = (int(x) for x in a.gemm_shape.split(","))
+    lib = _lib.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g = torch.Generator(device=dev).manual_seed(0)
+    A = torch.randn((M, K), device=dev, generator=g, dtype=torch.float32)
+    Bt = torch.randn((N, K), device=dev, generator=g, dtype=torch.float32)
+    C = torch.empty((M, N), device=dev, dtype=torch.float32)
+    nbytes = lib.hotrg_gemm_scratch_bytes(M, N, K)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+
+    def launch():
+        check(lib.hotrg_gemm_split(c_void_p(A.data_ptr()), A.stride(0), c_void_p(Bt.data_ptr()), Bt.stride(0),
+                                   c_void_p(C.data_ptr()), C.stride(0), M, N, K, a.npass, a.kblock, a.fold_group,
+                                   c_void_p(scratch.data_ptr()), nbytes, c_void_p(s.cuda_stream)),
+              "hotrg_gemm_split")
+
+    for _ in range(max(1, a.warmup)):
+        launch()
+    check(lib.hotrg_gemm_status(c_void_p(scratch.data_ptr()), c_void_p(s.cuda_stream)), "gemm status")
+    times = []
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        launch()
+        e1.record(s)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    check(lib.hotrg_gemm_status(c_void_p(scratch.data_ptr()), c_void_p(s.cuda_stream)), "gemm status")
+    flops = 2.0 * M * N * K
+    best = min(times)
+    return {"workload": "gemm", "M": M, "N": N, "K": K, "npass": a.npass, "kblock": a.kblock,
+            "fold_group": a.fold_group, "ms": times,
+            "note": "each timed launch includes the FP32 -> bf16 plane split of A and Bt",
+            "alg_tflops": flops / (best * 1e-3) / 1e12, "tensor_tflops": a.npass * flops / (best * 1e-3) / 1e12}
+
 def e2e(a):
     """Same metric through the public API from host inputs: context creation (beta, h copied
     from host), W + K steps with the free energy read back to the host after every step."""
@@ -422,6 +566,11 @@ def main():
             print(json.dumps(out))
         if dist:
             dist.destroy_process_group()
+        return
+    if a.workload in ("accuracy", "gemm"):
+        from paper_1906_06060_gb300 import build
+        build.build()
+        print(json.dumps(run_accuracy(a) if a.workload == "accuracy" else run_gemm(a)))
         return
     if a.warmup < 3:
         print("warm-up must be >= 3 steps", file=sys.stderr)

@@ -95,6 +95,8 @@ typedef struct hotrg_opts {
                              axis as a CUDA graph and replay it (default 1; off while timing and
                              on the legacy default stream, which cannot be captured) */
   double wait_timeout_s;  /* bound on any device-side spin wait, seconds (default 4) */
+  int max_sweeps;         /* Jacobi sweep limit of the eigensolver (default 40; 0 = default, at most
+                             1000); a Gram matrix not diagonalised within it sets HOTRG_ENOCONV */
 } hotrg_opts;
 
 typedef struct hotrg_obs {
@@ -171,8 +173,8 @@ int hotrg_get_tensor(hotrg_ctx *c, int instance, int *dims, double *host, size_t
  * dims[0..d) (each 1..Dcut). Used to coarse-grain arbitrary tensors. It does not normalise and
  * does not touch the ln Z accumulator; with opts.derivatives it zeroes the instance's tangents
  * (the supplied tensor does not depend on beta or h), with opts.impurities its impure tensors.
- * With opts.z2 it switches the context to the dense squeeze (the tensor's block structure is
- * unknown; hotrg_set_tensor_z2 keeps it). Errors: EINVAL (also when prod dims exceeds the
+ * With opts.z2 it switches the context to the dense squeeze for all instances (the tensor's block
+ * structure is unknown; hotrg_set_tensor_z2 keeps it). Errors: EINVAL (also when prod dims exceeds the
  * largest P of the workspace plan, i.e. of the states reachable from T^(0) within
  * opts.max_steps steps). */
 int hotrg_set_tensor(hotrg_ctx *c, int instance, const int *dims, const double *host);
@@ -181,8 +183,12 @@ int hotrg_set_tensor(hotrg_ctx *c, int instance, const int *dims, const double *
  * must have the zero-field block structure (Sec. 2's T^(0) at h = 0 and every coarse-grained
  * tensor of that flow), with the values of leg b ordered even-parity first and evens[b] of
  * them even (d ints, 0..dims[b]): every entry whose legs' parities add up to odd must be exactly
- * zero, which is checked on the host. Errors: EINVAL (bad sizes, structure violated), ESTATE
- * (context created without opts.z2). Synchronises. */
+ * zero, which is checked on the host. The block-sparse squeeze applies again only once every
+ * instance of the context holds such a tensor: one given a dense tensor by hotrg_set_tensor, and
+ * every instance after a step taken with the dense squeeze, needs its own hotrg_set_tensor_z2
+ * first (until then the context squeezes densely, which is correct for any tensor).
+ * Errors: EINVAL (bad sizes, structure violated), ESTATE (context created without opts.z2).
+ * Synchronises. */
 int hotrg_set_tensor_z2(hotrg_ctx *c, int instance, const int *dims, const int *evens, const double *host);
 
 /* Checkpoint: size of, save to and restore from a host buffer holding the full flow state
@@ -263,12 +269,15 @@ int hotrg_gemm_split(const float *A, long long lda, const float *Bt, long long l
  * (it may synchronise the device). This variant allocates nothing: the bf16 planes and the
  * status word live in a fixed device array inside the library (about 12 MiB, held on every GPU
  * where this entry point is used until the process exits).
- *   Limit: (M + N) * round_up(K, 64) <= HOTRG_GEMM_NOALLOC_MAX_ELEMS, else HOTRG_EINVAL.
+ *   Sizes: M >= 128, N >= 256, K >= 64 (as hotrg_gemm_split) and
+ *          (M + N) * round_up(K, 64) <= HOTRG_GEMM_NOALLOC_MAX_ELEMS (2^21), else HOTRG_EINVAL.
  *   Set-up: the first call on a device (made while it is current) looks up the array's device
- *   address; make that first call before any stream capture.
+ *   address.
+ *   Capture: every call synchronises `stream` and reads the status word back to the host, so the
+ *   entry point cannot be used inside a CUDA stream capture.
  *   Sharing: every call uses the same array. Calls whose GPU work overlaps (other streams or
- *   host threads) race on it. The call synchronises `stream` and returns the GEMM's status
- *   (0, HOTRG_ETIMEOUT if a pipeline wait gave up, HOTRG_EDEVICE). Other errors: EINVAL. */
+ *   host threads) race on it. Returns the GEMM's status (0, HOTRG_ETIMEOUT if a pipeline wait
+ *   gave up, HOTRG_EDEVICE). Other errors: EINVAL. */
 #define HOTRG_GEMM_NOALLOC_MAX_ELEMS 2097152LL
 int hotrg_gemm_split_noalloc(const float *A, long long lda, const float *Bt, long long ldb, float *C,
                              long long ldc, long long M, long long N, long long K, int npass,
@@ -278,6 +287,14 @@ int hotrg_gemm_split_noalloc(const float *A, long long lda, const float *Bt, lon
  * pipeline wait of the GEMM kernel gave up). The word lives in the first bytes of scratch and
  * is cleared by each GEMM call. Synchronises `stream`. */
 int hotrg_gemm_status(const void *scratch, void *stream);
+
+/* Benchmark support (the paper has no counterpart): the GPU's FP64 FMA rate, measured with
+ * independent FMA chains on every SM (two launches of `iters` loop iterations; the second is timed
+ * with CUDA events on `stream`). It is the roofline denominator of the FP64 squeeze, whose cost is
+ * fixed by Sec. 2's O(Dcut^15) statement. `sink` is a device array of at least 8 x (SM count)
+ * doubles that the kernel may write (in practice it writes nothing); *tflops receives the rate.
+ * Synchronises `stream`. Errors: EINVAL (iters outside 1..2^32, null pointers), EDEVICE. */
+int hotrg_bench_fp64_fma(long long iters, double *sink, double *tflops, void *stream);
 
 #ifdef __cplusplus
 }

@@ -126,6 +126,18 @@ def lnz_1d(beta: float, h: float, N: int) -> float:
     return N * math.log(lp) + math.log1p((lm / lp) ** N)
 
 
+def x_1d(beta: float, h: float, N: int) -> float:
+    """X of Eq. (x) for the periodic Ising chain of N sites. In one dimension the coarse-grained
+    tensor after n steps is (up to normalisation) the site matrix to the power N = 2^n, whose
+    eigenvalues are those of the transfer matrix, lam+^N and lam-^N, so with q = (lam-/lam+)^N:
+        X = (Tr A)^2 / Tr A^2 = (lam+^N + lam-^N)^2 / (lam+^{2N} + lam-^{2N}) = (1 + q)^2 / (1 + q^2).
+    """
+    eb = math.exp(beta)
+    r = math.sqrt(eb * eb * math.sinh(beta * h) ** 2 + 1.0 / (eb * eb))
+    q = ((eb * math.cosh(beta * h) - r) / (eb * math.cosh(beta * h) + r)) ** N
+    return (1.0 + q) ** 2 / (1.0 + q * q)
+
+
 def lnz_onsager(beta: float) -> float:
     """Onsager's free energy of the 2D square-lattice Ising model at h = 0, per site:
     ln(2 cosh 2b) + (1/pi) int_0^{pi/2} ln[(1 + sqrt(1 - k^2 sin^2 t)) / 2] dt,

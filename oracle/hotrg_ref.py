@@ -184,7 +184,7 @@ def _new_dims(dims, a, U):
 
 
 def squeeze(T1: np.ndarray, T2: np.ndarray, a: int, U: dict[int, np.ndarray],
-            max_slices: int | None = None) -> np.ndarray:
+            max_slices: int | None = None, slices=None) -> np.ndarray:
     """Coarse-grained tensor of the pair (T1 lower, T2 upper along a), slice by slice.
 
     For each slice s = (k_b for the transverse axes b):
@@ -192,7 +192,9 @@ def squeeze(T1: np.ndarray, T2: np.ndarray, a: int, U: dict[int, np.ndarray],
       GEMM     : O_s = sum over (b2 for all b, al) of A_s * T2     (the O(D^15) contraction)
       epilogue : T'[s, a1; k'.., a2'] = sum over (b1', b2') of U_b[b1', b2', k'_b] O_s
     No intermediate larger than one slice (D^8 entries) is formed. max_slices stops after that
-    many slices (leaving the rest zero): only for timing a bounded sample of the work.
+    many slices (leaving the rest zero): only for timing a bounded sample of the work. slices (a
+    set of (k_b for the transverse axes b, in axis order) tuples) computes only those slices,
+    leaving the rest zero: for checking sampled slices of a large squeeze.
     """
     d = T1.ndim // 2
     dims = dims_of(T1)
@@ -203,6 +205,8 @@ def squeeze(T1: np.ndarray, T2: np.ndarray, a: int, U: dict[int, np.ndarray],
     for count, ks in enumerate(itertools.product(*[range(c) for c in chis])):
         if max_slices is not None and count >= max_slices:
             break
+        if slices is not None and tuple(ks) not in slices:
+            continue
         A = T1
         for b, k in zip(trans, ks):
             A = np.moveaxis(np.tensordot(U[b][:, :, k], A, axes=([0], [b])), 0, b)

@@ -19,7 +19,7 @@ import numpy as np
 from . import _lib
 from ._lib import HOTRG_BF16X3, HOTRG_BF16X4, HOTRG_BF16X6, HOTRG_FP64, HotrgError, check
 
-__all__ = ["HOTRG", "HotrgError", "gemm_split", "workspace_bytes", "PRECISIONS"]
+__all__ = ["HOTRG", "HotrgError", "gemm_split", "workspace_bytes", "fp64_fma_tflops", "PRECISIONS"]
 
 PRECISIONS = {"fp64": HOTRG_FP64, "bf16x3": HOTRG_BF16X3, "bf16x4": HOTRG_BF16X4, "bf16x6": HOTRG_BF16X6}
 # derivative modes: isometries held fixed, or differentiated through the eigendecomposition
@@ -34,7 +34,7 @@ def _torch():
 
 
 def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0, kblock=0,
-          graphs=True, fold_group=0, derivatives=False, impurities=False, z2=False):
+          graphs=True, fold_group=0, derivatives=False, impurities=False, z2=False, max_sweeps=0):
     lib = _lib.load()
     o = _lib.Opts()
     lib.hotrg_opts_default(byref(o))
@@ -50,6 +50,7 @@ def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=
     o.z2 = 1 if z2 else 0
     o.max_steps = int(max_steps)
     o.wait_timeout_s = float(wait_timeout_s)
+    o.max_sweeps = int(max_sweeps)
     return o
 
 
@@ -75,12 +76,13 @@ class HOTRG:
     impurities: also coarse-grain the impure tensors of Sec. 2; the observables then carry the
     estimates <s_i s_j> (nn_correlation) and <s_i> (spin).
     z2: zero-field block-sparse squeeze (h = 0 only; see include/hotrg.h).
+    max_sweeps: Jacobi sweep limit of the eigensolver (0: the default, 40).
     """
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
                  max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0,
                  kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives=False,
-                 impurities: bool = False, z2: bool = False):
+                 impurities: bool = False, z2: bool = False, max_sweeps: int = 0):
         torch = _torch()
         lib = _lib.load()
         betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))
@@ -96,7 +98,7 @@ class HOTRG:
         self.beta = betas
         self.h = hs
         o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps, kblock, graphs, fold_group,
-                  derivatives, impurities, z2)
+                  derivatives, impurities, z2, max_sweeps)
         n = c_size_t(0)
         check(lib.hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -231,3 +233,15 @@ def gemm_split(A, Bt, npass: int = 3, C=None, stream=None, kblock: int = 0, fold
           "hotrg_gemm_split")
     check(lib.hotrg_gemm_status(c_void_p(scratch.data_ptr()), c_void_p(stream.cuda_stream)), "gemm status")
     return C
+
+
+def fp64_fma_tflops(iters: int = 1 << 16, stream=None) -> float:
+    """The GPU's FP64 FMA rate in TFLOP/s (hotrg_bench_fp64_fma): the roofline denominator of
+    the FP64 squeeze."""
+    torch = _torch()
+    stream = stream or torch.cuda.current_stream()
+    sink = torch.zeros(8 * 1024, dtype=torch.float64, device=stream.device)
+    out = c_double(0.0)
+    check(_lib.load().hotrg_bench_fp64_fma(int(iters), c_void_p(sink.data_ptr()), byref(out),
+                                           c_void_p(stream.cuda_stream)), "hotrg_bench_fp64_fma")
+    return float(out.value)

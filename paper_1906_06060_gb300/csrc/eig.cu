@@ -17,7 +17,6 @@ namespace hotrg {
 namespace {
 
 constexpr int kEigThreads = 512;
-constexpr int kMaxSweeps = 40;
 
 __device__ void sm_red_sum(double* sred, double v, int tid) {
   sred[tid] = v;
@@ -74,7 +73,7 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(EigAxes ea, int* status,
   int sweep = 0;
   for (;; ++sweep) {
     if (tid == 0) s_rot = 0;
-    if (sweep >= kMaxSweeps) {
+    if (sweep >= ea.max_sweeps) {
       if (tid == 0) atomic_status(status, ST_NOCONV);
       break;
     }
@@ -303,9 +302,10 @@ void launch_eig_axes(const EigAxes& ea, int batch, int* status, cudaStream_t s, 
 
 void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o, double* U,
                 long long u_stride, double* work, int* status, cudaStream_t s, const int* z2_ev, int* z2_ev_new,
-                int z2_axis, int Db) {
+                int z2_axis, int Db, int max_sweeps) {
   EigAxes ea;
   ea.nt = 1;
+  ea.max_sweeps = max_sweeps;
   ea.g_stride = g_stride;
   ea.u_stride = u_stride;
   ea.out = o;

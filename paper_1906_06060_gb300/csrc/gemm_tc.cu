@@ -27,10 +27,12 @@
 //               columns 128*((w-2)/4).. of the buffer, adds them into 128 FP32 registers per
 //               thread and frees the buffer; after the last k-block it stores its 128 columns.
 // Every mbarrier wait is bounded by a timeout; on expiry the CTA records ST_TIMEOUT, drains
-// the copies and MMAs it issued (again with a bound), frees TMEM and returns.
+// the copies and MMAs it issued (waits bounded by max(timeout, 1 s): issued work always
+// completes, so a short caller limit never lets the CTA exit before it), frees TMEM and returns.
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "kernels.h"
@@ -40,6 +42,7 @@ namespace hotrg {
 namespace {
 
 constexpr int TC_BM = 128, TC_BN = 256;
+constexpr int kMaxDevices = 64;
 constexpr int TC_THREADS = 320;
 constexpr int TC_FOLD_THREADS = 256;  // warps 2-9
 constexpr uint32_t TMEM_COLS = 2 * TC_BN;
@@ -170,6 +173,12 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
       return false;
     }
   }
+}
+// Limit of the waits for work this CTA already issued (TMA copies, MMAs), which always
+// completes: at least one second, so that a short caller limit cannot let the CTA exit (and
+// release TMEM or shared memory) while that work is still in flight.
+__device__ __forceinline__ unsigned long long drain_ns(unsigned long long timeout_ns) {
+  return timeout_ns > 1000000000ull ? timeout_ns : 1000000000ull;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
                                             int y) {
@@ -329,12 +338,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
         }
       }
-      if (!ok) {
-        // drain: the last min(STAGES, issued) loads must land before the CTA exits
-        for (long long i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i)
-          mbar_wait(full0 + 8 * (int)(i % TC_STAGES), (uint32_t)((i / TC_STAGES) & 1), abort_flag,
-                    p.timeout_ns, false);
-      }
+      // Drain, on every exit path: the last min(STAGES, issued) loads must land before the CTA
+      // exits (a consumer that gave up may never have waited for them). Each stage holds at most
+      // one load in flight, and issued copies always complete, so these waits use a floor of one
+      // second whatever the caller's limit (after a normal run they return at once).
+      for (long long i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i)
+        mbar_wait(full0 + 8 * (int)(i % TC_STAGES), (uint32_t)((i / TC_STAGES) & 1), abort_flag,
+                  drain_ns(p.timeout_ns), false);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -392,9 +402,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (++buf == 2) { buf = 0; bphase ^= 1; }
         }
       }
-      // all MMAs issued by this thread complete before TMEM is released
+      // all MMAs issued by this thread complete before TMEM is released (issued MMAs always
+      // complete: the wait has the drain's floor, not the caller's limit)
       mma_commit(final_bar);
-      mbar_wait(final_bar, 0, abort_flag, p.timeout_ns, false);
+      mbar_wait(final_bar, 0, abort_flag, drain_ns(p.timeout_ns), false);
     }
   } else {
     const int q = warp & 3;          // TMEM lane quadrant this warp may access
@@ -516,24 +527,36 @@ int launch_variant(int grid, const Planes<__nv_bfloat16>& A, long long lda, cons
     if (!make_map(&maps.a[i], A.p[i], p.M, p.K, lda, TC_BM, BK) ||
         !make_map(&maps.b[i], B.p[i], p.N, p.K, ldb, TC_BN, BK))
       return HOTRG_EDEVICE;
-  static bool attr = false;
-  if (!attr) {
+  // the dynamic shared-memory limit is a per-device attribute of the kernel: set it once on each
+  // device this variant launches on
+  static std::atomic<bool> attr[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HOTRG_EDEVICE;
+  if (!attr[dev].load()) {
     if (cudaFuncSetAttribute(k_gemm_split<BK, NPL, NPASS, FG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<BK, NPL>::SMEM) != cudaSuccess)
       return HOTRG_EDEVICE;
-    attr = true;
+    attr[dev].store(true);
   }
   k_gemm_split<BK, NPL, NPASS, FG><<<grid, TC_THREADS, Cfg<BK, NPL>::SMEM, s>>>(maps, p);
   return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
 }
 
+// SM count of the current device (cached per device)
 int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 1;
+  }
+  int n = cache[dev].load();
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 1;
+    }
+    cache[dev].store(n);
   }
   return n;
 }

@@ -36,6 +36,7 @@ struct hotrg_ctx {
     int npass = 0, nparts = 0;
   } last_gemm;
   double timeout_s = 4.0;
+  int max_sweeps = 40;  // Jacobi sweep limit of the eigensolver
   cudaStream_t stream = nullptr;
   int dims[kMaxD] = {1, 1, 1, 1};
   int steps = 0, last_axis = -1, sticky = 0;
@@ -67,6 +68,9 @@ struct hotrg_ctx {
   // the per-instance layouts, index tables and the current chunk's GEMM blocks and parity
   bool z2 = false;      // the block-sparse squeeze is in use
   bool z2_opt = false;  // requested at init (set_tensor turns z2 off, set_tensor_z2 back on)
+  // per instance: its tensor is known to have the block structure, with even-first bonds and the
+  // even counts in z2ev (z2 is on only while every instance is)
+  std::vector<char> z2_inst;
   int *z2ev = nullptr, *z2ev_new = nullptr;
   Z2Layout* z2L = nullptr;
   int *z2rank = nullptr, *z2kcol = nullptr, *z2colpos = nullptr, *z2pi = nullptr;
@@ -896,6 +900,7 @@ void hotrg_opts_default(hotrg_opts* o) {
   o->kblock = 64;
   o->graphs = 1;
   o->wait_timeout_s = 4.0;
+  o->max_sweeps = 40;
 }
 
 int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) {
@@ -931,6 +936,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   if (opt->fold_group < 0) return HOTRG_EINVAL;
   if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X4) return HOTRG_EINVAL;
   if (opt->derivatives < 0 || opt->derivatives > 2) return HOTRG_EINVAL;
+  if (opt->max_sweeps < 0 || opt->max_sweeps > 1000) return HOTRG_EINVAL;
   std::vector<double> vb(opt->batch), vh(opt->batch);
   for (int i = 0; i < opt->batch; ++i) {
     vb[i] = opt->beta ? opt->beta[i] : beta;
@@ -966,7 +972,9 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->impure = opt->impurities != 0;
   c->z2 = opt->z2 != 0;
   c->z2_opt = c->z2;
+  c->z2_inst.assign(opt->batch, c->z2 ? 1 : 0);
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
+  c->max_sweeps = opt->max_sweeps > 0 ? opt->max_sweeps : 40;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
   c->h = vh;
@@ -1063,6 +1071,7 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
       // every transverse axis' Gram matrix, then one eigensolver launch for all of them
       EigAxes ea;
       ea.nt = nt;
+      ea.max_sweeps = c->max_sweeps;
       ea.g_stride = c->g_stride;
       ea.u_stride = c->u_stride;
       ea.out = EigOut{nullptr, c->spec_stride, (long long)c->d * kSpecCap, c->dstep, c->max_steps};
@@ -1088,7 +1097,7 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
       EigOut eo{c->spec_log + (long long)b * kSpecCap, c->spec_stride, (long long)c->d * kSpecCap, c->dstep,
                 c->max_steps};
       launch_eig(Gb, c->g_stride, c->batch, n, chi[b], eo, Ub, c->u_stride, c->ework, c->status, s,
-                 c->z2 ? c->z2ev : nullptr, c->z2ev_new, b, g.D[b]);
+                 c->z2 ? c->z2ev : nullptr, c->z2ev_new, b, g.D[b], c->max_sweeps);
       if (c->deriv_mode == 2)
         for (int w = 0; w < 2; ++w) {
           // dG from the half-Gram tangents, then dU from the eigensystem still in ework
@@ -1232,6 +1241,9 @@ int hotrg_step(hotrg_ctx* c, int axis) {
     }
   }
   if (cuda_err(c)) return HOTRG_EDEVICE;
+  // a dense step writes its bonds in plain descending order and no even counts: no instance keeps
+  // a known block layout after it
+  if (!c->z2) std::fill(c->z2_inst.begin(), c->z2_inst.end(), 0);
   for (int b = 0; b < c->d; ++b) c->hist_dims[step - 1][b] = c->dims[b];
   c->hist_axis[step - 1] = a;
   for (int b = 0; b < c->d; ++b) c->dims[b] = nd[b];
@@ -1361,6 +1373,8 @@ int hotrg_set_tensor(hotrg_ctx* c, int instance, const int* dims, const double* 
                         c->stream) != cudaSuccess)
       return c->sticky = HOTRG_EDEVICE;
   // an arbitrary tensor need not have the zero-field block structure: use the dense squeeze
+  // (for every instance: they share the launches)
+  if (c->z2_opt) c->z2_inst[instance] = 0;
   c->z2 = false;
   drop_graphs(c);
   // nor does it carry impurities: the impure estimates restart from zero
@@ -1401,7 +1415,10 @@ int hotrg_set_tensor_z2(hotrg_ctx* c, int instance, const int* dims, const int* 
       cudaMemcpy(c->z2ev + instance * kMaxD, ev, sizeof(ev), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->z2ev_new + instance * kMaxD, ev, sizeof(ev), cudaMemcpyHostToDevice) != cudaSuccess)
     return c->sticky = HOTRG_EDEVICE;
-  c->z2 = true;
+  // the block-sparse squeeze resumes only once every instance is known to be structured (an
+  // instance given a dense tensor by hotrg_set_tensor, or stepped densely since, is not)
+  c->z2_inst[instance] = 1;
+  c->z2 = std::all_of(c->z2_inst.begin(), c->z2_inst.end(), [](char v) { return v != 0; });
   drop_graphs(c);
   for (int b = 0; b < c->d; ++b) c->dims[b] = dims[b];
   return HOTRG_OK;
@@ -1555,6 +1572,7 @@ int hotrg_state_load(hotrg_ctx* c, const void* host, size_t size) {
   c->steps = h.steps;
   c->last_axis = h.last_axis;
   c->z2 = h.z2 != 0;
+  std::fill(c->z2_inst.begin(), c->z2_inst.end(), c->z2 ? 1 : 0);
   drop_graphs(c);
   return HOTRG_OK;
 }

@@ -121,6 +121,7 @@ struct EigAxis {
 };
 struct EigAxes {
   int nt;
+  int max_sweeps;  // sweep limit (ST_NOCONV when reached)
   long long g_stride, u_stride;
   EigOut out;  // strides, step counter and step limit (its base is unused here)
   EigAxis ax[kMaxD];
@@ -133,7 +134,8 @@ void launch_eig_axes(const EigAxes& ea, int batch, int* status, cudaStream_t s, 
 // parity-pure sets ST_Z2.
 void launch_eig(const double* G, long long g_stride, int batch, int n, int chi, const EigOut& o,
                 double* U, long long u_stride, double* work, int* status, cudaStream_t s,
-                const int* z2_ev = nullptr, int* z2_ev_new = nullptr, int z2_axis = 0, int Db = 0);
+                const int* z2_ev = nullptr, int* z2_ev_new = nullptr, int z2_axis = 0, int Db = 0,
+                int max_sweeps = 40);
 // First-order change of the kept eigenvectors for a change dG of G, from the eigensystem that
 // launch_eig left in `work` (call before the next launch_eig reuses it):
 //   dU_k = sign_k sum_{j >= chi} V_j (V_j^T dG V_k) / (lambda_k - lambda_j),  k < chi,

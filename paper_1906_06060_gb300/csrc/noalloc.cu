@@ -9,10 +9,11 @@
 //
 // The array (kNoallocBytes, about 12 MiB) belongs to this library's device code: every GPU on
 // which it is used holds it until the process exits. Its device address is looked up once per
-// device with cudaGetSymbolAddress, on the first call made while that device is current; that
-// first call should therefore happen before any stream capture. All calls share the array, so
-// calls whose GPU work overlaps (different streams, or different host threads) race on it; the
-// call synchronises its stream before returning, so calls on one stream are safe in sequence.
+// device with cudaGetSymbolAddress, on the first call made while that device is current. Every
+// call synchronises its stream and copies the status word to the host, so the entry point
+// cannot be used inside a stream capture at all. All calls share the array, so calls whose GPU
+// work overlaps (different streams, or different host threads) race on it; calls on one stream
+// are safe in sequence.
 #include <mutex>
 
 #include "kernels.h"
@@ -22,7 +23,9 @@ namespace {
 
 constexpr long long kNoallocMaxElems = HOTRG_GEMM_NOALLOC_MAX_ELEMS;  // (M + N) * round_up(K, 64)
 constexpr size_t kNoallocStatusBytes = 256;
-constexpr size_t kNoallocBytes = kNoallocStatusBytes + 3 * 2 * (size_t)kNoallocMaxElems;
+// six bf16 planes of (M + N) * round_up(K, 64) elements in all, each plane start rounded up to
+// 256 bytes (at most 255 bytes of padding per plane): every request within the limit fits
+constexpr size_t kNoallocBytes = kNoallocStatusBytes + 3 * 2 * (size_t)kNoallocMaxElems + 6 * 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -62,6 +65,8 @@ extern "C" int hotrg_gemm_split_noalloc(const float* A, long long lda, const flo
                                         int npass, void* stream) {
   if (!A || !Bt || !C || M <= 0 || N <= 0 || K <= 0 || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
   if (npass != 1 && npass != 3 && npass != 4 && npass != 6) return HOTRG_EINVAL;
+  // the smallest problem the tensor-core kernel takes: one 128 x 256 output tile, one 64-wide k-block
+  if (M < 128 || N < 256 || K < 64) return HOTRG_EINVAL;
   const long long ld = round64(K);
   if (M > kNoallocMaxElems || N > kNoallocMaxElems || (M + N) > kNoallocMaxElems / ld) return HOTRG_EINVAL;
   int err = HOTRG_OK;

@@ -1,0 +1,69 @@
+// FP64 FMA throughput of the GPU: the denominator of the FP64 path's roofline. The paper's cost
+// statement (Sec. 2: O(Dcut^15) flops per step) fixes the work; how fast the FP64 squeeze can
+// run is set by the rate of the CUDA cores' double-precision FMA units, which this kernel
+// measures (independent FMA chains in every thread, enough warps to cover the FMA latency).
+#include "kernels.h"
+
+namespace hotrg {
+namespace {
+
+constexpr int kChains = 8;    // independent FMA chains per thread
+constexpr int kUnroll = 16;   // FMAs per chain per loop iteration
+
+__global__ void __launch_bounds__(256) k_dfma_chains(long long iters, double seed, double* sink) {
+  double a[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) a[i] = seed + 1e-9 * threadIdx.x + i;
+  // x -> x m + c contracts towards c / (1 - m) and stays finite for any number of iterations
+  const double m = 0.999999999999, c = 1e-13;
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r)
+#pragma unroll
+      for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s += a[i];
+  // a store the compiler cannot remove, taken by no thread in practice
+  if (s == -1.0) sink[blockIdx.x] = s;
+}
+
+}  // namespace
+}  // namespace hotrg
+
+using namespace hotrg;
+
+extern "C" int hotrg_bench_fp64_fma(long long iters, double* sink, double* tflops, void* stream) {
+  if (iters < 1 || iters > (1LL << 32) || !sink || !tflops) return HOTRG_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return HOTRG_EDEVICE;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = sms * 8, threads = 256;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return HOTRG_EDEVICE;
+  }
+  k_dfma_chains<<<blocks, threads, 0, s>>>(iters, 1.0, sink);  // warm-up (clocks, code load)
+  cudaEventRecord(e0, s);
+  k_dfma_chains<<<blocks, threads, 0, s>>>(iters, 1.0, sink);
+  cudaEventRecord(e1, s);
+  count_launches(2);
+  float ms = 0.f;
+  const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok || ms <= 0.f) {
+    cudaGetLastError();
+    return HOTRG_EDEVICE;
+  }
+  const double flops = 2.0 * (double)iters * kUnroll * kChains * (double)blocks * threads;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return HOTRG_OK;
+}

@@ -1,0 +1,149 @@
+"""Failure detection through the C ABI: every failure is made on the host or by a wait limit
+that runs out, never by a GPU fault.
+
+* HOTRG_ETIMEOUT: a context whose device-side wait limit is far below the time one k-block of
+  the tensor-core GEMM takes. The GEMM's waits give up, the kernel drains the copies and MMAs
+  it issued (those waits have a floor of one second: issued work always completes), frees its
+  tensor memory and returns; the host reads the status word.
+* HOTRG_ENUMERIC: a tensor with a NaN entry, loaded from the host (the norm of the next step
+  is not finite); a tensor with a negative trace (the free energy has no logarithm).
+* HOTRG_ENOCONV: an eigensolver sweep limit of one sweep on a generic Gram matrix.
+
+Each error is sticky on its context, the context stays queryable (calls return the error
+instead of failing), and the device stays usable for new contexts.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from tests.inputs import random_site_tensor, random_z2_site_tensor
+from oracle import hotrg_ref as R
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _flow(*args, **kw):
+    from paper_1906_06060_gb300 import HOTRG
+    return HOTRG(*args, **kw)
+
+
+def _fresh_context_still_matches_the_oracle():
+    with open(os.path.join(GOLDEN, "flow_d4_b0.1497_h0_D5_n16.json")) as fh:
+        g = json.load(fh)
+    with _flow(4, 0.1497, 0.0, 5) as f:
+        for _ in range(4):
+            f.step()
+        lnz = f.free_energy()[0][0]
+    assert abs(lnz - g["steps"][3]["lnz"]) < 1e-12 * abs(lnz)
+
+
+def test_wait_limit_that_runs_out_gives_etimeout_and_a_usable_device():
+    from paper_1906_06060_gb300 import HotrgError, _lib
+    # 100 ns: shorter than any TMA copy or k-block of MMAs; steps 3 and 4 run the tensor-core GEMM
+    with _flow(4, 0.1497, 0.0, 5, precision="bf16x3", fp64_steps=2, wait_timeout_s=1e-7, graphs=False) as f:
+        code = None
+        try:
+            for _ in range(4):
+                f.step()
+            f.free_energy()
+        except HotrgError as e:
+            code = e.code
+        assert code == _lib.HOTRG_ETIMEOUT
+        # sticky: every later call reports it, and nothing else goes wrong
+        for call in (f.step, f.free_energy, f.observables, f.ln_norms):
+            with pytest.raises(HotrgError) as e:
+                call()
+            assert e.value.code == _lib.HOTRG_ETIMEOUT
+        assert f.dims() is not None  # host-side query still answers
+    _fresh_context_still_matches_the_oracle()
+
+
+def test_nan_tensor_gives_enumeric():
+    from paper_1906_06060_gb300 import HotrgError, _lib
+    T = random_site_tensor((2, 2, 2, 2), seed=5)
+    T[0, 1, 0, 1, 1, 0, 1, 0] = np.nan
+    with _flow(4, 0.3, 0.0, 4) as f:
+        f.set_tensor(T)
+        f.step(3)
+        with pytest.raises(HotrgError) as e:
+            f.free_energy()
+        assert e.value.code == _lib.HOTRG_ENUMERIC
+        with pytest.raises(HotrgError) as e:
+            f.step()
+        assert e.value.code == _lib.HOTRG_ENUMERIC
+    _fresh_context_still_matches_the_oracle()
+
+
+def test_negative_trace_gives_enumeric_without_poisoning_the_flow():
+    from paper_1906_06060_gb300 import HotrgError, _lib
+    P = 16
+    T = -np.eye(P).reshape((2,) * 8)
+    with _flow(4, 0.3, 0.0, 4) as f:
+        f.set_tensor(T)
+        with pytest.raises(HotrgError) as e:
+            f.free_energy()
+        assert e.value.code == _lib.HOTRG_ENUMERIC
+        # the flow state itself is valid: a positive tensor afterwards gives a free energy
+        f.set_tensor(np.eye(P).reshape((2,) * 8))
+        lnz = f.free_energy()[0][0]
+        assert math.isfinite(lnz)
+
+
+def test_sweep_limit_gives_enoconv():
+    from paper_1906_06060_gb300 import HotrgError, _lib
+    T = random_site_tensor((3, 3, 3, 3), seed=9)
+    with _flow(4, 0.3, 0.0, 9, max_sweeps=1) as f:
+        f.set_tensor(T)
+        f.step(0)
+        with pytest.raises(HotrgError) as e:
+            f.free_energy()
+        assert e.value.code == _lib.HOTRG_ENOCONV
+    # the default limit converges on the same matrix, and the result matches the oracle
+    ref, _ = R.coarse_grain(T, 0, 9)
+    with _flow(4, 0.3, 0.0, 9) as f:
+        f.set_tensor(T)
+        f.step(0)
+        assert abs(f.ln_norms()[1] - math.log(R.frobenius(ref))) < 1e-12
+
+
+def test_sweep_limit_out_of_range_is_refused():
+    from paper_1906_06060_gb300 import HotrgError, _lib
+    with pytest.raises(HotrgError) as e:
+        _flow(4, 0.3, 0.0, 4, max_sweeps=1001)
+    assert e.value.code == _lib.HOTRG_EINVAL
+
+
+def test_batched_set_tensor_z2_keeps_the_dense_squeeze_while_an_instance_is_unstructured():
+    """Two instances of a zero-field context: instance 0 gets an arbitrary tensor (set_tensor),
+    instance 1 a block-structured one (set_tensor_z2). The context must keep squeezing densely,
+    or instance 0's odd-parity entries would be dropped: both coarse-grained tensors match the
+    oracle element by element. Once instance 0 is given a structured tensor too, the
+    block-sparse squeeze resumes and the gauge-invariant results (ln c, spectra) still match."""
+    dims, evens = (2, 2, 2, 2), (1, 1, 1, 1)
+    T0 = random_site_tensor(dims, seed=21)
+    T1 = random_z2_site_tensor(dims, evens, seed=22)
+    with _flow(4, [0.2, 0.2], 0.0, 4, z2=True) as f:
+        f.set_tensor(T0, instance=0)
+        f.set_tensor(T1, instance=1, evens=evens)
+        f.step(3)
+        for i, T in enumerate((T0, T1)):
+            ref, info = R.coarse_grain(T, 3, 4)
+            ref /= R.frobenius(ref)
+            got = f.get_tensor(i)
+            np.testing.assert_allclose(got, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+    S0 = random_z2_site_tensor(dims, evens, seed=23)
+    with _flow(4, [0.2, 0.2], 0.0, 4, z2=True) as f:
+        f.set_tensor(T0, instance=0)
+        f.set_tensor(T1, instance=1, evens=evens)
+        f.set_tensor(S0, instance=0, evens=evens)  # now both structured: block-sparse again
+        f.step(3)
+        for i, T in enumerate((S0, T1)):
+            ref, info = R.coarse_grain(T, 3, 4)
+            assert abs(f.ln_norms(i)[1] - math.log(R.frobenius(ref))) < 1e-12
+            for b, iso in info.isometries.items():
+                np.testing.assert_allclose(f.spectra(1, b, i), iso.eigenvalues, rtol=0,
+                                           atol=1e-12 * iso.eigenvalues[0])

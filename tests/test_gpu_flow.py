@@ -187,17 +187,21 @@ def test_fp64_2d_flow_40_steps_matches_oracle_and_onsager():
     assert abs(lnz - E.lnz_onsager(0.3)) < 1e-6
 
 
-@pytest.mark.parametrize("precision,x6_steps,bound", [("bf16x6", 0, 2e-7), ("bf16x3", 8, 2e-7),
-                                                     ("bf16x3", 0, 3e-7)])
-def test_split_flow_dcut5_relative_free_energy(precision, x6_steps, bound):
-    """Split-precision paths: |delta f / f| against the FP64 oracle after every step.
+@pytest.mark.parametrize("precision,fp64_steps,x6_steps,bound", [
+    ("bf16x3", 3, 12, 1e-7),   # the mixed path: the benchmark's schedule, the benchmark spec's 1e-7
+    ("bf16x6", 3, 0, 1e-7),    # six-product GEMM after the FP64 steps
+    ("bf16x3", 2, 0, 3e-7),    # BF16X3 products alone from step 3: not the mixed path (see below)
+])
+def test_split_flow_dcut5_relative_free_energy(precision, fp64_steps, x6_steps, bound):
+    """Split-precision flows: |delta f / f| against the FP64 oracle after every step.
 
-    The bound is set by the tensor cores' FP32 accumulation, which rounds toward zero: each
-    k-block's partial sum (restarted every 64 K, folded with round-to-nearest) keeps a bias
-    of about 2^-24 relative, which the flow turns into ~1e-7 in ln Z/N."""
+    The mixed path (FP64 for steps 1-3, where the flow's early steps weigh most, six-product
+    GEMMs to step 12, BF16X3 after) must meet 1e-7. BF16X3 alone drops the lo*lo product, which
+    is systematic when both GEMM operands come from the same tensor; it is checked separately
+    with its own bound and is not what the benchmark runs."""
     g = golden("flow_d4_b0.1497_h0_D5_n16")
     worst = 0.0
-    with flow(4, 0.1497, 0.0, 5, precision=precision, fp64_steps=2, x6_steps=x6_steps) as f:
+    with flow(4, 0.1497, 0.0, 5, precision=precision, fp64_steps=fp64_steps, x6_steps=x6_steps) as f:
         for st in g["steps"]:
             f.step()
             lnz = f.free_energy()[0][0]
@@ -291,6 +295,15 @@ def test_error_codes():
         f.step()
 
 
+def test_gpu_x_indicator_1d_matches_transfer_matrix():
+    """X^(n) on the device against the exact d = 1 value (transfer-matrix eigenvalues)."""
+    beta, h = 0.5, 0.1
+    with flow(1, beta, h, 4) as f:
+        for n in range(1, 9):
+            f.step()
+            assert abs(f.observables()["x_indicator"] - E.x_1d(beta, h, 2 ** n)) < 1e-13, n
+
+
 def test_autotune_picks_a_candidate_and_keeps_accuracy():
     g = golden("flow_d4_b0.1497_h0_D5_n16")
     with flow(4, 0.1497, 0.0, 5, precision="bf16x3", fp64_steps=2) as f:
@@ -304,4 +317,5 @@ def test_autotune_picks_a_candidate_and_keeps_accuracy():
         for _ in range(4):
             f.step()
         lnz = f.free_energy()[0][0]
+    # BF16X3 products alone from step 3 (the bound of that case above): tuning must not cost accuracy
     assert abs(lnz - g["steps"][7]["lnz"]) < 3e-7 * abs(lnz)

@@ -188,12 +188,42 @@ def test_sliced_squeeze_matches_whole_network(d, dims, a, Dcut):
                                rtol=1e-12, atol=1e-12)
 
 
+def test_squeeze_slice_selection_picks_the_same_slices():
+    """The slice selection used by the full-size parity tests only chooses which slices to
+    compute: the selected slices equal those of the whole squeeze, the others stay zero."""
+    d, dims, a, Dcut = 4, (3, 2, 3, 2), 1, 5
+    T = random_site_tensor(dims, seed=77)
+    U = {b: R.isometry_from_gram(R.gram(T, a, b), dims[b], Dcut).U for b in range(d) if b != a}
+    full = R.squeeze(T, T, a, U)
+    pick = {(0, 0, 1), (4, 2, 3)}
+    part = R.squeeze(T, T, a, U, slices=pick)
+    for k0 in range(full.shape[0]):
+        for k2 in range(full.shape[2]):
+            for k3 in range(full.shape[3]):
+                sl = (k0, slice(None), k2, k3)
+                if (k0, k2, k3) in pick:
+                    assert np.array_equal(part[sl], full[sl])
+                else:
+                    assert not np.any(part[sl])
+
+
 def test_x_indicator_phases():
     """X^(n) -> 1 in the disordered and -> 2 in the ordered phase (Sec. 3, Eq. (x))."""
     hot = R.run(4, 0.10, 0.0, 4, 24)
     cold = R.run(4, 0.25, 0.0, 4, 24)
     assert abs(hot.x[-1] - 1.0) < 1e-3
     assert abs(cold.x[-1] - 2.0) < 1e-3
+
+
+@pytest.mark.parametrize("beta,h", [(0.5, 0.1), (1.3, -0.02), (0.2, 0.3), (0.9, 0.0)])
+def test_x_indicator_1d_matches_transfer_matrix(beta, h):
+    """Exact pin of X^(n) (Eqs. (matA), (x)): in d = 1 the flow's tensor is the site matrix to the
+    power 2^n, so X is fixed by the transfer-matrix eigenvalues at every step (values well
+    between 1 and 2 at the first steps)."""
+    f = R.run(1, beta, h, 4, 8)
+    for n in range(1, 9):
+        assert abs(f.x[n - 1] - E.x_1d(beta, h, 2 ** n)) < 1e-13, n
+    assert 1.01 < f.x[0] < 1.99
 
 
 def test_dims_schedule_reaches_dcut_at_step_3():
