@@ -29,6 +29,8 @@ Other workloads of the same path (same JSON line; e2e and the CPU baseline only 
     --workload accuracy  per-step |delta(lnZ/N)| / |lnZ/N| of split-precision schedules against the
                        FP64 GPU flow (--ref-steps of it, timed step by step) and the oracle's golden
     --workload gemm    the tcgen05 squeeze GEMM alone (--gemm-shape M,N,K --npass)
+    --workload phase   X^(n) flows at the temperatures --temps (h = 0), classified ordered /
+                       disordered (Sec. 3: T_c(Dcut = 13) = 6.650365(5) on 1024^4)
 
 Multi-GPU (torchrun, one process per GPU): the single-flow workload does not shard, so each rank
 runs an independent replica; value = total flops of all ranks / max time over ranks.
@@ -61,19 +63,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=12)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x4", "bf16x6", "fp64"])
+    ap.add_argument("--precision", default="bf16x3",
+                    choices=["bf16x3", "bf16x4", "bf16x6", "fp16x3", "fp16x4", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--kblock", type=int, default=64)
     ap.add_argument("--fold-group", type=int, default=0)
     ap.add_argument("--x6-steps", type=int, default=12)
-    ap.add_argument("--workload", default="flow", choices=["flow", "scan", "deriv", "accuracy", "gemm"])
+    ap.add_argument("--workload", default="flow", choices=["flow", "scan", "deriv", "accuracy", "gemm", "phase"])
+    ap.add_argument("--temps", default="6.650355,6.650375",
+                    help="phase workload: temperatures T = 1/beta of the X^(n) flows (h = 0)")
     ap.add_argument("--gemm-shape", default="10000,40000,10000",
                     help="gemm workload: M,N,K of the squeeze GEMM alone (default: a quarter of one Dcut=10 chunk)")
     ap.add_argument("--npass", type=int, default=3, help="gemm workload: split products (1, 3, 4 or 6)")
     ap.add_argument("--ref-steps", type=int, default=8,
                     help="accuracy workload: steps of the FP64 GPU reference flow (0: read the committed one)")
     ap.add_argument("--flow-steps", type=int, default=40, help="accuracy workload: steps of each split flow")
-    ap.add_argument("--schedules", default="bf16x3:3:12,bf16x3:3:0,bf16x6:3:0",
+    ap.add_argument("--schedules", default="bf16x3:3:12,bf16x3:3:0,bf16x6:3:0,fp16x3:3:0,fp16x4:3:0,fp16x3:2:0",
                     help="accuracy workload: precision:fp64_steps:x6_steps of each split flow")
     ap.add_argument("--instances", type=int, default=0)
     ap.add_argument("--dcut", type=int, default=0)
@@ -84,6 +89,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=2)
+    ap.add_argument("--log-jsonl", default="",
+                    help="flow workload: write one JSON record per step of the e2e flow to this file")
     a = ap.parse_args()
     if not a.dcut:
         a.dcut = 8 if a.workload == "scan" else 10
@@ -432,7 +439,10 @@ def run_accuracy(a):
     ref, ref_src = {}, None
     if a.ref_steps > 0:
         steps = []
-        with HOTRG(4, a.beta, a.h, a.dcut, precision="fp64", z2=z2, stream=stream, graphs=False) as f:
+        # the workspace plan covers only the states these steps reach (Dcut = 13 in FP64 would
+        # otherwise plan steady-state FP64 buffers of about 100 GB)
+        with HOTRG(4, a.beta, a.h, a.dcut, precision="fp64", z2=z2, stream=stream, graphs=False,
+                   max_steps=a.ref_steps) as f:
             for n in range(1, a.ref_steps + 1):
                 f.timing_start()
                 f.step()
@@ -458,7 +468,7 @@ def run_accuracy(a):
         lnzs = []
         t0 = time.perf_counter()
         with HOTRG(4, a.beta, a.h, a.dcut, precision=prec, fp64_steps=int(f64), x6_steps=int(x6), z2=z2,
-                   stream=stream) as f:
+                   stream=stream, max_steps=a.flow_steps) as f:
             for _ in range(a.flow_steps):
                 f.step()
                 lnzs.append(float(f.free_energy()[0][0]))
@@ -520,6 +530,40 @@ def run_gemm(a):
             "note": "each timed launch includes the FP32 -> bf16 plane split of A and Bt",
             "alg_tflops": flops / (best * 1e-3) / 1e12, "tensor_tflops": a.npass * flops / (best * 1e-3) / 1e12}
 
+
+# ----------------------------------------------------------------------------- X^(n) phase flows
+def run_phase(a):
+    """X^(n) flows (Sec. 3, Eq. (x)) of the 4D Ising model at h = 0 at the given temperatures, each
+    its own context (block-sparse squeeze, the precision schedule of --precision / --fp64-steps /
+    --x6-steps), --flow-steps steps (40: the 1024^4 lattice); every flow classified from its
+    converged tail (paper_1906_06060_gb300.phase). Progress goes to stderr one line per step."""
+    import torch
+    from paper_1906_06060_gb300 import HOTRG, phase
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    temps = [float(t) for t in a.temps.split(",") if t]
+    flows = []
+    for T in temps:
+        xs, lnz, ms = [], [], []
+        with HOTRG(4, 1.0 / T, 0.0, a.dcut, precision=a.precision, fp64_steps=a.fp64_steps, x6_steps=a.x6_steps,
+                   z2=not a.no_z2, stream=stream, max_steps=a.flow_steps) as f:
+            for n in range(1, a.flow_steps + 1):
+                t0 = time.perf_counter()
+                f.step()
+                ob = f.observables()
+                ms.append(1e3 * (time.perf_counter() - t0))
+                xs.append(ob["x_indicator"])
+                lnz.append(ob["lnz_per_site"])
+                print(json.dumps({"T": T, "n": n, "x": xs[-1], "lnz": lnz[-1], "ms": ms[-1]}), file=sys.stderr,
+                      flush=True)
+        flows.append({"T": T, "beta": 1.0 / T, "x": xs, "lnz": lnz, "ms_per_step": ms,
+                      "phase": phase.classify(xs)})
+    br = phase.bracket([fl["beta"] for fl in flows], [fl["phase"] for fl in flows])
+    return {"workload": "phase", "d": 4, "h": 0.0, "Dcut": a.dcut, "steps": a.flow_steps,
+            "precision": a.precision, "fp64_steps": a.fp64_steps, "x6_steps": a.x6_steps, "z2": not a.no_z2,
+            "flows": flows, "beta_bracket": br,
+            "T_bracket": [1.0 / br[1], 1.0 / br[0]] if br else None}
+
 def e2e(a):
     """Same metric through the public API from host inputs: context creation (beta, h copied
     from host), W + K steps with the free energy read back to the host after every step."""
@@ -532,19 +576,48 @@ def e2e(a):
                  kblock=a.kblock, fold_group=a.fold_group, z2=use_z2(a))
     flops = 0.0
     dims = [2, 2, 2, 2]
+    records = []
+    lnzs = []
     for n in range(nsteps):
         ax = 3 - (n % 4)
         P = math.prod(dims)
         chi = [min(dims[b] ** 2, a.dcut) for b in range(4) if b != ax]
         flops += 2.0 * math.prod(chi) * P ** 3
         dims = [dims[b] if b == ax else min(dims[b] ** 2, a.dcut) for b in range(4)]
+        ts = time.perf_counter()
         flow.step()
-        flow.free_energy()
+        lnzs.append(float(flow.free_energy()[0][0]))
+        if a.log_jsonl:
+            rec = flow.step_record()
+            rec["wall_ms"] = 1e3 * (time.perf_counter() - ts)
+            records.append(rec)
     dt = time.perf_counter() - t0
     flow.close()
-    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16.0 / nsteps,
-            "d2h_bytes_per_step": 3 * 8 + 4, "steps": nsteps,
-            "note": "wall clock: context creation + every step + host read of ln Z/N after each step"}
+    if a.log_jsonl:
+        # written after the timed flow (the records' queries are inside it: they synchronise anyway)
+        with open(a.log_jsonl, "w") as fh:
+            for rec in records:
+                fh.write(json.dumps(rec) + "\n")
+    out = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16.0 / nsteps,
+           "d2h_bytes_per_step": 3 * 8 + 4, "steps": nsteps,
+           "note": "wall clock: context creation + every step + host read of ln Z/N after each step"}
+    return out, lnzs
+
+
+def accuracy_line(a, lnzs):
+    """|delta(lnZ/N)| / |lnZ/N| of this run's flow after each step against the FP64 GPU flow of the
+    committed accuracy summary (steps 1-8, same configuration) and the oracle's golden (steps 1-4)."""
+    if not (a.dcut == 10 and a.beta == 0.1497 and a.h == 0.0):
+        return None
+    ref, ora = stored_fp64_reference(), oracle_golden_lnz()
+    rel = {str(n): abs(lnzs[n - 1] - v) / abs(v) for n, v in sorted(ref.items()) if n <= len(lnzs)}
+    rel_o = {str(n): abs(lnzs[n - 1] - v) / abs(v) for n, v in sorted(ora.items()) if n <= len(lnzs)}
+    return {"rel_err_vs_fp64_gpu": rel, "rel_err_vs_oracle": rel_o,
+            "lnz_per_site_last": lnzs[-1] if lnzs else None,
+            "basis": "ln Z/N of the e2e flow (this run, this schedule) after each step, against the FP64 GPU "
+                     "flow recorded in profiles/accuracy_fp64_vs_split_dcut10.md and the FP64 oracle's "
+                     "tests/golden/flow_d4_b0.1497_h0_D10_n4.json; the measured tail beyond step 8 "
+                     "is in that summary"}
 
 
 def main():
@@ -567,10 +640,11 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    if a.workload in ("accuracy", "gemm"):
+    if a.workload in ("accuracy", "gemm", "phase"):
         from paper_1906_06060_gb300 import build
         build.build()
-        print(json.dumps(run_accuracy(a) if a.workload == "accuracy" else run_gemm(a)))
+        run = {"accuracy": run_accuracy, "gemm": run_gemm, "phase": run_phase}[a.workload]
+        print(json.dumps(run(a)))
         return
     if a.warmup < 3:
         print("warm-up must be >= 3 steps", file=sys.stderr)
@@ -580,7 +654,10 @@ def main():
     out = run_ours(a, rank, world, dist)
     if out is not None:
         if not a.no_e2e and a.workload == "flow":
-            out["e2e"] = e2e(a)
+            out["e2e"], lnzs = e2e(a)
+            acc = accuracy_line(a, lnzs)
+            if acc:
+                out["accuracy"] = acc
         if not a.no_cpu_baseline and world == 1 and a.workload == "flow":
             dt, f = oracle_sample(a.dcut, a.cpu_slices)
             out["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_threads(),

@@ -55,15 +55,24 @@ typedef enum hotrg_precision {
                        and ln sums stay FP64; other intermediates are FP32. */
   HOTRG_BF16X6 = 2, /* as BF16X3 with three planes x = hi + mid + lo and the six products
                        hh, hm, mh, hl, mm, lh: O(2^-24) per product, twice the tensor work */
-  HOTRG_BF16X4 = 3  /* two planes and all four products (adds lo*lo): no systematic
+  HOTRG_BF16X4 = 3, /* two planes and all four products (adds lo*lo): no systematic
                        truncation of the product, O(2^-17) unbiased per product */
+  HOTRG_FP16X3 = 4, /* as BF16X3 with fp16 planes: each operand is first scaled by an exact power
+                       of two 2^e (from its largest magnitude, measured on the device, so that it
+                       lies below 2^15), then split x 2^e = hi + lo in fp16 (11 significant bits
+                       each); hi*hi + hi*lo + lo*hi accumulate in FP32 and the result is scaled
+                       back by 2^-(eA + eB): O(2^-22) relative error per product (entries more than
+                       2^-18 below their operand's largest lose the lo part's low bits, an absolute
+                       error below 2^-39 of that largest), at the tensor cost of BF16X3 */
+  HOTRG_FP16X4 = 5  /* FP16X3 plus lo*lo: no systematic truncation of the product */
 } hotrg_precision;
 
 typedef struct hotrg_opts {
   int precision;          /* hotrg_precision (default HOTRG_FP64) */
-  int fp64_steps;         /* in BF16X3/X6 modes the first fp64_steps steps run in FP64 (default 2) */
-  int x6_steps;           /* in BF16X3/X4 modes, steps fp64_steps+1 .. x6_steps use the 6-pass
-                             GEMM (the early steps weigh 2^-n in ln Z/N; default 0) */
+  int fp64_steps;         /* in the split modes the first fp64_steps steps run in FP64 (default 2) */
+  int x6_steps;           /* in the two-plane split modes (BF16X3/X4, FP16X3/X4), steps
+                             fp64_steps+1 .. x6_steps use the 6-pass BF16X6 GEMM (the early steps
+                             weigh 2^-n in ln Z/N; default 0) */
   int batch;              /* independent (beta, h) instances in the context (default 1) */
   const double *beta;     /* [batch] host array; NULL: all instances use the beta argument */
   const double *h;        /* [batch] host array; NULL: all instances use the h argument */
@@ -283,14 +292,26 @@ int hotrg_gemm_split_noalloc(const float *A, long long lda, const float *Bt, lon
                              long long ldc, long long M, long long N, long long K, int npass,
                              void *stream);
 
-/* Status of the last hotrg_gemm_split call that used `scratch` (0 = ok, HOTRG_ETIMEOUT if a
- * pipeline wait of the GEMM kernel gave up). The word lives in the first bytes of scratch and
- * is cleared by each GEMM call. Synchronises `stream`. */
+/* The same GEMM with fp16 planes (the FP16X3 / FP16X4 products of the flow): A and Bt are each
+ * scaled by an exact power of two 2^e from their largest magnitude (measured on the device) so
+ * that they lie below 2^15, split x 2^e = hi + lo in fp16, multiplied on the tensor cores
+ * (npass 1: hi*hi; 3: + hi*lo + lo*hi; 4: + lo*lo) with FP32 accumulation, and the result is
+ * scaled back by 2^-(eA + eB). Per product O(2^-22) relative error, plus an absolute error below
+ * 2^-39 x max|A| |b| (resp. max|Bt| |a|) for entries far below their operand's largest. Same
+ * arguments, sizes, scratch (hotrg_gemm_scratch_bytes) and errors as hotrg_gemm_split. */
+int hotrg_gemm_split_f16(const float *A, long long lda, const float *Bt, long long ldb, float *C,
+                         long long ldc, long long M, long long N, long long K, int npass, int kblock,
+                         int fold_group, void *scratch, size_t scratch_bytes, void *stream);
+
+/* Status of the last hotrg_gemm_split or hotrg_gemm_split_f16 call that used `scratch` (0 = ok,
+ * HOTRG_ETIMEOUT if a pipeline wait of the GEMM kernel gave up). The word lives in the first bytes
+ * of scratch and is cleared by each GEMM call. Synchronises `stream`. */
 int hotrg_gemm_status(const void *scratch, void *stream);
 
 /* Benchmark support (the paper has no counterpart): the GPU's FP64 FMA rate, measured with
- * independent FMA chains on every SM (two launches of `iters` loop iterations; the second is timed
- * with CUDA events on `stream`). It is the roofline denominator of the FP64 squeeze, whose cost is
+ * independent FMA chains on every SM (8, 16 and 32 chains per thread, each as two launches of
+ * `iters` loop iterations of which the second is timed with CUDA events on `stream`; the best
+ * rate is returned). It is the roofline denominator of the FP64 squeeze, whose cost is
  * fixed by Sec. 2's O(Dcut^15) statement. `sink` is a device array of at least 8 x (SM count)
  * doubles that the kernel may write (in practice it writes nothing); *tflops receives the rate.
  * Synchronises `stream`. Errors: EINVAL (iters outside 1..2^32, null pointers), EDEVICE. */

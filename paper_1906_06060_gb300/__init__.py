@@ -17,11 +17,13 @@ from ctypes import byref, c_double, c_int, c_size_t, c_void_p
 import numpy as np
 
 from . import _lib
-from ._lib import HOTRG_BF16X3, HOTRG_BF16X4, HOTRG_BF16X6, HOTRG_FP64, HotrgError, check
+from ._lib import (HOTRG_BF16X3, HOTRG_BF16X4, HOTRG_BF16X6, HOTRG_FP16X3, HOTRG_FP16X4, HOTRG_FP64, HotrgError,
+                   check)
 
 __all__ = ["HOTRG", "HotrgError", "gemm_split", "workspace_bytes", "fp64_fma_tflops", "PRECISIONS"]
 
-PRECISIONS = {"fp64": HOTRG_FP64, "bf16x3": HOTRG_BF16X3, "bf16x4": HOTRG_BF16X4, "bf16x6": HOTRG_BF16X6}
+PRECISIONS = {"fp64": HOTRG_FP64, "bf16x3": HOTRG_BF16X3, "bf16x4": HOTRG_BF16X4, "bf16x6": HOTRG_BF16X6,
+              "fp16x3": HOTRG_FP16X3, "fp16x4": HOTRG_FP16X4}
 # derivative modes: isometries held fixed, or differentiated through the eigendecomposition
 _DERIV = {"none": 0, "fixed": 1, "eig": 2}
 
@@ -141,6 +143,31 @@ class HOTRG:
         check(_lib.load().hotrg_ln_norms(self._ctx, instance, buf, 65, byref(n)), "hotrg_ln_norms")
         return np.array(buf[: n.value])
 
+    def step_record(self, instance: int = 0, top: int = 6) -> dict:
+        """Summary of the last step of one instance, for a per-step log (one JSON object per step):
+        step number n, axis, bond dimensions after the step, ln c_n, ln Z/N, X^(n), and for each
+        transverse axis the leading Gram eigenvalues relative to the largest, the discarded
+        weight (sum of the eigenvalues beyond the kept chi over their total) and the relative gap
+        at the cut ((lam_chi - lam_chi+1) / lam_chi; null when nothing is cut). Synchronises."""
+        ob = self.observables(instance)
+        n, axis = ob["steps"], ob["last_axis"]
+        rec = {"n": n, "axis": axis, "dims": list(self.dims()), "ln_c": ob["last_ln_c"],
+               "lnz_per_site": ob["lnz_per_site"], "x": ob["x_indicator"], "cuts": {}}
+        if n < 1:
+            return rec
+        for b, chi in enumerate(rec["dims"]):
+            lam = self.spectra(n, b, instance)
+            if b == axis or lam.size == 0 or lam[0] <= 0:
+                continue
+            lam = np.clip(lam, 0.0, None)
+            total = float(lam.sum())
+            cut = chi < lam.size
+            rec["cuts"][str(b)] = {
+                "chi": int(chi), "top": [float(x) for x in lam[:top] / lam[0]],
+                "discarded_weight": float(lam[chi:].sum() / total) if cut else 0.0,
+                "gap": float((lam[chi - 1] - lam[chi]) / lam[chi - 1]) if cut and lam[chi - 1] > 0 else None}
+        return rec
+
     def dims(self) -> tuple:
         dims = (c_int * 4)()
         check(_lib.load().hotrg_get_tensor(self._ctx, 0, dims, None, 0), "hotrg_get_tensor")
@@ -214,9 +241,11 @@ class HOTRG:
             pass
 
 
-def gemm_split(A, Bt, npass: int = 3, C=None, stream=None, kblock: int = 0, fold_group: int = 0):
+def gemm_split(A, Bt, npass: int = 3, C=None, stream=None, kblock: int = 0, fold_group: int = 0,
+               fp16: bool = False):
     """C = A @ Bt^T through the tcgen05 kernel (A: M x K, Bt: N x K, float32 CUDA tensors);
-    npass 1 / 3 / 4 / 6 selects hi*hi, BF16X3, BF16X4 or BF16X6 products."""
+    npass 1 / 3 / 4 / 6 selects hi*hi, BF16X3, BF16X4 or BF16X6 products; fp16=True the scaled
+    fp16 planes (npass 1 / 3 / 4: hi*hi, FP16X3, FP16X4)."""
     torch = _torch()
     lib = _lib.load()
     assert A.dtype == torch.float32 and Bt.dtype == torch.float32 and A.is_cuda and Bt.is_cuda
@@ -227,15 +256,16 @@ def gemm_split(A, Bt, npass: int = 3, C=None, stream=None, kblock: int = 0, fold
     stream = stream or torch.cuda.current_stream()
     nbytes = lib.hotrg_gemm_scratch_bytes(M, N, K)
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=A.device)
-    check(lib.hotrg_gemm_split(c_void_p(A.data_ptr()), A.stride(0), c_void_p(Bt.data_ptr()), Bt.stride(0),
-                                c_void_p(C.data_ptr()), C.stride(0), M, N, K, npass, kblock, fold_group,
-                                c_void_p(scratch.data_ptr()), nbytes, c_void_p(stream.cuda_stream)),
-          "hotrg_gemm_split")
+    fn = lib.hotrg_gemm_split_f16 if fp16 else lib.hotrg_gemm_split
+    check(fn(c_void_p(A.data_ptr()), A.stride(0), c_void_p(Bt.data_ptr()), Bt.stride(0),
+             c_void_p(C.data_ptr()), C.stride(0), M, N, K, npass, kblock, fold_group,
+             c_void_p(scratch.data_ptr()), nbytes, c_void_p(stream.cuda_stream)),
+          "hotrg_gemm_split_f16" if fp16 else "hotrg_gemm_split")
     check(lib.hotrg_gemm_status(c_void_p(scratch.data_ptr()), c_void_p(stream.cuda_stream)), "gemm status")
     return C
 
 
-def fp64_fma_tflops(iters: int = 1 << 16, stream=None) -> float:
+def fp64_fma_tflops(iters: int = 1 << 14, stream=None) -> float:
     """The GPU's FP64 FMA rate in TFLOP/s (hotrg_bench_fp64_fma): the roofline denominator of
     the FP64 squeeze."""
     torch = _torch()

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libhotrg.so")
 
 HOTRG_OK, HOTRG_EINVAL, HOTRG_ENOMEM, HOTRG_ENUMERIC = 0, -1, -2, -3
 HOTRG_ENOCONV, HOTRG_ETIMEOUT, HOTRG_EDEVICE, HOTRG_ESTATE, HOTRG_ENOTSUP = -4, -5, -6, -7, -8
-HOTRG_FP64, HOTRG_BF16X3, HOTRG_BF16X6, HOTRG_BF16X4 = 0, 1, 2, 3
+HOTRG_FP64, HOTRG_BF16X3, HOTRG_BF16X6, HOTRG_BF16X4, HOTRG_FP16X3, HOTRG_FP16X4 = 0, 1, 2, 3, 4, 5
 
 
 class Opts(ctypes.Structure):
@@ -65,6 +65,9 @@ _SIGS = {
     "hotrg_gemm_split": (c_int, [c_void_p, c_longlong, c_void_p, c_longlong, c_void_p, c_longlong,
                                  c_longlong, c_longlong, c_longlong, c_int, c_int, c_int, c_void_p, c_size_t,
                                  c_void_p]),
+    "hotrg_gemm_split_f16": (c_int, [c_void_p, c_longlong, c_void_p, c_longlong, c_void_p, c_longlong,
+                                     c_longlong, c_longlong, c_longlong, c_int, c_int, c_int, c_void_p, c_size_t,
+                                     c_void_p]),
     "hotrg_gemm_status": (c_int, [c_void_p, c_void_p]),
     "hotrg_gemm_split_noalloc": (c_int, [c_void_p, c_longlong, c_void_p, c_longlong, c_void_p, c_longlong,
                                          c_longlong, c_longlong, c_longlong, c_int, c_void_p]),

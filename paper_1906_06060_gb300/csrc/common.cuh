@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "../../include/hotrg.h"
@@ -66,15 +67,50 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// Exponent e of the power-of-two scale 2^e applied to an operand before its fp16 split, for an
+// operand whose entries are bounded by `bound`: the largest e with bound * 2^e < 2^15, so every
+// scaled entry is below 2^15 (fp16 holds up to 65504) and the largest one is at least 2^14.
+// Clamped to [-60, 60] (0 for a zero or non-finite bound). Both the operand builders and the GEMM's
+// epilogue (which multiplies by 2^-(eA + eB)) compute it with this function from the same inputs.
+__host__ __device__ __forceinline__ int f16_scale_exponent(float bound) {
+  if (!(bound > 0.f) || !(bound < 3.0e38f)) return 0;
+  int ex = 0;
+  frexpf(bound, &ex);  // bound = f 2^ex, 0.5 <= f < 1
+  int e = 15 - ex;
+  return e < -60 ? -60 : (e > 60 ? 60 : e);
+}
+// 2^e as a float, exactly, for |e| <= 126
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
 // Operand planes of a split-precision GEMM operand: nparts = 2 (hi, lo) or 3 (hi, mid, lo),
-// part i = rn_bf16(x - sum of the previous parts); or a single FP64 plane (nparts = 1).
+// part i = rn(x - sum of the previous parts); or a single FP64 plane (nparts = 1).
+// fmt 0: bf16 parts of x. fmt 1 (two-part only): fp16 parts of x 2^e, e = f16_scale_exponent of
+// amax_mult * (*amax), where *amax holds the bits of max |x| of the operand's source (a
+// non-negative float, so its bits order like its value): fp16 keeps 11 significant bits per part,
+// and the exact power-of-two scale keeps the operand inside fp16's exponent range.
 template <class T>
 struct Planes {
   T* p[3];
   int nparts;
+  int fmt = 0;
+  const unsigned* amax = nullptr;
+  float amax_mult = 1.f;
 };
 
+__device__ __forceinline__ float plane_bound(const unsigned* amax, float mult) {
+  return mult * __uint_as_float(*amax);
+}
+
 __device__ __forceinline__ void store_planes(const Planes<__nv_bfloat16>& o, long long i, float x) {
+  if (o.fmt) {
+    // fp16 hi + lo of the scaled value, stored as raw 16-bit patterns in the plane arrays
+    const float xs = x * pow2f(f16_scale_exponent(plane_bound(o.amax, o.amax_mult)));
+    const __half hi = __float2half_rn(xs);
+    const __half lo = __float2half_rn(xs - __half2float(hi));
+    o.p[0][i] = __ushort_as_bfloat16(__half_as_ushort(hi));
+    if (o.nparts > 1) o.p[1][i] = __ushort_as_bfloat16(__half_as_ushort(lo));
+    return;
+  }
   float r = x;
   for (int k = 0; k < o.nparts; ++k) {
     const __nv_bfloat16 v = __float2bfloat16_rn(r);

@@ -58,10 +58,12 @@ struct Cfg {
   static constexpr size_t SMEM = 1024 + STAGES * STAGE_BYTES + 256;
 };
 
-// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
-// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                           ((uint32_t)(TC_BM >> 4) << 24);
+// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A and B format (bits 7-9, 10-12:
+// 1 = BF16, 0 = F16; A and B always of the same type), both K-major, N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                                ((uint32_t)(TC_BM >> 4) << 24);
+constexpr uint32_t IDESC_F16 = (1u << 4) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 
 struct TmapSet {
   CUtensorMap a[3];
@@ -98,6 +100,18 @@ struct TcParams {
   unsigned long long timeout_ns;
   int vec4;
   const GemmBlocks* blk;  // null: one dense product over M x N x K
+  uint32_t idesc;         // IDESC_BF16 or IDESC_F16 (both operands in the same format)
+  // fp16 operands carry power-of-two scales 2^eA, 2^eB (see Planes): the epilogue multiplies by
+  // 2^-(eA + eB). Null amax: no scaling.
+  const unsigned* amaxA;
+  const unsigned* amaxB;
+  float multA, multB;
+  // batched launch: `batch` independent products of the same shape; instance i reads the operand
+  // planes at z = i of the 3D tensor maps, writes C + i c_inst, takes the descriptor blk[i] and the
+  // scale bounds amax + i amax_inst
+  int batch;
+  long long c_inst;
+  int amax_inst;
 };
 
 // One output block of the product as the kernel sees it (clamped to the operand extents).
@@ -105,21 +119,22 @@ struct Blk {
   int m0, mc, n0, nc, k0, num_m, num_n, num_kb, tiles;
 };
 
-// The (at most two) blocks of this launch: from the device descriptor of a block-sparse
-// product, or the single dense block. Thread 0 fills shared memory before the CTA's first barrier.
+// The (at most two) blocks of instance `inst`: from its device descriptor of a block-sparse
+// product (clamped to the operand extents), or the single dense block.
 template <int BK>
-__device__ __forceinline__ int load_blocks(const TcParams& p, Blk* b) {
+__device__ __forceinline__ int load_blocks(const TcParams& p, int inst, Blk* b) {
   int nb = 1;
   if (p.blk) {
-    nb = min(max(p.blk->nb, 0), 2);
+    const GemmBlocks* g = p.blk + inst;
+    nb = min(max(g->nb, 0), 2);
     for (int i = 0; i < nb; ++i) {
-      const long long m0 = max(p.blk->m0[i], 0), n0 = max(p.blk->n0[i], 0), k0 = max(p.blk->k0[i], 0);
+      const long long m0 = max(g->m0[i], 0), n0 = max(g->n0[i], 0), k0 = max(g->k0[i], 0);
       b[i].m0 = (int)min(m0, p.M);
       b[i].n0 = (int)min(n0, p.N);
       b[i].k0 = (int)min(k0, p.K);
-      b[i].mc = (int)min((long long)max(p.blk->mc[i], 0), p.M - b[i].m0);
-      b[i].nc = (int)min((long long)max(p.blk->nc[i], 0), p.N - b[i].n0);
-      const int kc = (int)min((long long)max(p.blk->kc[i], 0), p.K - b[i].k0);
+      b[i].mc = (int)min((long long)max(g->mc[i], 0), p.M - b[i].m0);
+      b[i].nc = (int)min((long long)max(g->nc[i], 0), p.N - b[i].n0);
+      const int kc = (int)min((long long)max(g->kc[i], 0), p.K - b[i].k0);
       b[i].num_kb = (kc + BK - 1) / BK;
     }
   } else {
@@ -180,12 +195,14 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
 __device__ __forceinline__ unsigned long long drain_ns(unsigned long long timeout_ns) {
   return timeout_ns > 1000000000ull ? timeout_ns : 1000000000ull;
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
-                                            int y) {
+// 3D tiled load: x along K (a multiple of BK: 16-byte aligned starts), y the tile's first row, z the
+// instance of a batched launch (0 otherwise)
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
+                                            int z) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -247,12 +264,37 @@ __device__ __forceinline__ void raster(int tile, int num_m, int num_n, int group
   nt = local / gsz;
 }
 
-// Tile -> (block, M-tile, N-tile): the blocks' tiles are numbered one after the other.
-__device__ __forceinline__ const Blk& tile_of(const Blk* b, int tile, int group_m, int& mt, int& nt) {
-  const int bi = tile < b[0].tiles ? 0 : 1;
-  const Blk& k = b[bi];
-  raster(bi ? tile - b[0].tiles : tile, k.num_m, k.num_n, group_m, mt, nt);
-  return k;
+// Largest number of instances one launch takes (the tile prefix lives in shared memory).
+constexpr int kMaxGemmBatch = 256;
+
+// Tile -> (instance, block, M-tile, N-tile). Instances' tiles are numbered one after the other
+// (prefix[i] = first tile of instance i, for block-sparse launches), and inside an instance the
+// blocks' tiles one after the other.
+template <int BK>
+__device__ __forceinline__ void locate(const TcParams& p, const int* prefix, int tile, int& inst, Blk& bk, int& mt,
+                                       int& nt) {
+  Blk b[2];
+  int local;
+  if (!p.blk) {
+    load_blocks<BK>(p, 0, b);
+    inst = tile / b[0].tiles;
+    local = tile - inst * b[0].tiles;
+    bk = b[0];
+  } else {
+    int lo = 0, hi = p.batch;  // prefix[lo] <= tile < prefix[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (prefix[mid] <= tile) lo = mid;
+      else hi = mid;
+    }
+    inst = lo;
+    local = tile - prefix[lo];
+    const int nb = load_blocks<BK>(p, inst, b);
+    const int bi = (nb > 1 && local >= b[0].tiles) ? 1 : 0;
+    if (bi) local -= b[0].tiles;
+    bk = b[bi];
+  }
+  raster(local, bk.num_m, bk.num_n, p.group_m, mt, nt);
 }
 
 template <int BK, int NPL, int NPASS, int FG>
@@ -281,11 +323,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tempty0 = tfull0 + 16;
   const uint32_t final_bar = tempty0 + 16;
 
-  __shared__ Blk blks[2];
+  __shared__ int s_prefix[kMaxGemmBatch + 1];
   __shared__ int s_total;
   if (threadIdx.x == 0) {
-    const int nb = load_blocks<BK>(p, blks);
-    s_total = blks[0].tiles + (nb > 1 ? blks[1].tiles : 0);
+    Blk b[2];
+    if (p.blk) {
+      // first tile of every instance (block-sparse: the descriptors differ per instance)
+      int t = 0;
+      for (int i = 0; i < p.batch; ++i) {
+        s_prefix[i] = t;
+        const int nb = load_blocks<BK>(p, i, b);
+        t += b[0].tiles + (nb > 1 ? b[1].tiles : 0);
+      }
+      s_prefix[p.batch] = t;
+      s_total = t;
+    } else {
+      load_blocks<BK>(p, 0, b);
+      s_total = b[0].tiles * p.batch;
+    }
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
@@ -322,8 +377,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       long long issued = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-        int mt, nt;
-        const Blk& bk = tile_of(blks, tile, p.group_m, mt, nt);
+        int inst, mt, nt;
+        Blk bk;
+        locate<BK>(p, s_prefix, tile, inst, bk, mt, nt);
         for (int kb = 0; kb < bk.num_kb; ++kb) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.timeout_ns)) { ok = false; break; }
           const uint32_t fb = full0 + 8 * stage;
@@ -331,8 +387,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int kx = bk.k0 + kb * TC_BK;
 #pragma unroll
           for (int pl = 0; pl < NPL; ++pl) {
-            tma_load_2d(smem_u32(a_tile(stage, pl)), &maps.a[pl], fb, kx, bk.m0 + mt * TC_BM);
-            tma_load_2d(smem_u32(b_tile(stage, pl)), &maps.b[pl], fb, kx, bk.n0 + nt * TC_BN);
+            tma_load_3d(smem_u32(a_tile(stage, pl)), &maps.a[pl], fb, kx, bk.m0 + mt * TC_BM, inst);
+            tma_load_3d(smem_u32(b_tile(stage, pl)), &maps.b[pl], fb, kx, bk.n0 + nt * TC_BN, inst);
           }
           ++issued;
           if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
@@ -354,14 +410,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t bphase = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-        int mt_, nt_;
-        const int num_kb = tile_of(blks, tile, p.group_m, mt_, nt_).num_kb;
+        int inst_, mt_, nt_;
+        Blk bk_;
+        locate<BK>(p, s_prefix, tile, inst_, bk_, mt_, nt_);
+        const int num_kb = bk_.num_kb;
         // Descriptors differ only in their start-address field (bits 0-13, address >> 4), so each
         // one is a base descriptor plus the tile's byte offset >> 4 (all offsets are multiples of
         // 16 bytes and the shared window is < 256 KB, so the field never carries over). Passes,
         // planes and the fold group are compile-time: a group's MMAs unroll into straight-line
         // issue code with constant offsets.
         const uint64_t desc_base = smem_desc<BK>(smem_u32(smem));
+        const uint32_t idesc = p.idesc;
         constexpr uint32_t B_OFF = NPL * A_TILE;
         for (int kb0 = 0; kb0 < num_kb && ok; kb0 += FG) {
           const int g = min(FG, num_kb - kb0);  // k-blocks in this fold group
@@ -389,7 +448,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint64_t db = desc_base + ((so[i] + B_OFF + (uint32_t)pass_plane_b(NPASS, ps) * B_TILE) >> 4);
 #pragma unroll
                 for (int k = 0; k < TC_BK / 16; ++k)
-                  mma_bf16(d_tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC,
+                  mma_bf16(d_tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), idesc,
                            (ps == 0 && i == 0 && k == 0) ? 0u : 1u);
               }
             }
@@ -414,12 +473,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t bphase = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-      int mt, nt;
-      const Blk& bk = tile_of(blks, tile, p.group_m, mt, nt);
+      int num_kb;
+      {
+        // only the k-block count stays live through the k loop (the accumulator holds 128
+        // registers); the tile is located again for the store
+        int inst, mt, nt;
+        Blk bk;
+        locate<BK>(p, s_prefix, tile, inst, bk, mt, nt);
+        num_kb = bk.num_kb;
+      }
       float acc[128];
 #pragma unroll
       for (int j = 0; j < 128; ++j) acc[j] = 0.f;
-      for (int kb = 0; kb < bk.num_kb; kb += FG) {
+      for (int kb = 0; kb < num_kb; kb += FG) {
         // one lane waits for the fold group's MMAs, the warp follows it
         int w = 1;
         if (lane == 0) w = mbar_wait(tfull0 + 8 * buf, bphase, abort_flag, p.timeout_ns) ? 1 : 0;
@@ -445,11 +511,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (++buf == 2) { buf = 0; bphase ^= 1; }
       }
       if (!ok) break;
+      int inst, mt, nt;
+      Blk bk;
+      locate<BK>(p, s_prefix, tile, inst, bk, mt, nt);
+      if (p.amaxA) {
+        // undo the operands' power-of-two scales (exact): the exponents the operand builders used
+        const float unscale =
+            pow2f(-(f16_scale_exponent(plane_bound(p.amaxA + (long long)inst * p.amax_inst, p.multA)) +
+                    f16_scale_exponent(plane_bound(p.amaxB + (long long)inst * p.amax_inst, p.multB))));
+#pragma unroll
+        for (int j = 0; j < 128; ++j) acc[j] *= unscale;
+      }
       const long long row = (long long)bk.m0 + (long long)mt * TC_BM + q * 32 + lane;
       const long long col0 = (long long)bk.n0 + (long long)nt * TC_BN + half * 128;
       const long long row_end = (long long)bk.m0 + bk.mc, col_end = (long long)bk.n0 + bk.nc;
       if (row < row_end && col0 < col_end) {
-        float* dst = p.C + row * p.ldc + col0;
+        float* dst = p.C + (long long)inst * p.c_inst + row * p.ldc + col0;
         if (p.vec4 && (bk.n0 & 3) == 0 && col0 + 128 <= col_end) {
 #pragma unroll
           for (int j = 0; j < 128; j += 4)
@@ -500,15 +577,18 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld,
-              int box_rows, int bk) {
+// 3D map of `batch` planes of rows x cols (row stride ld, instance stride inst elements), boxes of
+// box_rows x bk x 1.
+bool make_map(CUtensorMap* m, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld, int batch,
+              long long inst, int box_rows, int bk, bool f16) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box,
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)inst * 2};
+  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+             const_cast<__nv_bfloat16*>(ptr), dims, strides, box,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
              bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -519,13 +599,13 @@ bool make_map(CUtensorMap* m, const __nv_bfloat16* ptr, long long rows, long lon
 // so a TMA copy can never be larger than the stage slot it lands in.
 template <int BK, int NPL, int NPASS, int FG>
 int launch_variant(int grid, const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
-                   long long ldb, const TcParams& p, cudaStream_t s) {
+                   long long ldb, long long a_inst, long long b_inst, const TcParams& p, cudaStream_t s) {
   static_assert(Cfg<BK, NPL>::STAGE_BYTES == NPL * (TC_BM + TC_BN) * BK * 2, "stage holds exactly the boxes");
   TmapSet maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int i = 0; i < NPL; ++i)
-    if (!make_map(&maps.a[i], A.p[i], p.M, p.K, lda, TC_BM, BK) ||
-        !make_map(&maps.b[i], B.p[i], p.N, p.K, ldb, TC_BN, BK))
+    if (!make_map(&maps.a[i], A.p[i], p.M, p.K, lda, p.batch, a_inst, TC_BM, BK, A.fmt == 1) ||
+        !make_map(&maps.b[i], B.p[i], p.N, p.K, ldb, p.batch, b_inst, TC_BN, BK, B.fmt == 1))
       return HOTRG_EDEVICE;
   // the dynamic shared-memory limit is a per-device attribute of the kernel: set it once on each
   // device this variant launches on
@@ -566,7 +646,7 @@ int num_sms() {
 int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
                       int npass, int* status, double timeout_s, cudaStream_t s, int bk, int group_m,
-                      int fold_group, const GemmBlocks* blk) {
+                      int fold_group, const GemmBlocks* blk, const GemmBatch* bat) {
   if (bk != 32 && bk != 64) return HOTRG_EINVAL;
   if (group_m < 1 || group_m > 64 || fold_group < 1) return HOTRG_EINVAL;
   if (M < TC_BM || N < TC_BN || K < 64 || (npass != 1 && npass != 3 && npass != 4 && npass != 6))
@@ -575,11 +655,21 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
   if (nplanes == 3) bk = 32;  // three 64-wide planes do not fit two ring stages: resolved first
   if (nplanes == 1) bk = 64;  // single-plane GEMMs use 64-wide stages
   if (A.nparts < nplanes || B.nparts < nplanes) return HOTRG_EINVAL;
+  // fp16 planes: both operands (one MMA type), two planes at most, each with its scale bound
+  if (A.fmt != B.fmt || A.fmt < 0 || A.fmt > 1) return HOTRG_EINVAL;
+  if (A.fmt == 1 && (nplanes > 2 || !A.amax || !B.amax)) return HOTRG_EINVAL;
   if ((lda % 8) || (ldb % 8) || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
   if (M > 0x7fffffffLL || N > 0x7fffffffLL || K > 0x7fffffffLL) return HOTRG_EINVAL;
   auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
   for (int i = 0; i < nplanes; ++i)
     if (!al16(A.p[i]) || !al16(B.p[i])) return HOTRG_EINVAL;
+  // batched launch: instances' planes apart by at least a whole plane, 16-byte aligned
+  const int batch = bat ? bat->batch : 1;
+  const long long a_inst = bat ? bat->a_inst : M * lda, b_inst = bat ? bat->b_inst : N * ldb;
+  if (batch < 1 || batch > kMaxGemmBatch) return HOTRG_EINVAL;
+  if (batch > 1 && (a_inst < M * lda || b_inst < N * ldb || (a_inst % 8) || (b_inst % 8) ||
+                    bat->c_inst < M * ldc || bat->amax_inst < 0))
+    return HOTRG_EINVAL;
   TcParams p;
   p.M = M;
   p.N = N;
@@ -595,7 +685,15 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
   p.timeout_ns = (unsigned long long)(timeout_s * 1e9);
   p.vec4 = ((ldc % 4) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
   p.blk = blk;
-  const long long tiles = (long long)p.num_m * p.num_n;
+  p.idesc = A.fmt == 1 ? IDESC_F16 : IDESC_BF16;
+  p.amaxA = A.fmt == 1 ? A.amax : nullptr;
+  p.amaxB = A.fmt == 1 ? B.amax : nullptr;
+  p.multA = A.amax_mult;
+  p.multB = B.amax_mult;
+  p.batch = batch;
+  p.c_inst = bat ? bat->c_inst : 0;
+  p.amax_inst = bat ? bat->amax_inst : 0;
+  const long long tiles = (long long)p.num_m * p.num_n * batch;
   if (tiles > 0x7fffffffLL) return HOTRG_EINVAL;
   // with device-side blocks the tile count is known only on the device: one CTA per SM
   const int grid = blk ? num_sms() : (int)(tiles < num_sms() ? tiles : num_sms());
@@ -604,7 +702,7 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
   int rc = HOTRG_EINVAL;
 #define HOTRG_GEMM_VARIANT(BK_, NPL_, NP_, FG_)                                          \
   if (bk == BK_ && nplanes == NPL_ && npass == NP_ && fg == FG_)                        \
-    rc = launch_variant<BK_, NPL_, NP_, FG_>(grid, A, lda, B, ldb, p, s);
+    rc = launch_variant<BK_, NPL_, NP_, FG_>(grid, A, lda, B, ldb, a_inst, b_inst, p, s);
   HOTRG_GEMM_VARIANT(64, 1, 1, 1)
   HOTRG_GEMM_VARIANT(64, 1, 1, 2)
   HOTRG_GEMM_VARIANT(64, 2, 3, 1)

@@ -20,6 +20,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 using namespace hotrg;
@@ -33,7 +35,8 @@ struct hotrg_ctx {
   // shape of the last split-precision GEMM launched (what the autotuner times)
   struct LastGemm {
     long long M = 0, N = 0, K = 0, ldk = 0;
-    int npass = 0, nparts = 0;
+    int npass = 0, nparts = 0, fmt = 0;
+    float mult_b = 1.f;
   } last_gemm;
   double timeout_s = 4.0;
   int max_sweeps = 40;  // Jacobi sweep limit of the eigensolver
@@ -52,6 +55,7 @@ struct hotrg_ctx {
   long long ework_axis = 0;  // doubles of ework per axis (batch x 2 n_max^2)
   int* status = nullptr;
   int* dstep = nullptr;       // device-side step counter (steps done)
+  unsigned* amax = nullptr;   // [0] max |B source|, [1] max |A source| of the fp16 split GEMM
   // tangents d/d beta (0) and d/d h (1) of the flow: deriv_mode 1 holds the isometries fixed,
   // 2 also differentiates them through the eigendecomposition
   bool deriv = false;
@@ -105,16 +109,22 @@ struct hotrg_ctx {
 
 namespace {
 enum Phase { PH_STEP = 0, PH_ISO, PH_OPERANDS, PH_GEMM, PH_EPILOGUE, PH_NORM, PH_COUNT };
+const char* const kPhaseName[PH_COUNT] = {"hotrg step", "isometries", "operands", "squeeze gemm", "epilogue",
+                                          "norm"};
 
-// Records a start event now and an end event when it goes out of scope (timing enabled only).
+// Marks the phase as an NVTX range on the host thread that enqueues it (visible to profilers that
+// attach to NVTX; without one the calls do nothing), and with timing enabled records a start event
+// now and an end event when it goes out of scope.
 struct PhaseScope {
   hotrg_ctx* c;
   int phase;
   cudaEvent_t a = nullptr;
   PhaseScope(hotrg_ctx* ctx, int ph) : c(ctx), phase(ph) {
+    nvtxRangePushA(kPhaseName[ph]);
     if (c->timing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, c->stream);
   }
   ~PhaseScope() {
+    nvtxRangePop();
     cudaEvent_t b = nullptr;
     if (a && cudaEventCreate(&b) == cudaSuccess) {
       cudaEventRecord(b, c->stream);
@@ -210,7 +220,12 @@ int passes_for_step(int precision, int step, int fp64_steps, int x6_steps, long 
   const int pl = planes_for_step(precision, step, fp64_steps, x6_steps, P);
   if (pl == 0) return 0;
   if (pl == 3) return 6;
-  return precision == HOTRG_BF16X4 ? 4 : 3;
+  return (precision == HOTRG_BF16X4 || precision == HOTRG_FP16X4) ? 4 : 3;
+}
+
+// the two-plane split steps of the FP16 modes use fp16 planes with power-of-two operand scales
+bool f16_planes(int precision, int planes) {
+  return planes == 2 && (precision == HOTRG_FP16X3 || precision == HOTRG_FP16X4);
 }
 
 StepNeeds plan(int d, int Dcut, int precision, int fp64_steps, int x6_steps, int max_steps,
@@ -279,6 +294,7 @@ size_t carve(hotrg_ctx* c, char* base) {
   c->cval = k.take<double>(sizeof(double) * c->batch);
   c->status = k.take<int>(sizeof(int) * 32);
   c->dstep = k.take<int>(sizeof(int) * 32);
+  c->amax = k.take<unsigned>(sizeof(unsigned) * 64);
   c->norm_partial = k.take<double>(sizeof(double) * 1024);
   // Gram matrices and isometries: sized for the largest Gram this Dcut produces (n <= Dcut^2... 256)
   const int nmax = std::min(kMaxGram, std::max(16, c->Dcut * c->Dcut));
@@ -601,11 +617,22 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   if (tg.n && (!c->Tt2 || !c->dO || tg.n > 2)) return HOTRG_ESTATE;
   const int nparts = mixed ? planes : 1;
   const long long bt_plane = (long long)chi3 * P * ld, y_plane = P * ld;
-  auto blocks = [&](void* base, long long plane_elems, int blk) {
+  // fp16 planes (FP16 modes; the forward squeeze only, tangents keep bf16): each operand's scale
+  // comes from the largest entry of its source, measured on the device. |Bt| <= sqrt(D_c3) max|Tt|
+  // (each Bt entry contracts a fibre of D_c3 entries with part of a unit isometry vector); Y's
+  // entries are the source's own.
+  const bool f16 = mixed && tg.n == 0 && f16_planes(c->precision, planes);
+  const float bt_mult = c3 >= 0 ? (float)std::sqrt((double)g.D[c3]) : 1.f;
+  auto blocks = [&](void* base, long long plane_elems, int blk, int which = -1) {  // which: 0 = B, 1 = A
     Planes<Op> pl;
     pl.nparts = nparts;
     for (int k = 0; k < 3; ++k)
       pl.p[k] = static_cast<Op*>(base) + (size_t)(k < nparts ? k : 0) * plane_elems + blk * ldk;
+    if (f16 && which >= 0) {
+      pl.fmt = 1;
+      pl.amax = c->amax + which;
+      pl.amax_mult = which == 0 ? bt_mult : 1.f;
+    }
     return pl;
   };
   // tangent p: A operand block, B operand block written by its build, and the GEMM's first blocks
@@ -622,7 +649,8 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   }
   TC* Tt = static_cast<TC*>(c->Tt);
   launch_transpose<TC>(T2, Tt, P, s);
-  launch_build_bt<TC, Op>(Tt, blocks(c->Bt, bt_plane, fwd_blk), ld, g, c3, c3 >= 0 ? Ub(U, c3) : nullptr, chi3, s);
+  if (f16) launch_absmax<TC>(Tt, P, P, P, c->amax + 0, s);
+  launch_build_bt<TC, Op>(Tt, blocks(c->Bt, bt_plane, fwd_blk, 0), ld, g, c3, c3 >= 0 ? Ub(U, c3) : nullptr, chi3, s);
   for (int p = 0; p < tg.n; ++p) {
     TC* dTt = static_cast<TC*>(c->Tt2);
     launch_transpose<TC>(tg.dT[p], dTt, P, s);
@@ -643,7 +671,7 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   auto gemm = [&](int ablk, int bblk, TC* C, long long K) -> int {
     PhaseScope gemm_scope(c, PH_GEMM);
     if constexpr (mixed) {
-      const int rc = launch_gemm_split(blocks(c->Y, y_plane, ablk), ld, blocks(c->Bt, bt_plane, bblk), ld,
+      const int rc = launch_gemm_split(blocks(c->Y, y_plane, ablk, 1), ld, blocks(c->Bt, bt_plane, bblk, 0), ld,
                                        reinterpret_cast<float*>(C), ldO, P, ldO, K, npass, c->status, c->timeout_s,
                                        s, c->kblock, c->group_m, fold_group_for(c, npass));
       if (rc) return rc;
@@ -668,7 +696,8 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
     // producer: mode products on the unprimed legs of the other transverse axes
     ops_scope = new PhaseScope(c, PH_OPERANDS);
     if (no == 0) {
-      launch_build_y<double, Op>(T1, blocks(c->Y, y_plane, fwd_blk), ld, g, a, s);
+      if (f16) launch_absmax<double>(T1, P, P, P, c->amax + 1, s);
+      launch_build_y<double, Op>(T1, blocks(c->Y, y_plane, fwd_blk, 1), ld, g, a, s);
       for (int p = 0; p < tg.n; ++p) launch_build_y<double, Op>(tg.dT[p], blocks(c->Y, y_plane, dy_blk(p)), ld, g, a, s);
     } else {
       TC* X1 = static_cast<TC*>(c->X1);
@@ -686,7 +715,8 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
         launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(U, trans[1]), kcnt[1], s);
         X = X2;
       }
-      launch_build_y<TC, Op>(X, blocks(c->Y, y_plane, fwd_blk), ld, g, a, s);
+      if (f16) launch_absmax<TC>(X, P, P, P, c->amax + 1, s);
+      launch_build_y<TC, Op>(X, blocks(c->Y, y_plane, fwd_blk, 1), ld, g, a, s);
       for (int p = 0; p < tg.n; ++p) {
         const TC* dX = static_cast<TC*>(c->dX1[p]);
         if (no >= 2) {
@@ -709,6 +739,8 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
       c->last_gemm.ldk = ld;
       c->last_gemm.npass = npass;
       c->last_gemm.nparts = planes;
+      c->last_gemm.fmt = f16 ? 1 : 0;
+      c->last_gemm.mult_b = bt_mult;
     }
     // epilogue: O axes [m_0..m_{d-1}, j, n_0..n_{d-1}]
     std::vector<Ax> hist[kMaxD];  // axes of the input of each contraction of the chain
@@ -788,10 +820,18 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
     return HOTRG_ENOMEM;
   const int nparts = mixed ? planes : 1;
   const long long bt_plane = (long long)chi3 * P * ldz, y_plane = P * ldz;
-  auto pl = [&](void* base, long long plane_elems) {
+  // fp16 planes in the FP16 modes, with the scale bounds of squeeze<TC> (B: sqrt(D_c3) max|Tt|)
+  const bool f16 = mixed && f16_planes(c->precision, planes);
+  const float bt_mult = (float)std::sqrt((double)g.D[c3]);
+  auto pl = [&](void* base, long long plane_elems, int which) {  // which: 0 = B, 1 = A
     Planes<Op> q;
     q.nparts = nparts;
     for (int k = 0; k < 3; ++k) q.p[k] = static_cast<Op*>(base) + (size_t)(k < nparts ? k : 0) * plane_elems;
+    if (f16) {
+      q.fmt = 1;
+      q.amax = c->amax + which;
+      q.amax_mult = which == 0 ? bt_mult : 1.f;
+    }
     return q;
   };
   Z2Layout* L = c->z2L + inst;
@@ -805,7 +845,8 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
   cudaMemsetAsync(c->Y, 0, sizeof(Op) * nparts * y_plane, s);
   TC* Tt = static_cast<TC*>(c->Tt);
   launch_transpose<TC>(T, Tt, P, s);
-  launch_build_bt_z2<TC, Op>(Tt, pl(c->Bt, bt_plane), ldz, g, c3, Ub(c3), chi3, c->z2rank, c->z2kcol, c->z2colpos,
+  if (f16) launch_absmax<TC>(Tt, P, P, P, c->amax + 0, s);
+  launch_build_bt_z2<TC, Op>(Tt, pl(c->Bt, bt_plane, 0), ldz, g, c3, Ub(c3), chi3, c->z2rank, c->z2kcol, c->z2colpos,
                              L, s);
   delete ops_scope;
   TC* O = static_cast<TC*>(c->O);
@@ -824,7 +865,8 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
     launch_z2_chunk(L, ev_new, no, no > 0 ? trans[0] : 0, kcnt[0], no > 1 ? trans[1] : 0, kcnt[1], ldO, c->z2blk,
                     c->z2pi, c->z2flops, mixed ? npass : 1, s);
     if (no == 0) {
-      launch_build_y_z2<double, Op>(T, pl(c->Y, y_plane), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
+      if (f16) launch_absmax<double>(T, P, P, P, c->amax + 1, s);
+      launch_build_y_z2<double, Op>(T, pl(c->Y, y_plane, 1), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
     } else {
       TC* X1 = static_cast<TC*>(c->X1);
       TC* X2 = static_cast<TC*>(c->X2);
@@ -837,18 +879,19 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
         launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(trans[1]), kcnt[1], s);
         X = X2;
       }
-      launch_build_y_z2<TC, Op>(X, pl(c->Y, y_plane), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
+      if (f16) launch_absmax<TC>(X, P, P, P, c->amax + 1, s);
+      launch_build_y_z2<TC, Op>(X, pl(c->Y, y_plane, 1), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
     }
     delete ops_scope;
     {
       PhaseScope gemm_scope(c, PH_GEMM);
       if constexpr (mixed) {
-        const int rc = launch_gemm_split(pl(c->Y, y_plane), ldz, pl(c->Bt, bt_plane), ldz, O, ldO, P, ldO, ldz,
+        const int rc = launch_gemm_split(pl(c->Y, y_plane, 1), ldz, pl(c->Bt, bt_plane, 0), ldz, O, ldO, P, ldO, ldz,
                                          npass, c->status, c->timeout_s, s, c->kblock, c->group_m,
                                          fold_group_for(c, npass), c->z2blk);
         if (rc) return rc;
       } else {
-        launch_gemm_f64(pl(c->Y, y_plane).p[0], ldz, pl(c->Bt, bt_plane).p[0], ldz, O, ldO, P, ldO, ldz, s,
+        launch_gemm_f64(pl(c->Y, y_plane, 1).p[0], ldz, pl(c->Bt, bt_plane, 0).p[0], ldz, O, ldO, P, ldO, ldz, s,
                         c->z2blk);
       }
       // the blocks' flops are counted on the device (k_z2_chunk)
@@ -909,7 +952,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   hotrg_opts_default(&def);
   if (!opt) opt = &def;
   if (opt->batch < 1 || opt->max_steps < 1 || opt->max_steps > 64) return HOTRG_EINVAL;
-  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X4) return HOTRG_EINVAL;
+  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_FP16X4) return HOTRG_EINVAL;
   if (opt->derivatives < 0 || opt->derivatives > 2) return HOTRG_EINVAL;
   hotrg_ctx c;
   c.d = d;
@@ -934,7 +977,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   if (opt->max_steps < 1 || opt->max_steps > 64 || opt->fp64_steps < 0) return HOTRG_EINVAL;
   if (opt->kblock != 0 && opt->kblock != 32 && opt->kblock != 64) return HOTRG_EINVAL;
   if (opt->fold_group < 0) return HOTRG_EINVAL;
-  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_BF16X4) return HOTRG_EINVAL;
+  if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_FP16X4) return HOTRG_EINVAL;
   if (opt->derivatives < 0 || opt->derivatives > 2) return HOTRG_EINVAL;
   if (opt->max_sweeps < 0 || opt->max_sweeps > 1000) return HOTRG_EINVAL;
   std::vector<double> vb(opt->batch), vh(opt->batch);
@@ -1642,6 +1685,12 @@ int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
   if (lg.npass == 0) return HOTRG_ESTATE;  // no split-precision step has run yet
   Planes<__nv_bfloat16> Y, Bt;
   Y.nparts = Bt.nparts = lg.nparts;
+  if (lg.fmt == 1) {  // the fp16 planes and scale bounds the last step's GEMM used
+    Y.fmt = Bt.fmt = 1;
+    Y.amax = c->amax + 1;
+    Bt.amax = c->amax + 0;
+    Bt.amax_mult = lg.mult_b;
+  }
   for (int k = 0; k < 3; ++k) {
     const int kk = k < lg.nparts ? k : 0;
     Y.p[k] = static_cast<__nv_bfloat16*>(c->Y) + (size_t)kk * lg.M * lg.ldk;
@@ -1769,6 +1818,47 @@ int hotrg_gemm_split(const float* A, long long lda, const float* Bt, long long l
     p += round_up(N * ld * 2, kAlign);
   }
   cudaMemsetAsync(status, 0, sizeof(int), s);
+  launch_split_rows(A, lda, M, K, Ap, ld, s);
+  launch_split_rows(Bt, ldb, N, K, Bp, ld, s);
+  const int fg = fold_group > 0 ? fold_group : 1;
+  const int rc = launch_gemm_split(Ap, ld, Bp, ld, C, ldc, M, N, K, npass, status, 4.0, s, kblock, 16, fg);
+  if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
+}
+
+int hotrg_gemm_split_f16(const float* A, long long lda, const float* Bt, long long ldb, float* C, long long ldc,
+                         long long M, long long N, long long K, int npass, int kblock, int fold_group, void* scratch,
+                         size_t scratch_bytes, void* stream) {
+  if (fold_group < 0) return HOTRG_EINVAL;
+  if (!A || !Bt || !C || !scratch || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
+  if (kblock == 0) kblock = 64;
+  if (kblock != 32 && kblock != 64) return HOTRG_EINVAL;
+  if (npass != 1 && npass != 3 && npass != 4) return HOTRG_EINVAL;
+  if (scratch_bytes < hotrg_gemm_scratch_bytes(M, N, K) || (reinterpret_cast<uintptr_t>(scratch) % kAlign))
+    return HOTRG_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long ld = round_up(K, 64);
+  char* p = static_cast<char*>(scratch);
+  int* status = reinterpret_cast<int*>(p);
+  unsigned* amax = reinterpret_cast<unsigned*>(p + 64);  // [0] max |A|, [1] max |Bt|
+  p += kAlign;
+  const int nparts = npass == 1 ? 1 : 2;
+  Planes<__nv_bfloat16> Ap, Bp;
+  Ap.nparts = Bp.nparts = nparts;
+  Ap.fmt = Bp.fmt = 1;
+  Ap.amax = amax;
+  Bp.amax = amax + 1;
+  for (int k = 0; k < 3; ++k) {
+    Ap.p[k] = reinterpret_cast<__nv_bfloat16*>(p);
+    p += round_up(M * ld * 2, kAlign);
+  }
+  for (int k = 0; k < 3; ++k) {
+    Bp.p[k] = reinterpret_cast<__nv_bfloat16*>(p);
+    p += round_up(N * ld * 2, kAlign);
+  }
+  cudaMemsetAsync(status, 0, sizeof(int), s);
+  launch_absmax<float>(A, M, K, lda, amax, s);
+  launch_absmax<float>(Bt, N, K, ldb, amax + 1, s);
   launch_split_rows(A, lda, M, K, Ap, ld, s);
   launch_split_rows(Bt, ldb, N, K, Bp, ld, s);
   const int fg = fold_group > 0 ? fold_group : 1;

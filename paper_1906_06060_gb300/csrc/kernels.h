@@ -36,6 +36,10 @@ void launch_trace_tangent(const double* T, const double* dT, long long t_stride,
 // out[i] = Tr S_i / Tr T_i (Eqs. (energy), (spin)) for every instance.
 void launch_trace_ratio(const double* S, const double* T, long long t_stride, int batch, long long P, double* out,
                         cudaStream_t s);
+// *out = max |x| over a rows x cols array with row stride ld (upper bound as a float; the bits
+// of that non-negative float are written, after zeroing *out on the stream).
+template <class T>
+void launch_absmax(const T* x, long long rows, long long cols, long long ld, unsigned* out, cudaStream_t s);
 // dst = src / *c
 void launch_scale(const double* src, double* dst, long long n, const double* c, cudaStream_t s);
 // Tr T (Eq. (tTr)) and ln Z/N = L + 2^-n ln Tr (n = *dstep); X^(n) along `axis` (Eq. (x)).
@@ -172,10 +176,20 @@ struct GemmBlocks {
   int nb;
   int m0[2], mc[2], n0[2], nc[2], k0[2], kc[2];
 };
+// Batched launch (up to 256 instances): `batch` independent products of the same shape in one
+// persistent launch; plane k of instance i starts at A.p[k] + i a_inst (elements, multiple of 8,
+// at least M lda), likewise B (b_inst) and C (c_inst); with blk, instance i's blocks are blk[i];
+// fp16 scale bounds at A.amax + i amax_inst and B.amax + i amax_inst.
+struct GemmBatch {
+  int batch = 1;
+  long long a_inst = 0, b_inst = 0, c_inst = 0;
+  int amax_inst = 0;
+};
 int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
                       int npass, int* status, double timeout_s, cudaStream_t s, int bk = 64,
-                      int group_m = 16, int fold_group = 1, const GemmBlocks* blk = nullptr);
+                      int group_m = 16, int fold_group = 1, const GemmBlocks* blk = nullptr,
+                      const GemmBatch* bat = nullptr);
 // Largest fold group the kernel variant for (npass, bk) accepts.
 int max_fold_group(int npass, int bk);
 void launch_split_rows(const float* X, long long ldx, long long rows, long long cols,

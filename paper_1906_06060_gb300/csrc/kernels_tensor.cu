@@ -26,6 +26,27 @@ inline int grid_for(long long n, int block, int cap = 152 * 16) {
 
 constexpr int kNormBlocks = 1024;
 
+// ---------------------------------------------------------------------------- max |x|
+// Upper bound of |x| as a float (rounded up from double).
+__device__ __forceinline__ float abs_up(double x) { return __double2float_ru(fabs(x)); }
+__device__ __forceinline__ float abs_up(float x) { return fabsf(x); }
+
+// *out = max(*out, max |x|) over rows x cols entries with row stride ld, as the bits of a
+// non-negative float (their unsigned order is the order of the values). NaN entries are skipped.
+template <class T>
+__global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ x, long long rows, long long cols,
+                                                long long ld, unsigned* out) {
+  float m = 0.f;
+  const long long total = rows * cols;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / cols, c = i - r * cols;
+    m = fmaxf(m, abs_up(x[r * ld + c]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
 // ---------------------------------------------------------------------------- T^(0)
 // T[idx] = sum_s V_s prod_{legs} W[s, leg]; W[s,0] = sqrt(cosh b), W[s,1] = s sqrt(sinh b),
 // V_s = e^{b h s}; bit l of idx (from the most significant) is the index of leg l.
@@ -578,6 +599,15 @@ void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double*
                                                                             g.D[b], U, kk, nullptr, nullptr);
   count_launches(1);
 }
+
+template <class T>
+void launch_absmax(const T* x, long long rows, long long cols, long long ld, unsigned* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(unsigned), s);
+  k_absmax<T><<<grid_for(rows * cols, 256), 256, 0, s>>>(x, rows, cols, ld, out);
+  count_launches(1);
+}
+template void launch_absmax<float>(const float*, long long, long long, long long, unsigned*, cudaStream_t);
+template void launch_absmax<double>(const double*, long long, long long, long long, unsigned*, cudaStream_t);
 
 template <class Tout>
 void launch_transpose(const double* T, Tout* Tt, long long P, cudaStream_t s) {

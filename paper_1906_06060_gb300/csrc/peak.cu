@@ -2,14 +2,17 @@
 // statement (Sec. 2: O(Dcut^15) flops per step) fixes the work; how fast the FP64 squeeze can
 // run is set by the rate of the CUDA cores' double-precision FMA units, which this kernel
 // measures (independent FMA chains in every thread, enough warps to cover the FMA latency).
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace hotrg {
 namespace {
 
-constexpr int kChains = 8;    // independent FMA chains per thread
 constexpr int kUnroll = 16;   // FMAs per chain per loop iteration
 
+// kChains independent FMA chains per thread
+template <int kChains>
 __global__ void __launch_bounds__(256) k_dfma_chains(long long iters, double seed, double* sink) {
   double a[kChains];
 #pragma unroll
@@ -50,20 +53,32 @@ extern "C" int hotrg_bench_fp64_fma(long long iters, double* sink, double* tflop
     cudaGetLastError();
     return HOTRG_EDEVICE;
   }
-  k_dfma_chains<<<blocks, threads, 0, s>>>(iters, 1.0, sink);  // warm-up (clocks, code load)
-  cudaEventRecord(e0, s);
-  k_dfma_chains<<<blocks, threads, 0, s>>>(iters, 1.0, sink);
-  cudaEventRecord(e1, s);
-  count_launches(2);
-  float ms = 0.f;
-  const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  // 8, 16 and 32 chains per thread (the FMA latency must be covered); the best rate is the peak
+  double best = 0.0;
+  bool ok = true;
+  auto run = [&](auto kernel, int chains) {
+    kernel<<<blocks, threads, 0, s>>>(iters, 1.0, sink);  // warm-up (clocks, code load)
+    cudaEventRecord(e0, s);
+    kernel<<<blocks, threads, 0, s>>>(iters, 1.0, sink);
+    cudaEventRecord(e1, s);
+    count_launches(2);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f) {
+      ok = false;
+      return;
+    }
+    const double flops = 2.0 * (double)iters * kUnroll * chains * (double)blocks * threads;
+    best = std::max(best, flops / (ms * 1e-3) / 1e12);
+  };
+  run(k_dfma_chains<8>, 8);
+  if (ok) run(k_dfma_chains<16>, 16);
+  if (ok) run(k_dfma_chains<32>, 32);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!ok || ms <= 0.f) {
+  if (!ok) {
     cudaGetLastError();
     return HOTRG_EDEVICE;
   }
-  const double flops = 2.0 * (double)iters * kUnroll * kChains * (double)blocks * threads;
-  *tflops = flops / (ms * 1e-3) / 1e12;
+  *tflops = best;
   return HOTRG_OK;
 }

@@ -45,6 +45,10 @@ DERIV_CONFIGS = {
     # 4D, Dcut = 5, 8 steps: near the transition at h = 0, and with a field of 0.01
     "deriv_d4_b0.1497_h0_D5_n8": dict(d=4, beta=0.1497, h=0.0, Dcut=5, nsteps=8),
     "deriv_d4_b0.16_h0.01_D5_n8": dict(d=4, beta=0.16, h=0.01, Dcut=5, nsteps=8),
+    # the differentiation workload's point (beta = 0.1497, h = 1e-6, Dcut = 10), its first three
+    # steps (the third makes every bond 10): no cut of these steps splits a degenerate multiplet
+    # (at Dcut = 8 the second step's cut does, so its derivative does not exist there)
+    "deriv_d4_b0.1497_h1e-6_D10_n3": dict(d=4, beta=0.1497, h=1e-6, Dcut=10, nsteps=3),
 }
 
 IMPURITY_CONFIGS = {

@@ -252,6 +252,34 @@ def test_eig_mode_4d_dcut5_matches_golden(name, precision, fp64_steps, x6_steps,
             assert abs(dh - g["flow_dlnz_dh"][n]) < tol * max(1.0, abs(g["flow_dlnz_dh"][n])), n
 
 
+@pytest.mark.parametrize("mode,tol_fp64", [("fixed", 1e-9), ("eig", 1e-8)])
+@pytest.mark.parametrize("precision,fp64_steps,x6_steps,tol_split", [
+    ("fp64", 0, 0, None),
+    ("bf16x3", 2, 12, 1e-6),     # step 3 through the six-product GEMM
+    ("bf16x3", 2, 0, 1e-5),      # step 3 with three bf16 products
+])
+def test_4d_dcut10_first_steps_match_golden(mode, tol_fp64, precision, fp64_steps, x6_steps, tol_split):
+    """The differentiation workload's point (beta = 0.1497, h = 1e-6) at its Dcut = 10, through the
+    first three steps (the third makes every bond 10, P = 1600 -> 10^4; one steady step more
+    would be 2e15 flops per oracle run): d(lnZ/N)/d beta and d / d h with the isometries held
+    fixed and differentiated through the eigendecomposition, against the oracle's difference
+    quotients; the FP64 path to the quotients' accuracy, the split paths (step 3 on the tensor
+    cores) within their bounds."""
+    with open(os.path.join(GOLDEN, "deriv_d4_b0.1497_h1e-6_D10_n3.json")) as fh:
+        g = json.load(fh)
+    c = g["config"]
+    kb, kh = ("dlnz_dbeta", "dlnz_dh") if mode == "fixed" else ("flow_dlnz_dbeta", "flow_dlnz_dh")
+    tol = tol_fp64 if precision == "fp64" else tol_split
+    from paper_1906_06060_gb300 import HOTRG
+    with HOTRG(4, c["beta"], c["h"], c["Dcut"], derivatives=mode, precision=precision, fp64_steps=fp64_steps,
+               x6_steps=x6_steps, max_steps=c["nsteps"]) as f:
+        for n in range(1, c["nsteps"] + 1):
+            f.step()
+            db, dh, _ = derivs(f)
+            assert abs(db - g[kb][n]) < tol * max(1.0, abs(g[kb][n])), n
+            assert abs(dh - g[kh][n]) < tol * max(1.0, abs(g[kh][n])), n
+
+
 def test_eig_mode_graph_replay_is_bitwise():
     import torch
     from paper_1906_06060_gb300 import HOTRG

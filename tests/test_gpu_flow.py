@@ -23,6 +23,8 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 TOL_FP64 = 1e-12
 # BF16X3 path: the squeeze products carry O(2^-16) relative error before FP32 accumulation
 TOL_MIXED_TENSOR = 2e-4
+# FP16X3 path: O(2^-22) per product (fp16 planes of power-of-two scaled operands)
+TOL_F16_TENSOR = 1e-5
 
 
 def golden(name):
@@ -93,16 +95,17 @@ def test_single_step_fp64_elementwise(d, dims, a, Dcut):
 
 @pytest.mark.parametrize("d,dims,a,Dcut", [(4, (4, 4, 4, 4), 3, 8), (4, (4, 4, 4, 4), 0, 5),
                                            (2, (16, 16), 1, 16), (3, (8, 8, 5), 2, 8), (4, (5, 4, 4, 4), 1, 6)])
-def test_single_step_bf16x3_elementwise(d, dims, a, Dcut):
+@pytest.mark.parametrize("precision,tol", [("bf16x3", TOL_MIXED_TENSOR), ("fp16x3", TOL_F16_TENSOR)])
+def test_single_step_split_elementwise(d, dims, a, Dcut, precision, tol):
     """Tensor-core path (P >= 256, including P not a multiple of 64 and ragged tiles)."""
     T = random_site_tensor(dims, seed=sum(dims) + a)
     ref, _ = R.coarse_grain(T, a, Dcut)
     ref /= R.frobenius(ref)
-    with flow(d, 0.3, 0.0, Dcut, precision="bf16x3", fp64_steps=0) as f:
+    with flow(d, 0.3, 0.0, Dcut, precision=precision, fp64_steps=0) as f:
         f.set_tensor(T)
         f.step(a)
         got = f.get_tensor()
-        np.testing.assert_allclose(got, ref, rtol=0, atol=TOL_MIXED_TENSOR * np.abs(ref).max())
+        np.testing.assert_allclose(got, ref, rtol=0, atol=tol * np.abs(ref).max())
 
 
 # ------------------------------------------------------------------------- exact pins through the GPU
@@ -117,14 +120,14 @@ def test_gpu_4d_lossless_steps_match_enumeration(beta, h):
     assert abs(4 * lnz2 - E.lnz_bruteforce(beta, h, (1, 1, 2, 2))) < 1e-12
 
 
-@pytest.mark.parametrize("precision", ["fp64", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3", "bf16x6", "fp16x3"])
 def test_gpu_2d_4x4_matches_enumeration(precision):
     beta, h = 0.4407, 0.05
     with flow(2, beta, h, 16, precision=precision, fp64_steps=0) as f:
         for _ in range(4):
             f.step()
         lnz = f.free_energy()[0][0]
-    tol = {"fp64": 1e-12, "bf16x3": 1e-6, "bf16x6": 1e-9}[precision]
+    tol = {"fp64": 1e-12, "bf16x3": 1e-6, "bf16x6": 1e-9, "fp16x3": 1e-8}[precision]
     assert abs(16 * lnz - E.lnz_bruteforce(beta, h, (4, 4))) < tol * 16
 
 
@@ -191,6 +194,9 @@ def test_fp64_2d_flow_40_steps_matches_oracle_and_onsager():
     ("bf16x3", 3, 12, 1e-7),   # the mixed path: the benchmark's schedule, the benchmark spec's 1e-7
     ("bf16x6", 3, 0, 1e-7),    # six-product GEMM after the FP64 steps
     ("bf16x3", 2, 0, 3e-7),    # BF16X3 products alone from step 3: not the mixed path (see below)
+    ("fp16x3", 3, 0, 1e-7),    # fp16 planes (22-bit products) after the FP64 steps
+    ("fp16x4", 3, 0, 1e-7),
+    ("fp16x3", 2, 0, 1e-7),    # fp16 planes from step 3
 ])
 def test_split_flow_dcut5_relative_free_energy(precision, fp64_steps, x6_steps, bound):
     """Split-precision flows: |delta f / f| against the FP64 oracle after every step.

@@ -29,8 +29,9 @@ TRANS = [1, 2, 3]
 # chunks in between
 DENSE_SLICES = [(0, 0, 0), (D - 1, D - 1, D - 1), (3, 7, 5), (7, 2, D - 1)]
 # (precision, GEMM k-block, tolerance relative to the largest sampled entry): BF16X3 with
-# k-block 64 is the benchmark's steady-state step, BF16X6 with k-block 32 its six-product steps.
-VARIANTS = [("bf16x3", 64, 2e-4), ("bf16x6", 32, 2e-6)]
+# k-block 64 is the benchmark's steady-state step, BF16X6 with k-block 32 its six-product steps,
+# FP16X3 the fp16-plane product set.
+VARIANTS = [("bf16x3", 64, 2e-4), ("bf16x6", 32, 2e-6), ("fp16x3", 64, 1e-5)]
 
 
 def _isometries(T):

@@ -83,6 +83,53 @@ def test_gemm_strided_inputs_and_output():
     assert np.all(got[:, N:] == 7.0)  # nothing written beyond N
 
 
+def _f16_exponent(amax):
+    """Scale exponent the library derives from an operand's largest magnitude: the largest e with
+    amax 2^e < 2^15 (frexp convention), clamped to [-60, 60]."""
+    import math
+    if not amax > 0:
+        return 0
+    return max(-60, min(60, 15 - math.frexp(amax)[1]))
+
+
+def _bound_f16(A, Bt, K, npass):
+    """Elementwise bound of the fp16-plane GEMM. Each operand is scaled by 2^e (exact), split into
+    fp16 hi + lo (u = 2^-11; subnormal spacing 2^-24 in scaled units). Per product: dropped plane
+    products and split residuals (2u hi*hi only, 3u^2 for 3 passes, 2u^2 for 4), an absolute
+    floor of 2^-24 scaled units per operand entry (2^-24-eA in A's own units), and FP32
+    accumulation (K * 2^-24)."""
+    u = 2.0 ** -11
+    rel = {1: 2 * u, 3: 3 * u ** 2, 4: 2 * u ** 2}[npass]
+    eA = _f16_exponent(float(np.abs(A).max()))
+    eB = _f16_exponent(float(np.abs(Bt).max()))
+    absA, absB = np.abs(A), np.abs(Bt)
+    floor = (2.0 ** (-24 - eB) * absA.sum(axis=1)[:, None] + 2.0 ** (-24 - eA) * absB.sum(axis=1)[None, :])
+    return (rel + K * 2.0 ** -24) * (absA @ absB.T) + floor + 1e-30
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 700, 200), (257, 513, 129), (1000, 2560, 1000)])
+@pytest.mark.parametrize("npass", [3, 4, 1])
+@pytest.mark.parametrize("spread,scale", [(0.0, 1.0), (2.0, 1e-4), (3.0, 3e3)])
+def test_gemm_split_f16_matches_fp64(M, N, K, npass, spread, scale):
+    """fp16 planes with power-of-two operand scales (FP16X3 / FP16X4): operands spanning several
+    decades, far below 1 or above fp16's range before scaling."""
+    import torch
+    from paper_1906_06060_gb300 import gemm_split
+    A = (scale * random_matrix(M, K, seed=M + 3 * K, scale_spread=spread)).astype(np.float32)
+    Bt = random_matrix(N, K, seed=N + 5 * K, scale_spread=spread).astype(np.float32)
+    C = gemm_split(torch.from_numpy(A).cuda(), torch.from_numpy(Bt).cuda(), npass=npass, fp16=True)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy().astype(np.float64)
+    ref = A.astype(np.float64) @ Bt.astype(np.float64).T
+    err = np.abs(got - ref)
+    bound = _bound_f16(A.astype(np.float64), Bt.astype(np.float64), K, npass)
+    assert np.all(err <= bound), f"max err/bound {np.max(err / bound):.3g}"
+    if npass >= 3 and spread == 0.0:
+        # 22-bit products: far better than BF16X3's 2^-16
+        rel = np.max(err / (np.abs(A.astype(np.float64)) @ np.abs(Bt.astype(np.float64)).T))
+        assert rel < 2.0 ** -19, rel
+
+
 def test_gemm_rejects_too_small_problem():
     import torch
     from paper_1906_06060_gb300 import gemm_split, HotrgError

@@ -38,7 +38,7 @@ def run(d, beta, Dcut, nsteps, **kw):
         return np.array(lnz), f.ln_norms(), spec, f.observables()
 
 
-@pytest.mark.parametrize("precision,x6", [("bf16x3", 0), ("bf16x3", 8), ("bf16x6", 0)])
+@pytest.mark.parametrize("precision,x6", [("bf16x3", 0), ("bf16x3", 8), ("bf16x6", 0), ("fp16x3", 0)])
 def test_z2_matches_dense_path_dcut5(precision, x6):
     kw = dict(precision=precision, fp64_steps=2, x6_steps=x6)
     lz, cz, sz, oz = run(4, 0.1497, 5, 12, z2=True, **kw)
@@ -55,6 +55,16 @@ def test_z2_flow_matches_oracle_golden_dcut5():
     BF16X3 after) against the oracle at every step: the benchmark spec's 1e-7."""
     g = golden("flow_d4_b0.1497_h0_D5_n16")
     lz, _, _, _ = run(4, 0.1497, 5, 16, z2=True, precision="bf16x3", fp64_steps=3, x6_steps=12)
+    for st in g["steps"]:
+        n = st["step"]
+        assert abs(lz[n - 1] - st["lnz"]) < 1e-7 * abs(st["lnz"]), n
+
+
+@pytest.mark.parametrize("precision", ["fp16x3", "fp16x4"])
+def test_z2_fp16_flow_matches_oracle_golden_dcut5(precision):
+    """fp16 planes after the FP64 steps, block-sparse: 1e-7 against the oracle at every step."""
+    g = golden("flow_d4_b0.1497_h0_D5_n16")
+    lz, _, _, _ = run(4, 0.1497, 5, 16, z2=True, precision=precision, fp64_steps=3, x6_steps=0)
     for st in g["steps"]:
         n = st["step"]
         assert abs(lz[n - 1] - st["lnz"]) < 1e-7 * abs(st["lnz"]), n
