@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--schedules", default="bf16x3:3:12,bf16x3:3:0,bf16x6:3:0,fp16x3:3:0,fp16x4:3:0,fp16x3:2:0",
                     help="accuracy workload: precision:fp64_steps:x6_steps of each split flow")
     ap.add_argument("--instances", type=int, default=0)
+    ap.add_argument("--group", type=int, default=0,
+                    help="instances per squeeze GEMM launch (0: for a scan the largest of 64, 32, 16, 8 "
+                         "whose workspaces fit 80%% of the free device memory, else the library default)")
     ap.add_argument("--dcut", type=int, default=0)
     ap.add_argument("--beta", type=float, default=0.1497)
     ap.add_argument("--h", type=float, default=0.0)
@@ -305,6 +308,21 @@ def over_ranks(dist, ms, flops, executed, device):
     return float(mx[0]), float(sm[1]), float(sm[2])
 
 
+def squeeze_group(a, torch=None):
+    """Instances per squeeze GEMM launch: --group, or for a scan the largest of 64, 32, 16, 8 whose
+    contexts' workspaces together fit in 80 % of the free device memory."""
+    if a.group > 0 or a.workload != "scan":
+        return a.group
+    from paper_1906_06060_gb300 import workspace_bytes
+    free = torch.cuda.mem_get_info()[0] if torch is not None else float("inf")
+    for g in (64, 32, 16, 8):
+        need = sum(workspace_bytes(4, a.dcut, a.precision, len(b), a.fp64_steps, x6_steps=a.x6_steps, z2=z2,
+                                   group=g) for b, _, z2 in groups(a))
+        if need <= 0.8 * free:
+            return g
+    return 1
+
+
 def run_ours(a, rank, world, dist):
     import torch
     from paper_1906_06060_gb300 import HOTRG
@@ -319,6 +337,7 @@ def run_ours(a, rank, world, dist):
 
     if a.workload == "deriv":
         kw["derivatives"] = "eig"
+    kw["group"] = squeeze_group(a, torch)
     # one context per group (a scan's h = 0 instances run block-sparse in a context of their own);
     # all contexts step on the same stream, one after the other
     flows = [HOTRG(4, b, h, a.dcut, z2=z2, **kw) for b, h, z2 in groups(a)]
@@ -390,6 +409,7 @@ def run_ours(a, rank, world, dist):
            "executed_flops_fraction": exec_all / flops_all if flops_all else None,
            "phases_ms_per_step": {k[3:]: v / a.steps for k, v in t.items() if k.startswith("ms_")},
            "gpu_launches": int(t["kernel_launches"]), "lnz_per_site_after": lnz, **extra}
+    out["config"]["squeeze_group"] = kw["group"] or "library default (up to 8)"
     out["clocks"] = clk.summary()
     return out
 
@@ -400,9 +420,10 @@ ACCURACY_PROFILE = os.path.join(ROOT, "profiles", "accuracy_fp64_vs_split_dcut10
 ORACLE_GOLDEN_D10 = os.path.join(ROOT, "tests", "golden", "flow_d4_b0.1497_h0_D10_n4.json")
 
 
-def stored_fp64_reference(path=ACCURACY_PROFILE):
+def stored_fp64_reference(path=None):
     """Per-step ln Z/N of the FP64 GPU flow recorded in the committed accuracy summary
     ("- fp64_lnz_step_<n> = <value>" lines), or {} if there is none."""
+    path = path or ACCURACY_PROFILE
     out = {}
     try:
         with open(path) as fh:
@@ -416,8 +437,9 @@ def stored_fp64_reference(path=ACCURACY_PROFILE):
     return out
 
 
-def oracle_golden_lnz(path=ORACLE_GOLDEN_D10):
+def oracle_golden_lnz(path=None):
     """Per-step ln Z/N of the FP64 oracle's Dcut = 10 flow (tests/golden, written by the oracle)."""
+    path = path or ORACLE_GOLDEN_D10
     try:
         with open(path) as fh:
             g = json.load(fh)

@@ -106,6 +106,10 @@ typedef struct hotrg_opts {
   double wait_timeout_s;  /* bound on any device-side spin wait, seconds (default 4) */
   int max_sweeps;         /* Jacobi sweep limit of the eigensolver (default 40; 0 = default, at most
                              1000); a Gram matrix not diagonalised within it sets HOTRG_ENOCONV */
+  int group;              /* instances squeezed together: the squeeze GEMM of a chunk is one persistent
+                             launch over a group (its tile list spans the group's instances), and the
+                             workspace holds that many copies of the per-step buffers. 1..256, capped
+                             at batch; 0 (default) = 8; with derivatives or impurities always 1 */
 } hotrg_opts;
 
 typedef struct hotrg_obs {
@@ -302,6 +306,16 @@ int hotrg_gemm_split_noalloc(const float *A, long long lda, const float *Bt, lon
 int hotrg_gemm_split_f16(const float *A, long long lda, const float *Bt, long long ldb, float *C,
                          long long ldc, long long M, long long N, long long K, int npass, int kblock,
                          int fold_group, void *scratch, size_t scratch_bytes, void *stream);
+
+/* Failure-detection probe of the bounded device-side waits (the paper has no counterpart): one
+ * launch of the tensor-core GEMM (one 128 x 256 tile, BF16X3) whose copy-issuing thread issues no
+ * copies, so that the first wait for operand data can never be satisfied. The wait gives up after
+ * timeout_s (0 < timeout_s <= 10), the kernel records the timeout, frees its tensor memory and
+ * returns; nothing is left in flight. `scratch` (device, 256-B aligned) holds at least
+ * hotrg_gemm_wait_probe_bytes() bytes. Synchronises `stream` and returns the launch's status:
+ * HOTRG_ETIMEOUT when the waits work as intended. Other errors: EINVAL, EDEVICE. */
+size_t hotrg_gemm_wait_probe_bytes(void);
+int hotrg_gemm_wait_probe(double timeout_s, void *scratch, size_t scratch_bytes, void *stream);
 
 /* Status of the last hotrg_gemm_split or hotrg_gemm_split_f16 call that used `scratch` (0 = ok,
  * HOTRG_ETIMEOUT if a pipeline wait of the GEMM kernel gave up). The word lives in the first bytes

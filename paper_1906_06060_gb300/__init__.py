@@ -36,7 +36,7 @@ def _torch():
 
 
 def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0, kblock=0,
-          graphs=True, fold_group=0, derivatives=False, impurities=False, z2=False, max_sweeps=0):
+          graphs=True, fold_group=0, derivatives=False, impurities=False, z2=False, max_sweeps=0, group=0):
     lib = _lib.load()
     o = _lib.Opts()
     lib.hotrg_opts_default(byref(o))
@@ -53,14 +53,15 @@ def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=
     o.max_steps = int(max_steps)
     o.wait_timeout_s = float(wait_timeout_s)
     o.max_sweeps = int(max_sweeps)
+    o.group = int(group)
     return o
 
 
 def workspace_bytes(d: int, Dcut: int, precision="fp64", batch: int = 1, fp64_steps: int = 2,
                     max_steps: int = 64, x6_steps: int = 0, derivatives=False, impurities=False,
-                    z2=False) -> int:
+                    z2=False, group: int = 0) -> int:
     o = _opts(precision, batch, fp64_steps, max_steps, x6_steps=x6_steps, derivatives=derivatives,
-              impurities=impurities, z2=z2)
+              impurities=impurities, z2=z2, group=group)
     n = c_size_t(0)
     check(_lib.load().hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
     return int(n.value)
@@ -79,12 +80,14 @@ class HOTRG:
     estimates <s_i s_j> (nn_correlation) and <s_i> (spin).
     z2: zero-field block-sparse squeeze (h = 0 only; see include/hotrg.h).
     max_sweeps: Jacobi sweep limit of the eigensolver (0: the default, 40).
+    group: instances squeezed together, one GEMM launch per chunk for each group (0: up to 8; the
+    workspace holds that many copies of the per-step buffers).
     """
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
                  max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0,
                  kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives=False,
-                 impurities: bool = False, z2: bool = False, max_sweeps: int = 0):
+                 impurities: bool = False, z2: bool = False, max_sweeps: int = 0, group: int = 0):
         torch = _torch()
         lib = _lib.load()
         betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))
@@ -100,7 +103,7 @@ class HOTRG:
         self.beta = betas
         self.h = hs
         o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps, kblock, graphs, fold_group,
-                  derivatives, impurities, z2, max_sweeps)
+                  derivatives, impurities, z2, max_sweeps, group)
         n = c_size_t(0)
         check(lib.hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -19,7 +19,7 @@ class Opts(ctypes.Structure):
                 ("workspace", c_void_p), ("workspace_bytes", c_size_t), ("max_steps", c_int),
                 ("kblock", c_int), ("fold_group", c_int), ("derivatives", c_int), ("impurities", c_int),
                 ("z2", c_int), ("graphs", c_int),
-                ("wait_timeout_s", c_double), ("max_sweeps", c_int)]
+                ("wait_timeout_s", c_double), ("max_sweeps", c_int), ("group", c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -69,6 +69,8 @@ _SIGS = {
                                      c_longlong, c_longlong, c_longlong, c_int, c_int, c_int, c_void_p, c_size_t,
                                      c_void_p]),
     "hotrg_gemm_status": (c_int, [c_void_p, c_void_p]),
+    "hotrg_gemm_wait_probe_bytes": (c_size_t, []),
+    "hotrg_gemm_wait_probe": (c_int, [c_double, c_void_p, c_size_t, c_void_p]),
     "hotrg_gemm_split_noalloc": (c_int, [c_void_p, c_longlong, c_void_p, c_longlong, c_void_p, c_longlong,
                                          c_longlong, c_longlong, c_longlong, c_int, c_void_p]),
     "hotrg_bench_fp64_fma": (c_int, [c_longlong, c_void_p, POINTER(c_double), c_void_p]),

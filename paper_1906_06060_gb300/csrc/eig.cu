@@ -18,6 +18,10 @@ namespace {
 
 constexpr int kEigThreads = 512;
 
+// Sort key of an eigenvalue: NaN (a Gram matrix of a tensor holding NaN) orders below every number,
+// so that the ranks computed from it always form a permutation of 0..n-1 (ties by index).
+__device__ __forceinline__ double order_key(double x) { return isnan(x) ? -INFINITY : x; }
+
 __device__ void sm_red_sum(double* sred, double v, int tid) {
   sred[tid] = v;
   __syncthreads();
@@ -132,14 +136,17 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(EigAxes ea, int* status,
   }
   // eigenvalues and ranks (descending, stable in the index)
   double* lam = sred;  // reuse: n <= 256 <= kEigThreads
-  for (int i = tid; i < n; i += kEigThreads) lam[i] = A[(long long)i * n + i];
+  for (int i = tid; i < n; i += kEigThreads) {
+    lam[i] = A[(long long)i * n + i];
+    if (isnan(lam[i])) atomic_status(status, ST_NUMERIC);
+  }
   __syncthreads();
   int* perm = sp;      // reuse 256 ints (sp and sq are contiguous)
   for (int i = tid; i < n; i += kEigThreads) {
-    const double li = lam[i];
+    const double li = order_key(lam[i]);
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const double lj = lam[j];
+      const double lj = order_key(lam[j]);
       rank += (lj > li) || (lj == li && j < i);
     }
     perm[rank] = i;
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(EigAxes ea, int* status,
   for (int k = warp; k < chi; k += kEigThreads / 32) {
     const int col = perm[k];
     double best = -1.0;
-    int bidx = n;
+    int bidx = 0;  // stays a valid row when every entry is NaN (no comparison succeeds)
     for (int r = lane; r < n; r += 32) {
       const double a = fabs(V[(long long)r * n + col]);
       if (a > best) { best = a; bidx = r; }
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(EigAxes ea, int* status,
   for (int k = warp; k < chi; k += kEigThreads / 32) {
     const int col = perm[k];
     double best = -1.0;
-    int bidx = n;
+    int bidx = 0;  // stays a valid row when every entry is NaN (no comparison succeeds)
     for (int r = lane; r < n; r += 32) {
       const double a = fabs(V[(long long)r * n + col]);
       if (a > best) { best = a; bidx = r; }
@@ -233,10 +240,10 @@ __global__ void __launch_bounds__(256) k_eig_tangent(const double* __restrict__ 
   __syncthreads();
   // the same descending, index-stable order as launch_eig
   for (int i = tid; i < n; i += blockDim.x) {
-    const double li = lam[i];
+    const double li = order_key(lam[i]);
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const double lj = lam[j];
+      const double lj = order_key(lam[j]);
       rank += (lj > li) || (lj == li && j < i);
     }
     perm[rank] = i;

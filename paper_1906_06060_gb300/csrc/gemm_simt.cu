@@ -11,16 +11,25 @@ constexpr int BM = 64, BN = 64, BK = 16;
 
 // With blk (block-sparse product), blockIdx.z picks the block: its rows [m0, m0+mc), columns
 // [n0, n0+nc) and k range [k0, k0+kc); CTAs whose tile lies outside the block return at once.
+// Batched launch: blockIdx.z / nbz is the instance (operands and output at its strides, its own
+// blocks blk[instance]), blockIdx.z % nbz the block (nbz = 2 with blocks, else 1).
 __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, long long lda,
                                                   const double* __restrict__ Bt, long long ldb,
                                                   double* __restrict__ C, long long ldc, long long M,
-                                                  long long N, long long K, const GemmBlocks* __restrict__ blk) {
+                                                  long long N, long long K, const GemmBlocks* __restrict__ blk,
+                                                  long long a_inst, long long b_inst, long long c_inst) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
+  const int nbz = blk ? 2 : 1;
+  const int inst = blockIdx.z / nbz;
+  A += inst * a_inst;
+  Bt += inst * b_inst;
+  C += inst * c_inst;
+  if (blk) blk += inst;
   long long mb = 0, nb = 0, kb = 0;
   if (blk) {
-    const int b = blockIdx.z;
+    const int b = blockIdx.z % nbz;
     if (b >= blk->nb) return;
     mb = min((long long)max(blk->m0[b], 0), M);
     nb = min((long long)max(blk->n0[b], 0), N);
@@ -80,10 +89,14 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A, 
 }  // namespace
 
 void launch_gemm_f64(const double* A, long long lda, const double* Bt, long long ldb, double* C,
-                     long long ldc, long long M, long long N, long long K, cudaStream_t s, const GemmBlocks* blk) {
-  // block-sparse: enough tiles for a block as large as the whole product, two blocks
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), blk ? 2 : 1);
-  k_gemm_f64<<<grid, 256, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, blk);
+                     long long ldc, long long M, long long N, long long K, cudaStream_t s, const GemmBlocks* blk,
+                     const GemmBatch* bat) {
+  // block-sparse: enough tiles for a block as large as the whole product, two blocks; batched:
+  // that for every instance
+  const int batch = bat ? bat->batch : 1;
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)(batch * (blk ? 2 : 1)));
+  k_gemm_f64<<<grid, 256, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, blk, bat ? bat->a_inst : 0,
+                                  bat ? bat->b_inst : 0, bat ? bat->c_inst : 0);
   count_launches(1);
 }
 

@@ -8,6 +8,15 @@
 // passes), accumulating in FP32 in tensor memory. Per product the dropped terms and split
 // residuals are O(2^-16) relative for 3 passes, O(2^-17) unbiased for 4 and O(2^-24) for 6. The
 // dropped lo*lo of 3 passes is systematic when A and B are built from the same tensor.
+// fp16 planes (two of them, 3 or 4 passes): each operand is scaled by an exact power of two 2^e
+// that brings its largest entry just below 2^15, then split into fp16 hi + lo (11 significant
+// bits each, O(2^-22) per product); the epilogue multiplies by 2^-(eA + eB). Same MMA cost as
+// bf16 (kind::f16 takes either type; A and B always share one).
+//
+// Batched launches: a persistent launch can cover several independent products of one shape (a
+// group of instances of a temperature scan): the tile list runs over the instances one after the
+// other, the operand planes are 3D tensor maps whose third coordinate is the instance, and each
+// instance has its own output, block descriptor and fp16 scale bounds.
 //
 // Accumulation: the tensor core's FP32 accumulate rounds toward zero, so a long chain of MMAs
 // into one TMEM accumulator drifts systematically towards zero by about (chain length) x 2^-25
@@ -112,6 +121,9 @@ struct TcParams {
   int batch;
   long long c_inst;
   int amax_inst;
+  // wait probe: the producer issues no copies, so the first wait for a stage can never be satisfied
+  // and must run out (nothing is in flight to drain)
+  int stall;
 };
 
 // One output block of the product as the kernel sees it (clamped to the operand extents).
@@ -264,9 +276,6 @@ __device__ __forceinline__ void raster(int tile, int num_m, int num_n, int group
   nt = local / gsz;
 }
 
-// Largest number of instances one launch takes (the tile prefix lives in shared memory).
-constexpr int kMaxGemmBatch = 256;
-
 // Tile -> (instance, block, M-tile, N-tile). Instances' tiles are numbered one after the other
 // (prefix[i] = first tile of instance i, for block-sparse launches), and inside an instance the
 // blocks' tiles one after the other.
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       long long issued = 0;
-      bool ok = true;
+      bool ok = !p.stall;
       for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
         int inst, mt, nt;
         Blk bk;
@@ -646,7 +655,7 @@ int num_sms() {
 int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
                       int npass, int* status, double timeout_s, cudaStream_t s, int bk, int group_m,
-                      int fold_group, const GemmBlocks* blk, const GemmBatch* bat) {
+                      int fold_group, const GemmBlocks* blk, const GemmBatch* bat, bool stall) {
   if (bk != 32 && bk != 64) return HOTRG_EINVAL;
   if (group_m < 1 || group_m > 64 || fold_group < 1) return HOTRG_EINVAL;
   if (M < TC_BM || N < TC_BN || K < 64 || (npass != 1 && npass != 3 && npass != 4 && npass != 6))
@@ -693,6 +702,7 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
   p.batch = batch;
   p.c_inst = bat ? bat->c_inst : 0;
   p.amax_inst = bat ? bat->amax_inst : 0;
+  p.stall = stall ? 1 : 0;
   const long long tiles = (long long)p.num_m * p.num_n * batch;
   if (tiles > 0x7fffffffLL) return HOTRG_EINVAL;
   // with device-side blocks the tile count is known only on the device: one CTA per SM

@@ -90,6 +90,10 @@ struct hotrg_ctx {
   void *Tt = nullptr, *Bt = nullptr, *X1 = nullptr, *X2 = nullptr, *Y = nullptr, *O = nullptr;
   void *R1 = nullptr, *R2 = nullptr;
   size_t sz_Tt = 0, sz_Bt = 0, sz_X = 0, sz_Y = 0, sz_O = 0, sz_R1 = 0, sz_R2 = 0;
+  // instances squeezed together (one GEMM launch per chunk for all of them): every per-step buffer
+  // holds `group` slots, st_* bytes apart
+  int group = 1;
+  size_t st_Tt = 0, st_Bt = 0, st_X = 0, st_Y = 0, st_O = 0, st_R1 = 0, st_R2 = 0, st_Tnext = 0;
   long long spec_stride = 0;  // doubles per instance in spec_log
   // phase timing (hotrg_timing_start/stop): CUDA events recorded on `stream`
   struct Ev {
@@ -137,6 +141,8 @@ struct PhaseScope {
 namespace {
 
 constexpr long long kAlign = 256;
+// shape of the wait probe's GEMM launch: one output tile, one k-block
+constexpr long long TC_PROBE_M = 128, TC_PROBE_N = 256, TC_PROBE_K = 64;
 constexpr int kSpecCap = kMaxGram;  // eigenvalues stored per (step, axis)
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -205,6 +211,14 @@ int planes_for_step(int precision, int step, int fp64_steps, int x6_steps, long 
   if (precision == HOTRG_FP64 || P < 256 || step <= fp64_steps) return 0;
   if (precision == HOTRG_BF16X6 || step <= x6_steps) return 3;
   return 2;
+}
+
+// Instances squeezed together (opts.group; 0: up to 8, whose per-step buffers are 8 copies), one
+// with tangents or impurities (those squeezes run instance by instance).
+int group_for(const hotrg_opts* o) {
+  if (o->derivatives || o->impurities) return 1;
+  const int g = o->group > 0 ? o->group : 8;
+  return std::max(1, std::min(std::min(g, o->batch), kMaxGemmBatch));
 }
 
 // k-blocks per accumulator fold: one unless the caller chose otherwise, within what the kernel
@@ -282,8 +296,10 @@ size_t carve(hotrg_ctx* c, char* base) {
   const long long P2 = Pmax * Pmax;
   const int nr_max = kMaxGram;
   Carver k{base};
+  const int G = c->group;
   c->T = k.take<double>(sizeof(double) * P2 * c->batch);
-  c->Tnext = k.take<double>(sizeof(double) * P2);
+  c->st_Tnext = (size_t)round_up((long long)(sizeof(double) * P2), kAlign);
+  c->Tnext = k.take<double>(c->st_Tnext * G);
   c->dbeta = k.take<double>(sizeof(double) * c->batch);
   c->dh = k.take<double>(sizeof(double) * c->batch);
   c->L = k.take<double>(sizeof(double) * c->batch);
@@ -294,7 +310,7 @@ size_t carve(hotrg_ctx* c, char* base) {
   c->cval = k.take<double>(sizeof(double) * c->batch);
   c->status = k.take<int>(sizeof(int) * 32);
   c->dstep = k.take<int>(sizeof(int) * 32);
-  c->amax = k.take<unsigned>(sizeof(unsigned) * 64);
+  c->amax = k.take<unsigned>(sizeof(unsigned) * 2 * G);
   c->norm_partial = k.take<double>(sizeof(double) * 1024);
   // Gram matrices and isometries: sized for the largest Gram this Dcut produces (n <= Dcut^2... 256)
   const int nmax = std::min(kMaxGram, std::max(16, c->Dcut * c->Dcut));
@@ -329,11 +345,11 @@ size_t carve(hotrg_ctx* c, char* base) {
     c->z2ev = k.take<int>(sizeof(int) * kMaxD * c->batch);
     c->z2ev_new = k.take<int>(sizeof(int) * kMaxD * c->batch);
     c->z2L = k.take<Z2Layout>(sizeof(Z2Layout) * c->batch);
-    c->z2rank = k.take<int>(sizeof(int) * Pmax);
-    c->z2kcol = k.take<int>(sizeof(int) * Pmax);
-    c->z2colpos = k.take<int>(sizeof(int) * Pmax * kMaxBond);
-    c->z2blk = k.take<GemmBlocks>(sizeof(GemmBlocks));
-    c->z2pi = k.take<int>(sizeof(int) * 32);
+    c->z2rank = k.take<int>(sizeof(int) * Pmax * G);
+    c->z2kcol = k.take<int>(sizeof(int) * Pmax * G);
+    c->z2colpos = k.take<int>(sizeof(int) * Pmax * kMaxBond * G);
+    c->z2blk = k.take<GemmBlocks>(sizeof(GemmBlocks) * G);  // contiguous: the batched GEMM reads blk[j]
+    c->z2pi = k.take<int>(sizeof(int) * G);
     c->z2flops = k.take<double>(sizeof(double) * 4);
   }
   if (c->impure) {
@@ -343,13 +359,21 @@ size_t carve(hotrg_ctx* c, char* base) {
   }
   // with tangents the operands hold three column blocks per row (see squeeze)
   const size_t blk = c->deriv ? 3 : 1;
-  c->sz_Tt = n.Tt; c->Tt = k.take<char>(n.Tt);
-  c->sz_Bt = n.Bt * blk; c->Bt = k.take<char>(n.Bt * blk);
-  c->sz_X = n.X;   c->X1 = k.take<char>(n.X); c->X2 = k.take<char>(n.X);
-  c->sz_Y = n.Y * blk; c->Y = k.take<char>(n.Y * blk);
-  c->sz_O = n.O;   c->O = k.take<char>(n.O);
-  c->sz_R1 = n.R1; c->R1 = k.take<char>(n.R1 ? n.R1 : 256);
-  c->sz_R2 = n.R2; c->R2 = k.take<char>(n.R2 ? n.R2 : 256);
+  // per-step buffers: `group` slots of each (slot strides 256-byte aligned: TMA plane starts)
+  auto slots = [&](size_t bytes, size_t& sz, size_t& st) {
+    sz = bytes;
+    st = (size_t)round_up((long long)(bytes ? bytes : 256), kAlign);
+    return k.take<char>(st * G);
+  };
+  size_t st_x2 = 0;
+  c->Tt = slots(n.Tt, c->sz_Tt, c->st_Tt);
+  c->Bt = slots(n.Bt * blk, c->sz_Bt, c->st_Bt);
+  c->X1 = slots(n.X, c->sz_X, c->st_X);
+  c->X2 = slots(n.X, c->sz_X, st_x2);
+  c->Y = slots(n.Y * blk, c->sz_Y, c->st_Y);
+  c->O = slots(n.O, c->sz_O, c->st_O);
+  c->R1 = slots(n.R1, c->sz_R1, c->st_R1);
+  c->R2 = slots(n.R2, c->sz_R2, c->st_R2);
   if (c->deriv) {
     c->Tt2 = k.take<char>(n.Tt);
     c->dX1[0] = k.take<char>(n.X);
@@ -584,10 +608,63 @@ struct Tangents {
   const double* dU[2] = {nullptr, nullptr};
 };
 
+// Per-step scratch of one instance of a squeeze group: slot j of every per-step buffer (the plan
+// holds opts.group slots of each).
+struct Slot {
+  void *Tt, *Bt, *X1, *X2, *Y, *O, *R1, *R2;
+  double* Tnext;
+  unsigned* amax;  // [0] bound of the B operand's source, [1] of the A operand's (fp16 planes)
+  int *z2rank, *z2kcol, *z2colpos, *z2pi;
+  GemmBlocks* z2blk;
+};
+
+Slot slot(const hotrg_ctx* c, int j) {
+  auto at = [j](void* base, size_t stride) -> void* {
+    return base ? static_cast<void*>(static_cast<char*>(base) + stride * (size_t)j) : nullptr;
+  };
+  Slot q;
+  q.Tt = at(c->Tt, c->st_Tt);
+  q.Bt = at(c->Bt, c->st_Bt);
+  q.X1 = at(c->X1, c->st_X);
+  q.X2 = at(c->X2, c->st_X);
+  q.Y = at(c->Y, c->st_Y);
+  q.O = at(c->O, c->st_O);
+  q.R1 = at(c->R1, c->st_R1);
+  q.R2 = at(c->R2, c->st_R2);
+  q.Tnext = static_cast<double*>(at(c->Tnext, c->st_Tnext));
+  q.amax = c->amax + 2 * j;
+  q.z2rank = c->z2rank ? c->z2rank + c->Pmax * j : nullptr;
+  q.z2kcol = c->z2kcol ? c->z2kcol + c->Pmax * j : nullptr;
+  q.z2colpos = c->z2colpos ? c->z2colpos + c->Pmax * kMaxBond * j : nullptr;
+  q.z2pi = c->z2pi ? c->z2pi + j : nullptr;
+  q.z2blk = c->z2blk ? c->z2blk + j : nullptr;
+  return q;
+}
+
+// The instances squeezed together: instance j reads T1[j] (lower site, A operand) and T2[j] (upper
+// site, B operand) with isometries U[j], writes out[j] and works in per-step slot j; inst[j] is its
+// index in the context (zero-field layouts). One GEMM launch per chunk covers all of them.
+struct Group {
+  int n = 0;
+  std::vector<const double*> T1, T2, U;
+  std::vector<double*> out;
+  std::vector<int> inst;
+  void add(const double* t1, const double* t2, const double* u, double* o, int i) {
+    T1.push_back(t1);
+    T2.push_back(t2);
+    U.push_back(u);
+    out.push_back(o);
+    inst.push_back(i);
+    ++n;
+  }
+};
+
 // planes: 0 = FP64 path (TC = double), 2 / 3 = tensor-core path (TC = float) with 3 / 6 passes.
 template <class TC>
 // Coarse-grained tensor of the pair (T1 lower site, T2 upper site along a) into `out` (new
-// geometry gn): T1 feeds the A operand, T2 the B operand. With tangents (T1 = T2 = T), also
+// geometry gn) for every instance of the group: T1 feeds the A operand, T2 the B operand. The
+// small operand and epilogue kernels run instance by instance; the squeeze GEMM of a chunk is one
+// batched launch over the group. With tangents (a group of one, T1 = T2 = T), also
 //   dT' = S(dT, T) + S(T, dT) + sum over the six places of an isometry of S with dU there,
 // computed as a dual-number pass: every producer and epilogue stage propagates (x, dx), and the
 // O(D^15) contraction of a tangent is one GEMM over the concatenated k range,
@@ -595,12 +672,13 @@ template <class TC>
 // with the operand blocks laid out side by side in one row: Y' = [dY_0 | Y | dY_1] and
 // Bt' = [dBt_1 | Bt | dBt_0] (row stride 3 ldk), so that [dY_0 | Y] pairs with [Bt | dBt_0] and
 // [Y | dY_1] with [dBt_1 | Bt].
-int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const double* U, const Geom& g,
-            const Geom& gn, int a, const int* chi, const int* trans, int nt, int planes, int npass,
-            const Tangents& tg = Tangents()) {
+int squeeze(hotrg_ctx* c, const Group& G, const Geom& g, const Geom& gn, int a, const int* chi, const int* trans,
+            int nt, int planes, int npass, const Tangents& tg = Tangents()) {
   using Op = typename Ops<TC>::Op;
   constexpr bool mixed = std::is_same<TC, float>::value;
   cudaStream_t s = c->stream;
+  const int ng = G.n;
+  if (ng < 1 || ng > c->group || (tg.n && ng != 1)) return HOTRG_ESTATE;
   const long long P = g.P;
   const long long ldk = mixed ? round_up(P, 64) : P;
   const int nblk = tg.n ? 3 : 1;
@@ -623,14 +701,15 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   // entries are the source's own.
   const bool f16 = mixed && tg.n == 0 && f16_planes(c->precision, planes);
   const float bt_mult = c3 >= 0 ? (float)std::sqrt((double)g.D[c3]) : 1.f;
-  auto blocks = [&](void* base, long long plane_elems, int blk, int which = -1) {  // which: 0 = B, 1 = A
+  // which: 0 = B operand, 1 = A operand (fp16 scale bound amax[which])
+  auto blocks = [&](void* base, long long plane_elems, int blk, int which = -1, const unsigned* amax = nullptr) {
     Planes<Op> pl;
     pl.nparts = nparts;
     for (int k = 0; k < 3; ++k)
       pl.p[k] = static_cast<Op*>(base) + (size_t)(k < nparts ? k : 0) * plane_elems + blk * ldk;
     if (f16 && which >= 0) {
       pl.fmt = 1;
-      pl.amax = c->amax + which;
+      pl.amax = amax + which;
       pl.amax_mult = which == 0 ? bt_mult : 1.f;
     }
     return pl;
@@ -640,26 +719,31 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   auto dbt_blk = [](int p) { return p == 0 ? 2 : 0; };
   auto gemm_a_blk = [](int p) { return p == 0 ? 0 : 1; };
   auto gemm_b_blk = [](int p) { return p == 0 ? 1 : 0; };
-  // B operand(s)
+  const Slot S0 = slot(c, 0);
+  // B operand(s), one per instance
   PhaseScope* ops_scope = new PhaseScope(c, PH_OPERANDS);
   if (tg.n && mixed && ldk != P) {
     // the concatenated k range runs over the zero padding between blocks
-    cudaMemsetAsync(c->Bt, 0, sizeof(Op) * nparts * bt_plane, s);
-    cudaMemsetAsync(c->Y, 0, sizeof(Op) * nparts * y_plane, s);
+    cudaMemsetAsync(S0.Bt, 0, sizeof(Op) * nparts * bt_plane, s);
+    cudaMemsetAsync(S0.Y, 0, sizeof(Op) * nparts * y_plane, s);
   }
-  TC* Tt = static_cast<TC*>(c->Tt);
-  launch_transpose<TC>(T2, Tt, P, s);
-  if (f16) launch_absmax<TC>(Tt, P, P, P, c->amax + 0, s);
-  launch_build_bt<TC, Op>(Tt, blocks(c->Bt, bt_plane, fwd_blk, 0), ld, g, c3, c3 >= 0 ? Ub(U, c3) : nullptr, chi3, s);
+  for (int j = 0; j < ng; ++j) {
+    const Slot S = slot(c, j);
+    TC* Tt = static_cast<TC*>(S.Tt);
+    launch_transpose<TC>(G.T2[j], Tt, P, s);
+    if (f16) launch_absmax<TC>(Tt, P, P, P, S.amax + 0, s);
+    launch_build_bt<TC, Op>(Tt, blocks(S.Bt, bt_plane, fwd_blk, 0, S.amax), ld, g, c3,
+                            c3 >= 0 ? Ub(G.U[j], c3) : nullptr, chi3, s);
+  }
   for (int p = 0; p < tg.n; ++p) {
     TC* dTt = static_cast<TC*>(c->Tt2);
     launch_transpose<TC>(tg.dT[p], dTt, P, s);
     const bool two = tg.dU[p] && c3 >= 0;
-    launch_build_bt<TC, Op>(dTt, blocks(c->Bt, bt_plane, dbt_blk(p)), ld, g, c3, c3 >= 0 ? Ub(U, c3) : nullptr,
-                            chi3, s, two ? Tt : nullptr, two ? Ub(tg.dU[p], c3) : nullptr);
+    launch_build_bt<TC, Op>(dTt, blocks(S0.Bt, bt_plane, dbt_blk(p)), ld, g, c3, c3 >= 0 ? Ub(G.U[0], c3) : nullptr,
+                            chi3, s, two ? static_cast<TC*>(S0.Tt) : nullptr, two ? Ub(tg.dU[p], c3) : nullptr);
   }
   delete ops_scope;
-  TC* O = static_cast<TC*>(c->O);
+  TC* O = static_cast<TC*>(S0.O);
   TC* dO = static_cast<TC*>(c->dO);
   const long long ldO = (long long)chi3 * P;
   // chunks over the other transverse axes
@@ -668,21 +752,30 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   long long nchunks = 1;
   for (int i = 0; i < no; ++i) nchunks *= chi[trans[i]];
   int prev_k0 = -1;
+  // instance j's operand planes and output are slot j's: one launch for the group
+  GemmBatch bat;
+  bat.batch = ng;
+  bat.a_inst = (long long)(c->st_Y / sizeof(Op));
+  bat.b_inst = (long long)(c->st_Bt / sizeof(Op));
+  bat.c_inst = (long long)(c->st_O / sizeof(TC));
+  bat.amax_inst = 2;
+  const GemmBatch* batp = ng > 1 ? &bat : nullptr;
   auto gemm = [&](int ablk, int bblk, TC* C, long long K) -> int {
     PhaseScope gemm_scope(c, PH_GEMM);
     if constexpr (mixed) {
-      const int rc = launch_gemm_split(blocks(c->Y, y_plane, ablk, 1), ld, blocks(c->Bt, bt_plane, bblk, 0), ld,
-                                       reinterpret_cast<float*>(C), ldO, P, ldO, K, npass, c->status, c->timeout_s,
-                                       s, c->kblock, c->group_m, fold_group_for(c, npass));
+      const int rc = launch_gemm_split(blocks(S0.Y, y_plane, ablk, 1, S0.amax), ld,
+                                       blocks(S0.Bt, bt_plane, bblk, 0, S0.amax), ld, reinterpret_cast<float*>(C),
+                                       ldO, P, ldO, K, npass, c->status, c->timeout_s, s, c->kblock, c->group_m,
+                                       fold_group_for(c, npass), nullptr, batp);
       if (rc) return rc;
-      if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * K * npass;
+      if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * K * npass * ng;
     } else {
-      launch_gemm_f64(blocks(c->Y, y_plane, ablk).p[0], ld, blocks(c->Bt, bt_plane, bblk).p[0], ld, C, ldO, P, ldO,
-                      K, s);
-      if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * K;
+      launch_gemm_f64(blocks(S0.Y, y_plane, ablk).p[0], ld, blocks(S0.Bt, bt_plane, bblk).p[0], ld, C, ldO, P, ldO,
+                      K, s, nullptr, batp);
+      if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * K * ng;
     }
     if (c->timing) {
-      c->t_gemm_flops += 2.0 * P * (double)ldO * K;
+      c->t_gemm_flops += 2.0 * P * (double)ldO * K * ng;
       ++c->t_gemm_launches;
     }
     return HOTRG_OK;
@@ -695,41 +788,47 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
     }
     // producer: mode products on the unprimed legs of the other transverse axes
     ops_scope = new PhaseScope(c, PH_OPERANDS);
-    if (no == 0) {
-      if (f16) launch_absmax<double>(T1, P, P, P, c->amax + 1, s);
-      launch_build_y<double, Op>(T1, blocks(c->Y, y_plane, fwd_blk, 1), ld, g, a, s);
-      for (int p = 0; p < tg.n; ++p) launch_build_y<double, Op>(tg.dT[p], blocks(c->Y, y_plane, dy_blk(p)), ld, g, a, s);
-    } else {
-      TC* X1 = static_cast<TC*>(c->X1);
-      TC* X2 = static_cast<TC*>(c->X2);
-      const int b0 = trans[0];
-      if (kcnt[0] != prev_k0) {
-        launch_mode_unprimed<double, TC>(T1, X1, g, b0, Ub(U, b0), kcnt[0], s);
+    for (int j = 0; j < ng; ++j) {
+      const Slot S = slot(c, j);
+      const double* T1 = G.T1[j];
+      const double* U = G.U[j];
+      if (no == 0) {
+        if (f16) launch_absmax<double>(T1, P, P, P, S.amax + 1, s);
+        launch_build_y<double, Op>(T1, blocks(S.Y, y_plane, fwd_blk, 1, S.amax), ld, g, a, s);
         for (int p = 0; p < tg.n; ++p)
-          launch_mode_unprimed<double, TC>(tg.dT[p], static_cast<TC*>(c->dX1[p]), g, b0, Ub(U, b0), kcnt[0], s,
-                                           tg.dU[p] ? T1 : nullptr, tg.dU[p] ? Ub(tg.dU[p], b0) : nullptr);
-        prev_k0 = kcnt[0];
-      }
-      const TC* X = X1;
-      if (no >= 2) {
-        launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(U, trans[1]), kcnt[1], s);
-        X = X2;
-      }
-      if (f16) launch_absmax<TC>(X, P, P, P, c->amax + 1, s);
-      launch_build_y<TC, Op>(X, blocks(c->Y, y_plane, fwd_blk, 1), ld, g, a, s);
-      for (int p = 0; p < tg.n; ++p) {
-        const TC* dX = static_cast<TC*>(c->dX1[p]);
-        if (no >= 2) {
-          TC* dX2 = static_cast<TC*>(c->dX2);
-          launch_mode_unprimed<TC, TC>(dX, dX2, g, trans[1], Ub(U, trans[1]), kcnt[1], s,
-                                       tg.dU[p] ? X1 : nullptr, tg.dU[p] ? Ub(tg.dU[p], trans[1]) : nullptr);
-          dX = dX2;
+          launch_build_y<double, Op>(tg.dT[p], blocks(S.Y, y_plane, dy_blk(p)), ld, g, a, s);
+      } else {
+        TC* X1 = static_cast<TC*>(S.X1);
+        TC* X2 = static_cast<TC*>(S.X2);
+        const int b0 = trans[0];
+        if (kcnt[0] != prev_k0) {
+          launch_mode_unprimed<double, TC>(T1, X1, g, b0, Ub(U, b0), kcnt[0], s);
+          for (int p = 0; p < tg.n; ++p)
+            launch_mode_unprimed<double, TC>(tg.dT[p], static_cast<TC*>(c->dX1[p]), g, b0, Ub(U, b0), kcnt[0], s,
+                                             tg.dU[p] ? T1 : nullptr, tg.dU[p] ? Ub(tg.dU[p], b0) : nullptr);
         }
-        launch_build_y<TC, Op>(dX, blocks(c->Y, y_plane, dy_blk(p)), ld, g, a, s);
+        const TC* X = X1;
+        if (no >= 2) {
+          launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(U, trans[1]), kcnt[1], s);
+          X = X2;
+        }
+        if (f16) launch_absmax<TC>(X, P, P, P, S.amax + 1, s);
+        launch_build_y<TC, Op>(X, blocks(S.Y, y_plane, fwd_blk, 1, S.amax), ld, g, a, s);
+        for (int p = 0; p < tg.n; ++p) {
+          const TC* dX = static_cast<TC*>(c->dX1[p]);
+          if (no >= 2) {
+            TC* dX2 = static_cast<TC*>(c->dX2);
+            launch_mode_unprimed<TC, TC>(dX, dX2, g, trans[1], Ub(U, trans[1]), kcnt[1], s,
+                                         tg.dU[p] ? X1 : nullptr, tg.dU[p] ? Ub(tg.dU[p], trans[1]) : nullptr);
+            dX = dX2;
+          }
+          launch_build_y<TC, Op>(dX, blocks(S.Y, y_plane, dy_blk(p)), ld, g, a, s);
+        }
       }
     }
+    if (no > 0) prev_k0 = kcnt[0];
     delete ops_scope;
-    // the O(D^15) GEMM
+    // the O(D^15) GEMM, all instances of the group in one launch
     {
       const int rc = gemm(fwd_blk, fwd_blk, O, P);
       if (rc) return rc;
@@ -744,38 +843,43 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
     }
     // epilogue: O axes [m_0..m_{d-1}, j, n_0..n_{d-1}]
     std::vector<Ax> hist[kMaxD];  // axes of the input of each contraction of the chain
-    TC* bufs[2] = {static_cast<TC*>(c->R1), static_cast<TC*>(c->R2)};
     TC* dbufs[2] = {static_cast<TC*>(c->dR1), static_cast<TC*>(c->dR2)};
     long long out_base = 0;
     for (int i = 0; i < no; ++i) out_base += (long long)kcnt[i] * gn.Sn[trans[i]] * gn.P;
     {
       PhaseScope epi_scope(c, PH_EPILOGUE);
-      std::vector<Ax> axes;
-      for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b] * ldO, 0, b});
-      axes.push_back({chi3, P, 1, -1});
-      for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
-      const TC* cur = O;
-      for (int i = 0; i < no; ++i) {
-        hist[i] = axes;
-        contract_axes<TC, TC>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(U, trans[i]), nullptr, 0, s);
-        cur = bufs[i];
-      }
-      hist[no] = axes;
-      long long fs[kMaxAxes];
-      if (c3 >= 0) {
-        // final axes after contracting c3 (m_c3 removed, n_c3 -> k'_c3)
-        final_strides(axes, c3, c3, gn, c3, fs);
-        contract_axes<TC, double>(axes, cur, out, c3, chi3, Ub(U, c3), fs, out_base, s);
-      } else {
-        copy_final<TC>(axes, cur, out, gn, s);
+      for (int j = 0; j < ng; ++j) {
+        const Slot S = slot(c, j);
+        TC* bufs[2] = {static_cast<TC*>(S.R1), static_cast<TC*>(S.R2)};
+        std::vector<Ax> axes;
+        for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b] * ldO, 0, b});
+        axes.push_back({chi3, P, 1, -1});
+        for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
+        const TC* cur = static_cast<TC*>(S.O);
+        for (int i = 0; i < no; ++i) {
+          hist[i] = axes;
+          contract_axes<TC, TC>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(G.U[j], trans[i]), nullptr, 0, s);
+          cur = bufs[i];
+        }
+        hist[no] = axes;
+        long long fs[kMaxAxes];
+        if (c3 >= 0) {
+          // final axes after contracting c3 (m_c3 removed, n_c3 -> k'_c3)
+          final_strides(axes, c3, c3, gn, c3, fs);
+          contract_axes<TC, double>(axes, cur, G.out[j], c3, chi3, Ub(G.U[j], c3), fs, out_base, s);
+        } else {
+          copy_final<TC>(axes, cur, G.out[j], gn, s);
+        }
       }
     }
-    // tangents: dO by one GEMM over the concatenated k range, then the epilogue chain in
-    // dual numbers (dR' = C_U(dR) + C_dU(R))
+    // tangents (a group of one): dO by one GEMM over the concatenated k range, then the epilogue
+    // chain in dual numbers (dR' = C_U(dR) + C_dU(R))
     for (int p = 0; p < tg.n; ++p) {
       const int rc = gemm(gemm_a_blk(p), gemm_b_blk(p), dO, ldk + P);
       if (rc) return rc;
       PhaseScope epi_scope(c, PH_EPILOGUE);
+      const double* U = G.U[0];
+      TC* bufs[2] = {static_cast<TC*>(S0.R1), static_cast<TC*>(S0.R2)};
       const TC* cur = dO;
       const TC* curF = O;
       for (int i = 0; i < no; ++i) {
@@ -799,21 +903,24 @@ int squeeze(hotrg_ctx* c, const double* T1, const double* T2, double* out, const
   return HOTRG_OK;
 }
 
-// The zero-field squeeze of T with itself (z2.cu): parity-blocked operands, two dense GEMM
-// blocks per chunk, the first epilogue contraction reading the blocked output. TC = float: the
-// tensor-core path (bf16 planes, npass split products); TC = double: the FP64 path. Same output
-// as squeeze<TC>(c, T, T, out, ...) up to the order of summation.
+// The zero-field squeeze of T with itself (z2.cu) for every instance of the group: parity-blocked
+// operands, two dense GEMM blocks per chunk and instance (one batched launch over the group, each
+// instance with its own block descriptor), the first epilogue contraction reading the blocked
+// output. TC = float: the tensor-core path (bf16 or fp16 planes, npass split products); TC = double:
+// the FP64 path. Same output as squeeze<TC> up to the order of summation.
 template <class TC>
-int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const double* U, const Geom& g,
-               const Geom& gn, int a, const int* chi, const int* trans, int nt, int planes, int npass) {
+int squeeze_z2(hotrg_ctx* c, const Group& G, const Geom& g, const Geom& gn, int a, const int* chi, const int* trans,
+               int nt, int planes, int npass) {
   using Op = typename Ops<TC>::Op;
   constexpr bool mixed = std::is_same<TC, float>::value;
   cudaStream_t s = c->stream;
+  const int ng = G.n;
+  if (ng < 1 || ng > c->group) return HOTRG_ESTATE;
   const long long P = g.P;
   const long long ldz = round_up(P, 64) + 64;
   const int c3 = trans[nt - 1];
   const int chi3 = chi[c3];
-  auto Ub = [&](int b) { return U + (long long)b * kMaxBond * kMaxGram; };
+  auto Ub = [&](int j, int b) { return G.U[j] + (long long)b * kMaxBond * kMaxGram; };
   StepNeeds need = needs_for(c->d, g.D, a, c->Dcut, planes);
   if (need.Tt > c->sz_Tt || need.Bt > c->sz_Bt || need.X > c->sz_X || need.Y > c->sz_Y || need.O > c->sz_O ||
       need.R1 > c->sz_R1 || need.R2 > c->sz_R2 || P > c->Pmax)
@@ -823,38 +930,48 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
   // fp16 planes in the FP16 modes, with the scale bounds of squeeze<TC> (B: sqrt(D_c3) max|Tt|)
   const bool f16 = mixed && f16_planes(c->precision, planes);
   const float bt_mult = (float)std::sqrt((double)g.D[c3]);
-  auto pl = [&](void* base, long long plane_elems, int which) {  // which: 0 = B, 1 = A
+  auto pl = [&](void* base, long long plane_elems, int which, const unsigned* amax) {  // which: 0 = B, 1 = A
     Planes<Op> q;
     q.nparts = nparts;
     for (int k = 0; k < 3; ++k) q.p[k] = static_cast<Op*>(base) + (size_t)(k < nparts ? k : 0) * plane_elems;
     if (f16) {
       q.fmt = 1;
-      q.amax = c->amax + which;
+      q.amax = amax + which;
       q.amax_mult = which == 0 ? bt_mult : 1.f;
     }
     return q;
   };
-  Z2Layout* L = c->z2L + inst;
-  const int* ev_new = c->z2ev_new + inst * kMaxD;
   const long long ldO = (long long)chi3 * P;
+  const Slot S0 = slot(c, 0);
   PhaseScope* ops_scope = new PhaseScope(c, PH_OPERANDS);
-  launch_z2_layout(c->z2ev + inst * kMaxD, ev_new, 1, g, c3, chi3, L, s);
-  launch_z2_tables(L, P, chi3, c->z2rank, c->z2kcol, c->z2colpos, s);
-  // zeros between and after the k classes (the GEMM's k-blocks run over them)
-  cudaMemsetAsync(c->Bt, 0, sizeof(Op) * nparts * bt_plane, s);
-  cudaMemsetAsync(c->Y, 0, sizeof(Op) * nparts * y_plane, s);
-  TC* Tt = static_cast<TC*>(c->Tt);
-  launch_transpose<TC>(T, Tt, P, s);
-  if (f16) launch_absmax<TC>(Tt, P, P, P, c->amax + 0, s);
-  launch_build_bt_z2<TC, Op>(Tt, pl(c->Bt, bt_plane, 0), ldz, g, c3, Ub(c3), chi3, c->z2rank, c->z2kcol, c->z2colpos,
-                             L, s);
+  for (int j = 0; j < ng; ++j) {
+    const Slot S = slot(c, j);
+    const int inst = G.inst[j];
+    Z2Layout* L = c->z2L + inst;
+    launch_z2_layout(c->z2ev + inst * kMaxD, c->z2ev_new + inst * kMaxD, 1, g, c3, chi3, L, s);
+    launch_z2_tables(L, P, chi3, S.z2rank, S.z2kcol, S.z2colpos, s);
+    // zeros between and after the k classes (the GEMM's k-blocks run over them)
+    cudaMemsetAsync(S.Bt, 0, sizeof(Op) * nparts * bt_plane, s);
+    cudaMemsetAsync(S.Y, 0, sizeof(Op) * nparts * y_plane, s);
+    TC* Tt = static_cast<TC*>(S.Tt);
+    launch_transpose<TC>(G.T2[j], Tt, P, s);
+    if (f16) launch_absmax<TC>(Tt, P, P, P, S.amax + 0, s);
+    launch_build_bt_z2<TC, Op>(Tt, pl(S.Bt, bt_plane, 0, S.amax), ldz, g, c3, Ub(j, c3), chi3, S.z2rank, S.z2kcol,
+                               S.z2colpos, L, s);
+  }
   delete ops_scope;
-  TC* O = static_cast<TC*>(c->O);
   const int no = nt - 1;
   int kcnt[kMaxD] = {0, 0, 0, 0};
   long long nchunks = 1;
   for (int i = 0; i < no; ++i) nchunks *= chi[trans[i]];
   int prev_k0 = -1;
+  GemmBatch bat;
+  bat.batch = ng;
+  bat.a_inst = (long long)(c->st_Y / sizeof(Op));
+  bat.b_inst = (long long)(c->st_Bt / sizeof(Op));
+  bat.c_inst = (long long)(c->st_O / sizeof(TC));
+  bat.amax_inst = 2;
+  const GemmBatch* batp = ng > 1 ? &bat : nullptr;
   for (long long ch = 0; ch < nchunks; ++ch) {
     long long r = ch;
     for (int i = no - 1; i >= 0; --i) {
@@ -862,37 +979,41 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
       r /= chi[trans[i]];
     }
     ops_scope = new PhaseScope(c, PH_OPERANDS);
-    launch_z2_chunk(L, ev_new, no, no > 0 ? trans[0] : 0, kcnt[0], no > 1 ? trans[1] : 0, kcnt[1], ldO, c->z2blk,
-                    c->z2pi, c->z2flops, mixed ? npass : 1, s);
-    if (no == 0) {
-      if (f16) launch_absmax<double>(T, P, P, P, c->amax + 1, s);
-      launch_build_y_z2<double, Op>(T, pl(c->Y, y_plane, 1), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
-    } else {
-      TC* X1 = static_cast<TC*>(c->X1);
-      TC* X2 = static_cast<TC*>(c->X2);
-      if (kcnt[0] != prev_k0) {
-        launch_mode_unprimed<double, TC>(T, X1, g, trans[0], Ub(trans[0]), kcnt[0], s);
-        prev_k0 = kcnt[0];
+    for (int j = 0; j < ng; ++j) {
+      const Slot S = slot(c, j);
+      const int inst = G.inst[j];
+      const Z2Layout* L = c->z2L + inst;
+      launch_z2_chunk(L, c->z2ev_new + inst * kMaxD, no, no > 0 ? trans[0] : 0, kcnt[0], no > 1 ? trans[1] : 0,
+                      kcnt[1], ldO, S.z2blk, S.z2pi, c->z2flops, mixed ? npass : 1, s);
+      if (no == 0) {
+        if (f16) launch_absmax<double>(G.T1[j], P, P, P, S.amax + 1, s);
+        launch_build_y_z2<double, Op>(G.T1[j], pl(S.Y, y_plane, 1, S.amax), ldz, g, a, S.z2rank, S.z2kcol, L,
+                                      S.z2pi, s);
+      } else {
+        TC* X1 = static_cast<TC*>(S.X1);
+        TC* X2 = static_cast<TC*>(S.X2);
+        if (kcnt[0] != prev_k0) launch_mode_unprimed<double, TC>(G.T1[j], X1, g, trans[0], Ub(j, trans[0]), kcnt[0], s);
+        const TC* X = X1;
+        if (no >= 2) {
+          launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(j, trans[1]), kcnt[1], s);
+          X = X2;
+        }
+        if (f16) launch_absmax<TC>(X, P, P, P, S.amax + 1, s);
+        launch_build_y_z2<TC, Op>(X, pl(S.Y, y_plane, 1, S.amax), ldz, g, a, S.z2rank, S.z2kcol, L, S.z2pi, s);
       }
-      const TC* X = X1;
-      if (no >= 2) {
-        launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(trans[1]), kcnt[1], s);
-        X = X2;
-      }
-      if (f16) launch_absmax<TC>(X, P, P, P, c->amax + 1, s);
-      launch_build_y_z2<TC, Op>(X, pl(c->Y, y_plane, 1), ldz, g, a, c->z2rank, c->z2kcol, L, c->z2pi, s);
     }
+    if (no > 0) prev_k0 = kcnt[0];
     delete ops_scope;
     {
       PhaseScope gemm_scope(c, PH_GEMM);
       if constexpr (mixed) {
-        const int rc = launch_gemm_split(pl(c->Y, y_plane, 1), ldz, pl(c->Bt, bt_plane, 0), ldz, O, ldO, P, ldO, ldz,
-                                         npass, c->status, c->timeout_s, s, c->kblock, c->group_m,
-                                         fold_group_for(c, npass), c->z2blk);
+        const int rc = launch_gemm_split(pl(S0.Y, y_plane, 1, S0.amax), ldz, pl(S0.Bt, bt_plane, 0, S0.amax), ldz,
+                                         static_cast<float*>(S0.O), ldO, P, ldO, ldz, npass, c->status, c->timeout_s,
+                                         s, c->kblock, c->group_m, fold_group_for(c, npass), S0.z2blk, batp);
         if (rc) return rc;
       } else {
-        launch_gemm_f64(pl(c->Y, y_plane, 1).p[0], ldz, pl(c->Bt, bt_plane, 0).p[0], ldz, O, ldO, P, ldO, ldz, s,
-                        c->z2blk);
+        launch_gemm_f64(pl(S0.Y, y_plane, 1, S0.amax).p[0], ldz, pl(S0.Bt, bt_plane, 0, S0.amax).p[0], ldz,
+                        static_cast<double*>(S0.O), ldO, P, ldO, ldz, s, S0.z2blk, batp);
       }
       // the blocks' flops are counted on the device (k_z2_chunk)
       if (c->timing) {
@@ -901,28 +1022,33 @@ int squeeze_z2(hotrg_ctx* c, int inst, const double* T, double* out, const doubl
       }
     }
     PhaseScope epi_scope(c, PH_EPILOGUE);
-    std::vector<Ax> axes;
-    for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b] * ldO, 0, b});
-    axes.push_back({chi3, P, 1, -1});
-    for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
     long long out_base = 0;
     for (int i = 0; i < no; ++i) out_base += (long long)kcnt[i] * gn.Sn[trans[i]] * gn.P;
-    TC* bufs[2] = {static_cast<TC*>(c->R1), static_cast<TC*>(c->R2)};
-    long long fs[kMaxAxes];
-    if (no == 0) {
+    for (int j = 0; j < ng; ++j) {
+      const Slot S = slot(c, j);
+      const Z2Layout* L = c->z2L + G.inst[j];
+      const TC* O = static_cast<TC*>(S.O);
+      std::vector<Ax> axes;
+      for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b] * ldO, 0, b});
+      axes.push_back({chi3, P, 1, -1});
+      for (int b = 0; b < c->d; ++b) axes.push_back({g.D[b], g.Sn[b], 2, b});
+      TC* bufs[2] = {static_cast<TC*>(S.R1), static_cast<TC*>(S.R2)};
+      long long fs[kMaxAxes];
+      if (no == 0) {
+        final_strides(axes, c3, c3, gn, c3, fs);
+        contract_axes_z2<TC, double>(axes, O, ldO, G.out[j], c3, chi3, Ub(j, c3), fs, out_base, L, S.z2pi, s);
+        continue;
+      }
+      contract_axes_z2<TC, TC>(axes, O, ldO, bufs[0], trans[0], chi[trans[0]], Ub(j, trans[0]), nullptr, 0, L,
+                               S.z2pi, s);
+      const TC* cur = bufs[0];
+      for (int i = 1; i < no; ++i) {
+        contract_axes<TC, TC>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(j, trans[i]), nullptr, 0, s);
+        cur = bufs[i];
+      }
       final_strides(axes, c3, c3, gn, c3, fs);
-      contract_axes_z2<TC, double>(axes, O, ldO, out, c3, chi3, Ub(c3), fs, out_base, L, c->z2pi, s);
-      continue;
+      contract_axes<TC, double>(axes, cur, G.out[j], c3, chi3, Ub(j, c3), fs, out_base, s);
     }
-    contract_axes_z2<TC, TC>(axes, O, ldO, bufs[0], trans[0], chi[trans[0]], Ub(trans[0]), nullptr, 0, L, c->z2pi,
-                             s);
-    const TC* cur = bufs[0];
-    for (int i = 1; i < no; ++i) {
-      contract_axes<TC, TC>(axes, cur, bufs[i], trans[i], chi[trans[i]], Ub(trans[i]), nullptr, 0, s);
-      cur = bufs[i];
-    }
-    final_strides(axes, c3, c3, gn, c3, fs);
-    contract_axes<TC, double>(axes, cur, out, c3, chi3, Ub(c3), fs, out_base, s);
   }
   return HOTRG_OK;
 }
@@ -951,7 +1077,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   hotrg_opts def;
   hotrg_opts_default(&def);
   if (!opt) opt = &def;
-  if (opt->batch < 1 || opt->max_steps < 1 || opt->max_steps > 64) return HOTRG_EINVAL;
+  if (opt->batch < 1 || opt->max_steps < 1 || opt->max_steps > 64 || opt->group < 0) return HOTRG_EINVAL;
   if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_FP16X4) return HOTRG_EINVAL;
   if (opt->derivatives < 0 || opt->derivatives > 2) return HOTRG_EINVAL;
   hotrg_ctx c;
@@ -966,6 +1092,7 @@ int hotrg_workspace_size(int d, int Dcut, const hotrg_opts* opt, size_t* bytes) 
   c.deriv_mode = opt->derivatives;
   c.impure = opt->impurities != 0;
   c.z2 = opt->z2 != 0;
+  c.group = group_for(opt);
   *bytes = carve(&c, nullptr);
   return HOTRG_OK;
 }
@@ -980,6 +1107,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_FP16X4) return HOTRG_EINVAL;
   if (opt->derivatives < 0 || opt->derivatives > 2) return HOTRG_EINVAL;
   if (opt->max_sweeps < 0 || opt->max_sweeps > 1000) return HOTRG_EINVAL;
+  if (opt->group < 0) return HOTRG_EINVAL;
   std::vector<double> vb(opt->batch), vh(opt->batch);
   for (int i = 0; i < opt->batch; ++i) {
     vb[i] = opt->beta ? opt->beta[i] : beta;
@@ -1016,6 +1144,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->z2 = opt->z2 != 0;
   c->z2_opt = c->z2;
   c->z2_inst.assign(opt->batch, c->z2 ? 1 : 0);
+  c->group = group_for(opt);
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->max_sweeps = opt->max_sweeps > 0 ? opt->max_sweeps : 40;
   c->stream = static_cast<cudaStream_t>(opt->stream);
@@ -1154,50 +1283,61 @@ static int enqueue_step(hotrg_ctx* c, int a, int step) {
         }
     }
   }
-  // 2-4. squeeze, normalise and accumulate, instance by instance (each fills the GPU)
-  for (int i = 0; i < c->batch; ++i) {
-    const double* Ti = c->T + i * P2max;
-    const double* Ui = c->U + i * c->u_stride;
-    Tangents tg;
+  // 2-4. squeeze (groups of instances: one GEMM launch per chunk for the whole group), normalise
+  // and accumulate instance by instance
+  for (int i0 = 0; i0 < c->batch; i0 += c->group) {
+    const int ng = std::min(c->group, c->batch - i0);
+    Group grp;
+    for (int j = 0; j < ng; ++j) {
+      const double* Ti = c->T + (i0 + j) * P2max;
+      grp.add(Ti, Ti, c->U + (i0 + j) * c->u_stride, slot(c, j).Tnext, i0 + j);
+    }
+    Tangents tg;  // the group is a single instance when there are tangents (group_for)
     if (c->deriv) {
       tg.n = 2;
       for (int w = 0; w < 2; ++w) {
-        tg.dT[w] = c->dT + (w * c->batch + i) * P2max;
+        tg.dT[w] = c->dT + (w * c->batch + i0) * P2max;
         tg.dout[w] = w ? c->D2 : c->D1;
-        tg.dU[w] = c->deriv_mode == 2 ? c->dU + (w * c->batch + i) * c->u_stride : nullptr;
+        tg.dU[w] = c->deriv_mode == 2 ? c->dU + (w * c->batch + i0) * c->u_stride : nullptr;
       }
     }
     int rc = (c->z2 && nt > 0)
-                 ? (planes ? squeeze_z2<float>(c, i, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass)
-                           : squeeze_z2<double>(c, i, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0))
-             : planes ? squeeze<float>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, planes, npass, tg)
-                      : squeeze<double>(c, Ti, Ti, c->Tnext, Ui, g, gn, a, chi, trans, nt, 0, 0, tg);
+                 ? (planes ? squeeze_z2<float>(c, grp, g, gn, a, chi, trans, nt, planes, npass)
+                           : squeeze_z2<double>(c, grp, g, gn, a, chi, trans, nt, 0, 0))
+             : planes ? squeeze<float>(c, grp, g, gn, a, chi, trans, nt, planes, npass, tg)
+                      : squeeze<double>(c, grp, g, gn, a, chi, trans, nt, 0, 0, tg);
     if (rc) return rc;
-    // impure tensors with the pure flow's isometries: the pair merges with itself at step 1
-    // (Eq. (SS)) and with a pure site after (Eq. (ST)); the single spin always with a pure site
+    // impure tensors with the pure flow's isometries (a group of one): the pair merges with itself
+    // at step 1 (Eq. (SS)) and with a pure site after (Eq. (ST)); the single spin always with a pure
+    // site
     for (int w = 0; c->impure && w < 2; ++w) {
-      const double* Si = c->SI + (w * c->batch + i) * P2max;
-      const double* partner = (w == 0 && step == 1) ? Si : Ti;
-      double* out = c->Stmp + w * P2max;
-      rc = planes ? squeeze<float>(c, Si, partner, out, Ui, g, gn, a, chi, trans, nt, planes, npass)
-                  : squeeze<double>(c, Si, partner, out, Ui, g, gn, a, chi, trans, nt, 0, 0);
+      const double* Si = c->SI + (w * c->batch + i0) * P2max;
+      const double* partner = (w == 0 && step == 1) ? Si : grp.T1[0];
+      Group imp;
+      imp.add(Si, partner, grp.U[0], c->Stmp + w * P2max, i0);
+      rc = planes ? squeeze<float>(c, imp, g, gn, a, chi, trans, nt, planes, npass)
+                  : squeeze<double>(c, imp, g, gn, a, chi, trans, nt, 0, 0);
       if (rc) return rc;
     }
-    double* Tw = c->T + i * P2max;
-    {
-      PhaseScope norm_scope(c, PH_NORM);
-      launch_norm_log(c->Tnext, gn.P * gn.P, c->norm_partial, c->cval + i,
-                      c->lnc_log + (long long)i * (c->max_steps + 1), c->L + i, c->dstep, c->status, s);
+    for (int j = 0; j < ng; ++j) {
+      const int i = i0 + j;
+      const double* Tn = grp.out[j];
+      double* Tw = c->T + i * P2max;
+      {
+        PhaseScope norm_scope(c, PH_NORM);
+        launch_norm_log(Tn, gn.P * gn.P, c->norm_partial, c->cval + i, c->lnc_log + (long long)i * (c->max_steps + 1),
+                        c->L + i, c->dstep, c->status, s);
+      }
+      // tangent of T' / ||T'||
+      for (int w = 0; w < tg.n; ++w) {
+        double* dTi = c->dT + (w * c->batch + i) * P2max;
+        launch_tangent_norm(Tn, tg.dout[w], nullptr, dTi, gn.P * gn.P, c->cval + i, c->norm_partial,
+                            c->dlnc + w * c->batch + i, c->dL + w * c->batch + i, c->dstep, s);
+      }
+      launch_scale(Tn, Tw, gn.P * gn.P, c->cval + i, s);
+      for (int w = 0; c->impure && w < 2; ++w)
+        launch_scale(c->Stmp + w * P2max, c->SI + (w * c->batch + i) * P2max, gn.P * gn.P, c->cval + i, s);
     }
-    // tangent of T' / ||T'||
-    for (int w = 0; w < tg.n; ++w) {
-      double* dTi = c->dT + (w * c->batch + i) * P2max;
-      launch_tangent_norm(c->Tnext, tg.dout[w], nullptr, dTi, gn.P * gn.P, c->cval + i, c->norm_partial,
-                          c->dlnc + w * c->batch + i, c->dL + w * c->batch + i, c->dstep, s);
-    }
-    launch_scale(c->Tnext, Tw, gn.P * gn.P, c->cval + i, s);
-    for (int w = 0; c->impure && w < 2; ++w)
-      launch_scale(c->Stmp + w * P2max, c->SI + (w * c->batch + i) * P2max, gn.P * gn.P, c->cval + i, s);
   }
   launch_trace_x(c->T, P2max, c->batch, gn, a, c->L, c->dstep, c->out3, s);
   for (int w = 0; c->impure && w < 2; ++w)
@@ -1865,6 +2005,37 @@ int hotrg_gemm_split_f16(const float* A, long long lda, const float* Bt, long lo
   const int rc = launch_gemm_split(Ap, ld, Bp, ld, C, ldc, M, N, K, npass, status, 4.0, s, kblock, 16, fg);
   if (rc) return rc;
   return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
+}
+
+size_t hotrg_gemm_wait_probe_bytes(void) {
+  return hotrg_gemm_scratch_bytes(TC_PROBE_M, TC_PROBE_N, TC_PROBE_K) + sizeof(float) * TC_PROBE_M * TC_PROBE_N;
+}
+
+int hotrg_gemm_wait_probe(double timeout_s, void* scratch, size_t scratch_bytes, void* stream) {
+  if (!scratch || !(timeout_s > 0.0) || timeout_s > 10.0) return HOTRG_EINVAL;
+  if (scratch_bytes < hotrg_gemm_wait_probe_bytes() || (reinterpret_cast<uintptr_t>(scratch) % kAlign))
+    return HOTRG_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long M = TC_PROBE_M, N = TC_PROBE_N, K = TC_PROBE_K;
+  char* p = static_cast<char*>(scratch);
+  int* status = reinterpret_cast<int*>(p);
+  p += kAlign;
+  Planes<__nv_bfloat16> Ap, Bp;
+  Ap.nparts = Bp.nparts = 2;
+  for (int k = 0; k < 3; ++k) {
+    Ap.p[k] = reinterpret_cast<__nv_bfloat16*>(p);
+    p += round_up(M * K * 2, kAlign);
+  }
+  for (int k = 0; k < 3; ++k) {
+    Bp.p[k] = reinterpret_cast<__nv_bfloat16*>(p);
+    p += round_up(N * K * 2, kAlign);
+  }
+  float* C = reinterpret_cast<float*>(p);
+  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return HOTRG_EDEVICE;
+  const int rc = launch_gemm_split(Ap, K, Bp, K, C, N, M, N, K, 3, status, timeout_s, s, 64, 16, 1, nullptr, nullptr,
+                                   true);
+  if (rc) return rc;
+  return hotrg_gemm_status(scratch, stream);
 }
 
 int hotrg_gemm_status(const void* scratch, void* stream) {

@@ -154,10 +154,13 @@ void prepare_eig_attributes();  // shared-memory limit of the tangent kernel (on
 // C[m][n] = sum_k A[m][k] Bt[n][k] in FP64 (CUDA cores).
 // With blk (device memory, see GemmBlocks below), only the listed output blocks are computed, each
 // over its own k range; M, N are then the extents of A's and Bt's rows.
+// With bat (a batched launch, see GemmBatch), `batch` such products, instance i at A + i a_inst,
+// Bt + i b_inst, C + i c_inst with blocks blk[i].
 struct GemmBlocks;
+struct GemmBatch;
 void launch_gemm_f64(const double* A, long long lda, const double* Bt, long long ldb, double* C,
                      long long ldc, long long M, long long N, long long K, cudaStream_t s,
-                     const GemmBlocks* blk = nullptr);
+                     const GemmBlocks* blk = nullptr, const GemmBatch* bat = nullptr);
 
 // ---- gemm_tc.cu ----------------------------------------------------------------------------
 // C[m][n] = sum over passes p of sum_k A_{a(p)}[m][k] Bt_{b(p)}[n][k], bf16 operand planes on
@@ -176,7 +179,9 @@ struct GemmBlocks {
   int nb;
   int m0[2], mc[2], n0[2], nc[2], k0[2], kc[2];
 };
-// Batched launch (up to 256 instances): `batch` independent products of the same shape in one
+// Largest number of instances one batched GEMM launch takes (its tile prefix lives in shared memory).
+constexpr int kMaxGemmBatch = 256;
+// Batched launch (up to kMaxGemmBatch instances): `batch` independent products of the same shape in one
 // persistent launch; plane k of instance i starts at A.p[k] + i a_inst (elements, multiple of 8,
 // at least M lda), likewise B (b_inst) and C (c_inst); with blk, instance i's blocks are blk[i];
 // fp16 scale bounds at A.amax + i amax_inst and B.amax + i amax_inst.
@@ -189,7 +194,9 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
                       int npass, int* status, double timeout_s, cudaStream_t s, int bk = 64,
                       int group_m = 16, int fold_group = 1, const GemmBlocks* blk = nullptr,
-                      const GemmBatch* bat = nullptr);
+                      const GemmBatch* bat = nullptr, bool stall = false);
+// stall (test of the bounded waits): the kernel's producer issues no copies, so every CTA's first
+// wait for a stage runs out after timeout_s and the launch ends with ST_TIMEOUT in *status.
 // Largest fold group the kernel variant for (npass, bk) accepts.
 int max_fold_group(int npass, int bk);
 void launch_split_rows(const float* X, long long ldx, long long rows, long long cols,

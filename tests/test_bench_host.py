@@ -74,3 +74,39 @@ def test_committed_profiles_parse():
         with open(path) as fh:
             text = fh.read()
         assert "gemm_tc_sha=" in text and "traffic_bytes_per_launch_full=" in text, path
+
+
+def test_accuracy_line_reads_the_committed_fp64_reference(monkeypatch, tmp_path):
+    """The bench's accuracy line compares its flow's ln Z/N after each step with the FP64 GPU flow
+    recorded in the committed accuracy summary (and the oracle's golden, when present)."""
+    ref = bench.stored_fp64_reference()
+    assert sorted(ref) == list(range(1, 9)) and all(0.7 < v < 1.2 for v in ref.values())
+    p = tmp_path / "acc.md"
+    p.write_text("# x\n\n- fp64_lnz_step_1 = 1.5\n- fp64_lnz_step_2 = 1.25\n")
+    monkeypatch.setattr(bench, "ACCURACY_PROFILE", str(p))
+    monkeypatch.setattr(bench, "ORACLE_GOLDEN_D10", str(tmp_path / "missing.json"))
+    a = args(monkeypatch)
+    acc = bench.accuracy_line(a, [1.5 * (1 + 1e-8), 1.25 * (1 - 2e-8), 1.1])
+    assert acc["rel_err_vs_fp64_gpu"]["1"] == pytest.approx(1e-8, rel=1e-6)
+    assert acc["rel_err_vs_fp64_gpu"]["2"] == pytest.approx(2e-8, rel=1e-6)
+    assert acc["rel_err_vs_oracle"] == {} and acc["lnz_per_site_last"] == 1.1
+    assert bench.accuracy_line(args(monkeypatch, "--dcut", "8"), [1.0]) is None   # other configuration
+
+
+def test_scan_group_is_the_largest_that_fits(monkeypatch):
+    class FakeCuda:
+        def __init__(self, free):
+            self.free = free
+
+        def mem_get_info(self):
+            return self.free, self.free
+
+    class FakeTorch:
+        def __init__(self, free):
+            self.cuda = FakeCuda(free)
+
+    a = args(monkeypatch, "--workload", "scan")
+    assert bench.squeeze_group(a, FakeTorch(1e15)) == 64
+    assert bench.squeeze_group(a, FakeTorch(1e6)) == 1
+    assert bench.squeeze_group(args(monkeypatch, "--workload", "scan", "--group", "4"), FakeTorch(1e6)) == 4
+    assert bench.squeeze_group(args(monkeypatch), FakeTorch(1e6)) == 0      # single flow: library default

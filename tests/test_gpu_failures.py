@@ -1,12 +1,13 @@
 """Failure detection through the C ABI: every failure is made on the host or by a wait limit
 that runs out, never by a GPU fault.
 
-* HOTRG_ETIMEOUT: a context whose device-side wait limit is far below the time one k-block of
-  the tensor-core GEMM takes. The GEMM's waits give up, the kernel drains the copies and MMAs
-  it issued (those waits have a floor of one second: issued work always completes), frees its
-  tensor memory and returns; the host reads the status word.
-* HOTRG_ENUMERIC: a tensor with a NaN entry, loaded from the host (the norm of the next step
-  is not finite); a tensor with a negative trace (the free energy has no logarithm).
+* HOTRG_ETIMEOUT: a probe launch of the tensor-core GEMM whose copy-issuing thread issues no
+  copies, so that a wait is on data that never arrives (a short limit alone does not do it: a
+  wait that the hardware lets block for a while is satisfied by real copies first). The wait
+  gives up, the kernel frees its tensor memory and returns; the host reads the status word.
+* HOTRG_ENUMERIC: a tensor with a NaN entry, loaded from the host (its Gram matrices and the norm
+  of the next step are not finite: the eigensolver still orders the eigenvalues as a permutation
+  and flags them); a tensor with a negative trace (the free energy has no logarithm).
 * HOTRG_ENOCONV: an eigensolver sweep limit of one sweep on a generic Gram matrix.
 
 Each error is sticky on its context, the context stays queryable (calls return the error
@@ -41,24 +42,29 @@ def _fresh_context_still_matches_the_oracle():
     assert abs(lnz - g["steps"][3]["lnz"]) < 1e-12 * abs(lnz)
 
 
-def test_wait_limit_that_runs_out_gives_etimeout_and_a_usable_device():
-    from paper_1906_06060_gb300 import HotrgError, _lib
-    # 100 ns: shorter than any TMA copy or k-block of MMAs; steps 3 and 4 run the tensor-core GEMM
-    with _flow(4, 0.1497, 0.0, 5, precision="bf16x3", fp64_steps=2, wait_timeout_s=1e-7, graphs=False) as f:
-        code = None
-        try:
-            for _ in range(4):
-                f.step()
-            f.free_energy()
-        except HotrgError as e:
-            code = e.code
-        assert code == _lib.HOTRG_ETIMEOUT
-        # sticky: every later call reports it, and nothing else goes wrong
-        for call in (f.step, f.free_energy, f.observables, f.ln_norms):
-            with pytest.raises(HotrgError) as e:
-                call()
-            assert e.value.code == _lib.HOTRG_ETIMEOUT
-        assert f.dims() is not None  # host-side query still answers
+def test_wait_that_nothing_satisfies_gives_etimeout_and_a_usable_device():
+    """The GEMM's bounded waits: a probe launch whose copy-issuing thread issues no copies, so the
+    first wait for operand data can never be satisfied. It must give up after its limit, record
+    HOTRG_ETIMEOUT and leave the device usable: a normal GEMM on the same stream afterwards is
+    correct, and so is a new flow context."""
+    import torch
+    from ctypes import c_void_p
+    from paper_1906_06060_gb300 import _lib, gemm_split
+    lib = _lib.load()
+    stream = torch.cuda.current_stream()
+    nbytes = lib.hotrg_gemm_wait_probe_bytes()
+    scratch = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    for limit in (0.05, 0.2):
+        assert lib.hotrg_gemm_wait_probe(limit, c_void_p(scratch.data_ptr()), nbytes,
+                                         c_void_p(stream.cuda_stream)) == _lib.HOTRG_ETIMEOUT
+    assert lib.hotrg_gemm_wait_probe(0.0, c_void_p(scratch.data_ptr()), nbytes,
+                                     c_void_p(stream.cuda_stream)) == _lib.HOTRG_EINVAL
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((256, 192)).astype(np.float32)
+    B = rng.standard_normal((512, 192)).astype(np.float32)
+    C = gemm_split(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), npass=6).cpu().numpy()
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    assert np.max(np.abs(C - ref)) < 1e-4 * np.max(np.abs(ref))
     _fresh_context_still_matches_the_oracle()
 
 

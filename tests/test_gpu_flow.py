@@ -236,6 +236,41 @@ def test_batched_instances_match_separate_runs(precision, tol):
             assert abs(f.observables()["x_indicator"] - x_b[i]) < 1e-6
 
 
+@pytest.mark.parametrize("precision,fp64_steps,x6_steps", [("fp64", 0, 0), ("bf16x3", 2, 5), ("fp16x3", 2, 0)])
+def test_grouped_squeeze_is_bitwise_the_instance_by_instance_squeeze(precision, fp64_steps, x6_steps):
+    """A temperature/field scan whose squeeze GEMM runs as one launch per chunk over a group of
+    instances (the tile list spans the instances, each with its own operand planes and output)
+    against the same context squeezing instance by instance: every tile sums the same products in
+    the same order, so the flows agree bit for bit (the batched Gram and eigensolver launches are
+    the same in both)."""
+    betas = [0.14, 0.1497, 0.16, 0.152, 0.145]
+    hs = [0.0, 1e-5, -1e-5, 0.0, 2e-5]
+    res = []
+    for group in (1, 5, 2):   # 2: groups of two and a group of one
+        with flow(4, betas, hs, 5, precision=precision, fp64_steps=fp64_steps, x6_steps=x6_steps,
+                  group=group) as f:
+            for _ in range(7):
+                f.step()
+            res.append((f.free_energy()[0], [f.ln_norms(i) for i in range(5)], f.get_tensor(4),
+                        [f.observables(i)["x_indicator"] for i in range(5)]))
+    for other in res[1:]:
+        assert np.array_equal(res[0][0], other[0])
+        for a, b in zip(res[0][1], other[1]):
+            assert np.array_equal(a, b)
+        assert np.array_equal(res[0][2], other[2])
+        assert res[0][3] == other[3]
+
+
+def test_group_larger_than_batch_and_invalid_group():
+    from paper_1906_06060_gb300 import HotrgError, _lib
+    with flow(4, [0.15, 0.16], 0.0, 4, group=64) as f:  # capped at the batch
+        f.step()
+        assert np.all(np.isfinite(f.free_energy()[0]))
+    with pytest.raises(HotrgError) as e:
+        flow(4, [0.15, 0.16], 0.0, 4, group=-1)
+    assert e.value.code == _lib.HOTRG_EINVAL
+
+
 @pytest.mark.parametrize("precision", ["fp64", "bf16x3"])
 def test_graph_replay_matches_direct_launches(precision):
     """Steady-state steps replayed from a captured CUDA graph give bit-identical results."""

@@ -131,6 +131,26 @@ def test_z2_dcut10_steady_steps_match_dense(x6):
         np.testing.assert_allclose(a[:n] / a[0], b[:n] / b[0], rtol=0, atol=5e-6)
 
 
+@pytest.mark.parametrize("precision,fp64_steps,x6_steps", [("fp64", 0, 0), ("bf16x3", 3, 12), ("fp16x3", 2, 0)])
+def test_z2_grouped_squeeze_is_bitwise_the_instance_by_instance_squeeze(precision, fp64_steps, x6_steps):
+    """Block-sparse: one GEMM launch per chunk over the group, each instance with its own parity
+    counts and block descriptor (the tile list's prefix over the instances), against squeezing
+    instance by instance in the same context: bit for bit."""
+    betas = [0.14, 0.1497, 0.16, 0.151]
+    res = []
+    for group in (1, 4, 3):
+        with hotrg(4, betas, 0.0, 5, precision=precision, fp64_steps=fp64_steps, x6_steps=x6_steps, z2=True,
+                   group=group, max_steps=8) as f:
+            for _ in range(8):
+                f.step()
+            res.append((f.free_energy()[0], [f.ln_norms(i) for i in range(4)], f.get_tensor(3)))
+    for other in res[1:]:
+        assert np.array_equal(res[0][0], other[0])
+        for a, b in zip(res[0][1], other[1]):
+            assert np.array_equal(a, b)
+        assert np.array_equal(res[0][2], other[2])
+
+
 def test_z2_batched_instances_match_separate_runs():
     """Each instance carries its own parity counts. Dcut = 5: no cut of these flows splits a
     degenerate multiplet (at Dcut = 6 one does, and the Gram's batch-dependent summation order
