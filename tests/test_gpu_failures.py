@@ -85,16 +85,18 @@ def test_nan_tensor_gives_enumeric():
 
 
 def test_negative_trace_gives_enumeric_without_poisoning_the_flow():
+    """d = 1: a step squares the site matrix; a quarter-turn rotation squares to -1, whose trace
+    has no logarithm. free_energy refuses it (not sticky: the flow itself is valid), and a positive
+    tensor afterwards gives a finite free energy."""
     from paper_1906_06060_gb300 import HotrgError, _lib
-    P = 16
-    T = -np.eye(P).reshape((2,) * 8)
-    with _flow(4, 0.3, 0.0, 4) as f:
-        f.set_tensor(T)
+    with _flow(1, 0.3, 0.0, 4) as f:
+        f.set_tensor(np.array([[0.0, -1.0], [1.0, 0.0]]))
+        f.step(0)
         with pytest.raises(HotrgError) as e:
             f.free_energy()
         assert e.value.code == _lib.HOTRG_ENUMERIC
-        # the flow state itself is valid: a positive tensor afterwards gives a free energy
-        f.set_tensor(np.eye(P).reshape((2,) * 8))
+        f.set_tensor(np.array([[2.0, 1.0], [1.0, 2.0]]))
+        f.step(0)
         lnz = f.free_energy()[0][0]
         assert math.isfinite(lnz)
 
