@@ -63,7 +63,8 @@ typedef enum hotrg_precision {
                        each); hi*hi + hi*lo + lo*hi accumulate in FP32 and the result is scaled
                        back by 2^-(eA + eB): O(2^-22) relative error per product (entries more than
                        2^-18 below their operand's largest lose the lo part's low bits, an absolute
-                       error below 2^-39 of that largest), at the tensor cost of BF16X3 */
+                       error below 2^-39 of that largest), at the tensor cost of BF16X3. With
+                       opts.derivatives the squeezes that carry tangents use bf16 planes (BF16X3) */
   HOTRG_FP16X4 = 5  /* FP16X3 plus lo*lo: no systematic truncation of the product */
 } hotrg_precision;
 

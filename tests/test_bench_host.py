@@ -18,7 +18,7 @@ def args(monkeypatch, *argv):
 
 def test_defaults_name_the_dcut10_flow(monkeypatch):
     a = args(monkeypatch)
-    assert (a.dcut, a.precision, a.fp64_steps, a.x6_steps, a.warmup, a.steps) == (10, "bf16x3", 3, 12, 12, 4)
+    assert (a.dcut, a.precision, a.fp64_steps, a.x6_steps, a.warmup, a.steps) == (10, "fp16x3", 3, 6, 12, 4)
     assert args(monkeypatch, "--workload", "scan").dcut == 8
     assert bench.steady_flops(10) == 2.0e15
 

@@ -90,7 +90,7 @@ def test_4d_dcut3_matches_oracle_fixed_isometry_difference_quotients(beta, h):
 @pytest.mark.parametrize("precision,fp64_steps,x6_steps,tol", [
     ("fp64", 0, 0, 1e-9),        # bounded by the difference quotients of the golden values
     ("bf16x6", 0, 0, 1e-6),      # every squeeze split, FP32 accumulation: ~2e-7 .. 9e-7 measured
-    ("bf16x3", 3, 12, 1e-6),     # the benchmark's precision schedule
+    ("bf16x3", 3, 12, 1e-6),     # the mixed path with BF16X6 to step 12 (tangent squeezes use bf16 planes)
     ("bf16x3", 0, 0, 1e-5),      # every squeeze with three bf16 products: ~4e-6 measured
 ])
 def test_4d_dcut5_matches_golden(name, precision, fp64_steps, x6_steps, tol):
@@ -237,7 +237,7 @@ def test_eig_mode_4d_dcut3_matches_oracle_flow_difference_quotients(beta, h):
 @pytest.mark.parametrize("name", ["deriv_d4_b0.1497_h0_D5_n8", "deriv_d4_b0.16_h0.01_D5_n8"])
 @pytest.mark.parametrize("precision,fp64_steps,x6_steps,tol", [
     ("fp64", 0, 0, 1e-8),        # bounded by the difference quotients of the golden values
-    ("bf16x3", 3, 12, 1e-6),     # the benchmark's precision schedule
+    ("bf16x3", 3, 12, 1e-6),     # the mixed path with BF16X6 to step 12 (tangent squeezes use bf16 planes)
 ])
 def test_eig_mode_4d_dcut5_matches_golden(name, precision, fp64_steps, x6_steps, tol):
     with open(os.path.join(GOLDEN, name + ".json")) as fh:
