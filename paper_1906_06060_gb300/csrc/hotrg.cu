@@ -801,18 +801,20 @@ int squeeze(hotrg_ctx* c, const Group& G, const Geom& g, const Geom& gn, int a, 
         TC* X1 = static_cast<TC*>(S.X1);
         TC* X2 = static_cast<TC*>(S.X2);
         const int b0 = trans[0];
+        // the mode product that writes X also measures max |X|, the fp16 scale bound of Y
         if (kcnt[0] != prev_k0) {
-          launch_mode_unprimed<double, TC>(T1, X1, g, b0, Ub(U, b0), kcnt[0], s);
+          launch_mode_unprimed<double, TC>(T1, X1, g, b0, Ub(U, b0), kcnt[0], s, nullptr, nullptr,
+                                           (f16 && no == 1) ? S.amax + 1 : nullptr);
           for (int p = 0; p < tg.n; ++p)
             launch_mode_unprimed<double, TC>(tg.dT[p], static_cast<TC*>(c->dX1[p]), g, b0, Ub(U, b0), kcnt[0], s,
                                              tg.dU[p] ? T1 : nullptr, tg.dU[p] ? Ub(tg.dU[p], b0) : nullptr);
         }
         const TC* X = X1;
         if (no >= 2) {
-          launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(U, trans[1]), kcnt[1], s);
+          launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(U, trans[1]), kcnt[1], s, nullptr, nullptr,
+                                       f16 ? S.amax + 1 : nullptr);
           X = X2;
         }
-        if (f16) launch_absmax<TC>(X, P, P, P, S.amax + 1, s);
         launch_build_y<TC, Op>(X, blocks(S.Y, y_plane, fwd_blk, 1, S.amax), ld, g, a, s);
         for (int p = 0; p < tg.n; ++p) {
           const TC* dX = static_cast<TC*>(c->dX1[p]);
@@ -992,13 +994,16 @@ int squeeze_z2(hotrg_ctx* c, const Group& G, const Geom& g, const Geom& gn, int 
       } else {
         TC* X1 = static_cast<TC*>(S.X1);
         TC* X2 = static_cast<TC*>(S.X2);
-        if (kcnt[0] != prev_k0) launch_mode_unprimed<double, TC>(G.T1[j], X1, g, trans[0], Ub(j, trans[0]), kcnt[0], s);
+        // the mode product that writes X also measures max |X|, the fp16 scale bound of Y
+        if (kcnt[0] != prev_k0)
+          launch_mode_unprimed<double, TC>(G.T1[j], X1, g, trans[0], Ub(j, trans[0]), kcnt[0], s, nullptr, nullptr,
+                                           (f16 && no == 1) ? S.amax + 1 : nullptr);
         const TC* X = X1;
         if (no >= 2) {
-          launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(j, trans[1]), kcnt[1], s);
+          launch_mode_unprimed<TC, TC>(X1, X2, g, trans[1], Ub(j, trans[1]), kcnt[1], s, nullptr, nullptr,
+                                       f16 ? S.amax + 1 : nullptr);
           X = X2;
         }
-        if (f16) launch_absmax<TC>(X, P, P, P, S.amax + 1, s);
         launch_build_y_z2<TC, Op>(X, pl(S.Y, y_plane, 1, S.amax), ldz, g, a, S.z2rank, S.z2kcol, L, S.z2pi, s);
       }
     }

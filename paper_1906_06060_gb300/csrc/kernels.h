@@ -47,10 +47,12 @@ void launch_scale(const double* src, double* dst, long long n, const double* c, 
 void launch_trace_x(const double* T, long long t_stride, int batch, Geom g, int axis, const double* L,
                     const int* dstep, double* out3, cudaStream_t s);
 // out[..u_b=j..] = sum_i U[kk][i][j] in[..u_b=i..] on unprimed leg b (U: [chi][Db][Db] fp64);
-// with in2, plus the same product of in2 with U2.
+// with in2, plus the same product of in2 with U2. With amax, *amax = max |out| (the bits of a
+// non-negative float, as launch_absmax writes them).
 template <class Tin, class Tout>
 void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double* U, int kk,
-                          cudaStream_t s, const Tin* in2 = nullptr, const double* U2 = nullptr);
+                          cudaStream_t s, const Tin* in2 = nullptr, const double* U2 = nullptr,
+                          unsigned* amax = nullptr);
 // Tt[p][u] = T[u][p] (P x P), converted to Tout.
 template <class Tout>
 void launch_transpose(const double* T, Tout* Tt, long long P, cudaStream_t s);

@@ -281,7 +281,8 @@ template <class Tin, class Tout, bool TWO>
 __global__ void __launch_bounds__(256) k_mode_unprimed(const Tin* __restrict__ in, Tout* __restrict__ out,
                                                        long long total, long long stride_b, int Db,
                                                        const double* __restrict__ U, int kk,
-                                                       const Tin* __restrict__ in2, const double* __restrict__ U2) {
+                                                       const Tin* __restrict__ in2, const double* __restrict__ U2,
+                                                       unsigned* amax) {
   using Acc = AccT<Tout>;
   __shared__ Acc W[kMaxGram];
   __shared__ Acc W2[TWO ? kMaxGram : 1];
@@ -291,6 +292,7 @@ __global__ void __launch_bounds__(256) k_mode_unprimed(const Tin* __restrict__ i
   }
   __syncthreads();
   const long long nbase = total / Db;
+  float m = 0.f;  // max |out| of this thread (with amax: the bound of an fp16 operand's source)
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nbase;
        t += (long long)gridDim.x * blockDim.x) {
     const long long base = (t / stride_b) * stride_b * Db + t % stride_b;
@@ -310,7 +312,12 @@ __global__ void __launch_bounds__(256) k_mode_unprimed(const Tin* __restrict__ i
           if (TWO) acc += W2[i * Db + j] * x2[i];
         }
       out[base + j * stride_b] = (Tout)acc;
+      if (amax) m = fmaxf(m, abs_up((Tout)acc));
     }
+  }
+  if (amax) {
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));
   }
 }
 
@@ -588,15 +595,16 @@ void launch_trace_x(const double* T, long long t_stride, int batch, Geom g, int 
 
 template <class Tin, class Tout>
 void launch_mode_unprimed(const Tin* in, Tout* out, Geom g, int b, const double* U, int kk,
-                          cudaStream_t s, const Tin* in2, const double* U2) {
+                          cudaStream_t s, const Tin* in2, const double* U2, unsigned* amax) {
   const long long total = g.P * g.P;
   const long long nbase = total / g.D[b];
+  if (amax) cudaMemsetAsync(amax, 0, sizeof(unsigned), s);
   if (in2)
     k_mode_unprimed<Tin, Tout, true><<<grid_for(nbase, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
-                                                                           g.D[b], U, kk, in2, U2);
+                                                                           g.D[b], U, kk, in2, U2, amax);
   else
     k_mode_unprimed<Tin, Tout, false><<<grid_for(nbase, 256), 256, 0, s>>>(in, out, total, g.Sn[b] * g.P,
-                                                                            g.D[b], U, kk, nullptr, nullptr);
+                                                                            g.D[b], U, kk, nullptr, nullptr, amax);
   count_launches(1);
 }
 
@@ -711,11 +719,11 @@ void prepare_kernel_attributes() {
 
 // explicit instantiations: FP64 path (double everywhere) and BF16X3 path (float intermediates)
 template void launch_mode_unprimed<double, double>(const double*, double*, Geom, int, const double*, int, cudaStream_t,
-                                                   const double*, const double*);
+                                                   const double*, const double*, unsigned*);
 template void launch_mode_unprimed<double, float>(const double*, float*, Geom, int, const double*, int, cudaStream_t,
-                                                  const double*, const double*);
+                                                  const double*, const double*, unsigned*);
 template void launch_mode_unprimed<float, float>(const float*, float*, Geom, int, const double*, int, cudaStream_t,
-                                                 const float*, const double*);
+                                                 const float*, const double*, unsigned*);
 template void launch_transpose<double>(const double*, double*, long long, cudaStream_t);
 template void launch_transpose<float>(const double*, float*, long long, cudaStream_t);
 template void launch_build_bt<double, double>(const double*, const Planes<double>&, long long, Geom, int, const double*, int,
