@@ -324,9 +324,9 @@ int hotrg_gemm_wait_probe(double timeout_s, void *scratch, size_t scratch_bytes,
 int hotrg_gemm_status(const void *scratch, void *stream);
 
 /* Benchmark support (the paper has no counterpart): the GPU's FP64 FMA rate, measured with
- * independent FMA chains on every SM (8, 16 and 32 chains per thread, each as two launches of
- * `iters` loop iterations of which the second is timed with CUDA events on `stream`; the best
- * rate is returned). It is the roofline denominator of the FP64 squeeze, whose cost is
+ * independent FMA chains on every SM (8, 16 and 32 chains per thread, and a 4 x 4 outer-product
+ * accumulation; each as two launches of `iters` loop iterations of which the second is timed with
+ * CUDA events on `stream`; the best rate is returned). It is the roofline denominator of the FP64 squeeze, whose cost is
  * fixed by Sec. 2's O(Dcut^15) statement. `sink` is a device array of at least 8 x (SM count)
  * doubles that the kernel may write (in practice it writes nothing); *tflops receives the rate.
  * Synchronises `stream`. Errors: EINVAL (iters outside 1..2^32, null pointers), EDEVICE. */

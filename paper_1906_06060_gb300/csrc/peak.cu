@@ -1,7 +1,8 @@
 // FP64 FMA throughput of the GPU: the denominator of the FP64 path's roofline. The paper's cost
 // statement (Sec. 2: O(Dcut^15) flops per step) fixes the work; how fast the FP64 squeeze can
-// run is set by the rate of the CUDA cores' double-precision FMA units, which this kernel
-// measures (independent FMA chains in every thread, enough warps to cover the FMA latency).
+// run is set by the rate of the CUDA cores' double-precision FMA units, which these kernels
+// measure (independent FMA chains in every thread, enough warps to cover the FMA latency, and
+// the 4 x 4 outer-product accumulation of a register-blocked GEMM).
 #include <algorithm>
 
 #include "kernels.h"
@@ -32,6 +33,36 @@ __global__ void __launch_bounds__(256) k_dfma_chains(long long iters, double see
   if (s == -1.0) sink[blockIdx.x] = s;
 }
 
+// 4 x 4 outer-product accumulation, the inner loop of a register-blocked GEMM: 16 independent
+// accumulators fed by 8 operands per iteration (the operands drift slowly so nothing is constant)
+__global__ void __launch_bounds__(256) k_dfma_outer(long long iters, double seed, double* sink) {
+  double a[4], b[4], acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[i] = seed + 1e-9 * threadIdx.x + 0.25 * i;
+    b[i] = 1.0 - 1e-12 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  }
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = fma(a[i], -1e-16, a[i]);
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += acc[i][j];
+  if (s == -1.0) sink[blockIdx.x] = s;
+}
+
 }  // namespace
 }  // namespace hotrg
 
@@ -56,7 +87,8 @@ extern "C" int hotrg_bench_fp64_fma(long long iters, double* sink, double* tflop
   // 8, 16 and 32 chains per thread (the FMA latency must be covered); the best rate is the peak
   double best = 0.0;
   bool ok = true;
-  auto run = [&](auto kernel, int chains) {
+  // flops per thread and loop iteration: chains x kUnroll FMAs, or 8 x (16 + 4) for the outer product
+  auto run = [&](auto kernel, int fmas_per_iter) {
     kernel<<<blocks, threads, 0, s>>>(iters, 1.0, sink);  // warm-up (clocks, code load)
     cudaEventRecord(e0, s);
     kernel<<<blocks, threads, 0, s>>>(iters, 1.0, sink);
@@ -67,12 +99,13 @@ extern "C" int hotrg_bench_fp64_fma(long long iters, double* sink, double* tflop
       ok = false;
       return;
     }
-    const double flops = 2.0 * (double)iters * kUnroll * chains * (double)blocks * threads;
+    const double flops = 2.0 * (double)iters * fmas_per_iter * (double)blocks * threads;
     best = std::max(best, flops / (ms * 1e-3) / 1e12);
   };
-  run(k_dfma_chains<8>, 8);
-  if (ok) run(k_dfma_chains<16>, 16);
-  if (ok) run(k_dfma_chains<32>, 32);
+  run(k_dfma_chains<8>, 8 * kUnroll);
+  if (ok) run(k_dfma_chains<16>, 16 * kUnroll);
+  if (ok) run(k_dfma_chains<32>, 32 * kUnroll);
+  if (ok) run(k_dfma_outer, 8 * 20);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!ok) {
