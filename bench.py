@@ -412,7 +412,10 @@ def run_ours(a, rank, world, dist):
                           "is what the kernels computed (about a quarter of it at h = 0)",
            "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "bf16",
+           "vs_baseline": None,
+           # the squeeze's operand type in the timed steps (split into hi + lo planes, FP32 accumulation;
+           # Gram matrices, eigensolver, norms and ln sums in FP64)
+           "dtype": "f64" if a.precision == "fp64" else ("fp16" if a.precision.startswith("fp16") else "bf16"),
            "data": "synthetic", "config": workload_config(a),
            "steps_per_s": a.steps / (ms_max * 1e-3), "roofline": roof,
            "executed_tflops": exec_all / (ms_max * 1e-3) / 1e12,
