@@ -44,7 +44,7 @@ typedef enum hotrg_status {
   HOTRG_ETIMEOUT = -5, /* a bounded device-side wait gave up */
   HOTRG_EDEVICE = -6,  /* CUDA runtime/driver error, or no sm_103 device */
   HOTRG_ESTATE = -7,   /* call not valid in the context's state (e.g. step log full) */
-  HOTRG_ENOTSUP = -8   /* valid request that this build does not provide */
+  HOTRG_ENOTSUP = -8   /* valid request that this library does not provide */
 } hotrg_status;
 
 typedef enum hotrg_precision {

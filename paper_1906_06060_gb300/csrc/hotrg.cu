@@ -1924,7 +1924,7 @@ const char* hotrg_strerror(int code) {
     case HOTRG_ETIMEOUT: return "a bounded device-side wait gave up";
     case HOTRG_EDEVICE: return "CUDA device error or no sm_103 device";
     case HOTRG_ESTATE: return "call not valid in the current state";
-    case HOTRG_ENOTSUP: return "not supported by this build";
+    case HOTRG_ENOTSUP: return "not supported by this library";
     default: return "unknown error";
   }
 }

@@ -224,7 +224,7 @@ def test_fp64_2d_flow_40_steps_matches_oracle_and_onsager():
 
 
 @pytest.mark.parametrize("precision,fp64_steps,x6_steps,bound", [
-    ("fp16x3", 3, 6, 1e-7),    # the mixed path: the benchmark's schedule, the benchmark spec's 1e-7
+    ("fp16x3", 3, 6, 1e-7),    # the mixed path: the benchmark's schedule, the 1e-7 target
     ("bf16x3", 3, 12, 1e-7),   # the same with BF16X3 after the six-product steps
     ("bf16x6", 3, 0, 1e-7),    # six-product GEMM after the FP64 steps
     ("fp16x3", 3, 0, 1e-7),    # fp16 planes (22-bit products) after the FP64 steps

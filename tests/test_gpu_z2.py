@@ -52,7 +52,7 @@ def test_z2_matches_dense_path_dcut5(precision, x6):
 
 def test_z2_flow_matches_oracle_golden_dcut5():
     """The benchmark's form of the mixed path (block-sparse, FP64 steps 1-3, BF16X6 to step 6,
-    FP16X3 after) against the oracle at every step: the benchmark spec's 1e-7."""
+    FP16X3 after) against the oracle at every step: the 1e-7 target."""
     g = golden("flow_d4_b0.1497_h0_D5_n16")
     lz, _, _, _ = run(4, 0.1497, 5, 16, z2=True, precision="fp16x3", fp64_steps=3, x6_steps=6)
     for st in g["steps"]:
