@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--no-z2", action="store_true",
                     help="dense squeeze at h = 0 (default: the zero-field block-sparse squeeze)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default GEMM tile configuration (default: autotune after the warm-up steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=2)
     ap.add_argument("--log-jsonl", default="",
@@ -347,6 +349,15 @@ def run_ours(a, rank, world, dist):
             flow.step()
     for flow in flows:
         flow.free_energy()
+    # the squeeze GEMM's tile configuration for the steady shape, picked by the library's
+    # autotuner on the last warm-up step's operands (outside the timed region)
+    tuned = []
+    if not a.no_autotune and a.precision != "fp64":
+        for flow in flows:
+            try:
+                tuned.append(flow.autotune())
+            except Exception as exc:  # the last warm-up step ran in FP64: nothing to tune
+                tuned.append({"skipped": str(exc)})
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -423,6 +434,7 @@ def run_ours(a, rank, world, dist):
            "phases_ms_per_step": {k[3:]: v / a.steps for k, v in t.items() if k.startswith("ms_")},
            "gpu_launches": int(t["kernel_launches"]), "lnz_per_site_after": lnz, **extra}
     out["config"]["squeeze_group"] = kw["group"] or "library default (up to 8)"
+    out["config"]["autotune"] = tuned or "off"
     out["clocks"] = clk.summary()
     return out
 

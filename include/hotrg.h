@@ -237,11 +237,12 @@ int hotrg_timing_start(hotrg_ctx *c);
 int hotrg_timing_stop(hotrg_ctx *c, hotrg_timing *out);
 
 /* Autotuner of the squeeze GEMM's tile configuration: times the split-precision GEMM of the
- * last step's shape (M = P, N = chi P, K = P, on the operands that step left in the workspace)
- * for each candidate - k-block 64 or 32 (unless opts.kblock fixed it; 32 only for 6 passes), one
- * or two k-blocks per accumulator fold at k-block 32, and tile-raster groups of 4, 8, 16 or 32
- * M-tiles - keeps the fastest for the following steps and
- * drops captured step graphs. Call it after a steady-state split-precision step. Synchronises.
+ * last step's shape (M = P, N = chi P, K = P, on the operands that step left in the workspace;
+ * with opts.z2 the two-block GEMM of the last chunk, on its block descriptor) for each candidate -
+ * k-block 64 or 32 (unless opts.kblock fixed it; 32 only for 6 passes), one or two k-blocks per
+ * accumulator fold at k-block 32, and tile-raster groups of 4, 8, 16, 32 or 64 M-tiles - keeps the
+ * fastest for the following steps and drops captured step graphs. Call it after a steady-state
+ * split-precision step (its operands must still be in the workspace). Synchronises.
  * Errors: ESTATE (no split-precision step yet), EDEVICE. */
 typedef struct hotrg_tuning {
   int kblock;

@@ -37,6 +37,7 @@ struct hotrg_ctx {
     long long M = 0, N = 0, K = 0, ldk = 0;
     int npass = 0, nparts = 0, fmt = 0;
     float mult_b = 1.f;
+    const GemmBlocks* blk = nullptr;  // block-sparse: the descriptor of the last chunk (slot 0)
   } last_gemm;
   double timeout_s = 4.0;
   int max_sweeps = 40;  // Jacobi sweep limit of the eigensolver
@@ -842,6 +843,7 @@ int squeeze(hotrg_ctx* c, const Group& G, const Geom& g, const Geom& gn, int a, 
       c->last_gemm.nparts = planes;
       c->last_gemm.fmt = f16 ? 1 : 0;
       c->last_gemm.mult_b = bt_mult;
+      c->last_gemm.blk = nullptr;
     }
     // epilogue: O axes [m_0..m_{d-1}, j, n_0..n_{d-1}]
     std::vector<Ax> hist[kMaxD];  // axes of the input of each contraction of the chain
@@ -1016,6 +1018,16 @@ int squeeze_z2(hotrg_ctx* c, const Group& G, const Geom& g, const Geom& gn, int 
                                          static_cast<float*>(S0.O), ldO, P, ldO, ldz, npass, c->status, c->timeout_s,
                                          s, c->kblock, c->group_m, fold_group_for(c, npass), S0.z2blk, batp);
         if (rc) return rc;
+        // what the autotuner replays: slot 0's operands and block descriptor of this chunk
+        c->last_gemm.M = P;
+        c->last_gemm.N = ldO;
+        c->last_gemm.K = ldz;
+        c->last_gemm.ldk = ldz;
+        c->last_gemm.npass = npass;
+        c->last_gemm.nparts = planes;
+        c->last_gemm.fmt = f16 ? 1 : 0;
+        c->last_gemm.mult_b = bt_mult;
+        c->last_gemm.blk = S0.z2blk;
       } else {
         launch_gemm_f64(pl(S0.Y, y_plane, 1, S0.amax).p[0], ldz, pl(S0.Bt, bt_plane, 0, S0.amax).p[0], ldz,
                         static_cast<double*>(S0.O), ldO, P, ldO, ldz, s, S0.z2blk, batp);
@@ -1847,7 +1859,7 @@ int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
   if (lg.npass == 6) kbs = {32};
   else if (c->kblock_fixed) kbs = {c->kblock};
   else kbs = {64, 32};
-  const int groups[4] = {4, 8, 16, 32};
+  const int groups[5] = {4, 8, 16, 32, 64};
   struct Cand {
     int kb, fg, gm;
   };
@@ -1864,7 +1876,7 @@ int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
     for (int rep = 0; rep < 2; ++rep) {
       cudaEventRecord(e0, c->stream);
       const int r = launch_gemm_split(Y, lg.ldk, Bt, lg.ldk, static_cast<float*>(c->O), lg.N, lg.M, lg.N, lg.K,
-                                      lg.npass, c->status, c->timeout_s, c->stream, cd.kb, cd.gm, cd.fg);
+                                      lg.npass, c->status, c->timeout_s, c->stream, cd.kb, cd.gm, cd.fg, lg.blk);
       cudaEventRecord(e1, c->stream);
       float ms = 0.f;
       if (r || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {

@@ -70,6 +70,27 @@ def test_z2_fp16_flow_matches_oracle_golden_dcut5(precision):
         assert abs(lz[n - 1] - st["lnz"]) < 1e-7 * abs(st["lnz"]), n
 
 
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+def test_z2_autotune_replays_the_block_gemm_and_keeps_accuracy(precision):
+    """The autotuner on the block-sparse path: it times the last chunk's two-block GEMM (its
+    device descriptor) for every candidate, and the flow continues on the chosen configuration
+    within the mixed path's bound against the oracle."""
+    g = golden("flow_d4_b0.1497_h0_D5_n16")
+    with hotrg(4, 0.1497, 0.0, 5, precision=precision, fp64_steps=3, z2=True, max_steps=16) as f:
+        with pytest.raises(Exception):
+            f.autotune()  # no split-precision step yet
+        for _ in range(4):
+            f.step()
+        t = f.autotune()
+        assert t["kblock"] in (32, 64) and t["group_m"] in (4, 8, 16, 32, 64) and t["fold_group"] in (1, 2)
+        assert t["ms"] > 0
+        for _ in range(8):
+            f.step()
+        lnz = f.free_energy()[0][0]
+    bound = 1e-7 if precision == "fp16x3" else 3e-7   # BF16X3 alone from step 4: its own bound
+    assert abs(lnz - g["steps"][11]["lnz"]) < bound * abs(lnz)
+
+
 def test_z2_fp64_flow_matches_oracle_golden_dcut5():
     """Every step in FP64 through the blocked FP64 GEMM: the oracle's ln Z/N, ln c_n and Gram
     spectra to reassociation of FP64 sums."""
