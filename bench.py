@@ -352,7 +352,8 @@ def run_ours(a, rank, world, dist):
     # the squeeze GEMM's tile configuration for the steady shape, picked by the library's
     # autotuner on the last warm-up step's operands (outside the timed region)
     tuned = []
-    if not a.no_autotune and a.precision != "fp64":
+    # only when the last warm-up step ran the GEMM the timed steps run (a two-plane split step)
+    if not a.no_autotune and a.precision != "fp64" and a.warmup > max(a.fp64_steps, a.x6_steps):
         for flow in flows:
             try:
                 tuned.append(flow.autotune())

@@ -241,8 +241,9 @@ int hotrg_timing_stop(hotrg_ctx *c, hotrg_timing *out);
  * with opts.z2 the two-block GEMM of the last chunk, on its block descriptor) for each candidate -
  * k-block 64 or 32 (unless opts.kblock fixed it; 32 only for 6 passes), one or two k-blocks per
  * accumulator fold at k-block 32, and tile-raster groups of 4, 8, 16, 32 or 64 M-tiles - keeps the
- * fastest for the following steps and drops captured step graphs. Call it after a steady-state
- * split-precision step (its operands must still be in the workspace). Synchronises.
+ * fastest for the following steps and drops captured step graphs (tuned on a six-product GEMM, it
+ * keeps the k-block of the two-plane steps). Call it after a steady-state split-precision step
+ * (its operands must still be in the workspace). Synchronises.
  * Errors: ESTATE (no split-precision step yet), EDEVICE. */
 typedef struct hotrg_tuning {
   int kblock;

@@ -1898,7 +1898,9 @@ int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
   cudaEventDestroy(e1);
   const int rc2 = sync_check(c);
   if (rc2) return rc2;
-  c->kblock = best_kb;
+  // a six-product GEMM always runs 32-wide k-blocks: tuning it must not change the k-block of the
+  // two-plane steps that follow
+  if (lg.npass != 6) c->kblock = best_kb;
   c->group_m = best_g;
   c->fold_group = best_fg;
   for (int a = 0; a < kMaxD; ++a)
