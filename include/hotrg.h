@@ -111,6 +111,12 @@ typedef struct hotrg_opts {
                              launch over a group (its tile list spans the group's instances), and the
                              workspace holds that many copies of the per-step buffers. 1..256, capped
                              at batch; 0 (default) = 8; with derivatives or impurities always 1 */
+  int cta_group;          /* split modes: CTAs per squeeze-GEMM output tile. 2 = a pair of CTAs (a
+                             thread-block cluster of two SMs) per 256 x 256 tile, whose tcgen05
+                             MMAs read A rows from both CTAs and half of the B rows from each;
+                             1 = one CTA per 128 x 256 tile. Both give identical results. 0 = 1
+                             (default; the autotuner may change it), 1 or 2 fix it; EINVAL
+                             otherwise */
 } hotrg_opts;
 
 typedef struct hotrg_obs {
@@ -240,7 +246,8 @@ int hotrg_timing_stop(hotrg_ctx *c, hotrg_timing *out);
  * last step's shape (M = P, N = chi P, K = P, on the operands that step left in the workspace;
  * with opts.z2 the two-block GEMM of the last chunk, on its block descriptor) for each candidate -
  * k-block 64 or 32 (unless opts.kblock fixed it; 32 only for 6 passes), one or two k-blocks per
- * accumulator fold at k-block 32, and tile-raster groups of 4, 8, 16, 32 or 64 M-tiles - keeps the
+ * accumulator fold at k-block 32, tile-raster groups of 4, 8, 16, 32 or 64 M-tiles, and CTA pairs or
+ * single CTAs per output tile (unless opts.cta_group fixed it) - keeps the
  * fastest for the following steps and drops captured step graphs (tuned on a six-product GEMM, it
  * keeps the k-block of the two-plane steps). Call it after a steady-state split-precision step
  * (its operands must still be in the workspace). Synchronises.
@@ -250,6 +257,7 @@ typedef struct hotrg_tuning {
   int group_m;
   int fold_group;
   double ms;  /* best GEMM time of the timed shape */
+  int cta_group;
 } hotrg_tuning;
 int hotrg_autotune(hotrg_ctx *c, hotrg_tuning *out);
 

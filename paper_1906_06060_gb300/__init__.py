@@ -36,7 +36,8 @@ def _torch():
 
 
 def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=4.0, x6_steps=0, kblock=0,
-          graphs=True, fold_group=0, derivatives=False, impurities=False, z2=False, max_sweeps=0, group=0):
+          graphs=True, fold_group=0, derivatives=False, impurities=False, z2=False, max_sweeps=0, group=0,
+          cta_group=0):
     lib = _lib.load()
     o = _lib.Opts()
     lib.hotrg_opts_default(byref(o))
@@ -54,6 +55,7 @@ def _opts(precision="fp64", batch=1, fp64_steps=2, max_steps=64, wait_timeout_s=
     o.wait_timeout_s = float(wait_timeout_s)
     o.max_sweeps = int(max_sweeps)
     o.group = int(group)
+    o.cta_group = int(cta_group)
     return o
 
 
@@ -82,12 +84,15 @@ class HOTRG:
     max_sweeps: Jacobi sweep limit of the eigensolver (0: the default, 40).
     group: instances squeezed together, one GEMM launch per chunk for each group (0: up to 8; the
     workspace holds that many copies of the per-step buffers).
+    cta_group: CTAs per squeeze-GEMM output tile, 2 (a CTA pair, 256 x 256 tiles) or 1 (128 x 256);
+    0: 1, and the autotuner may change it.
     """
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,
                  max_steps: int = 64, stream=None, wait_timeout_s: float = 4.0, x6_steps: int = 0,
                  kblock: int = 0, graphs: bool = True, fold_group: int = 0, derivatives=False,
-                 impurities: bool = False, z2: bool = False, max_sweeps: int = 0, group: int = 0):
+                 impurities: bool = False, z2: bool = False, max_sweeps: int = 0, group: int = 0,
+                 cta_group: int = 0):
         torch = _torch()
         lib = _lib.load()
         betas = np.atleast_1d(np.asarray(beta, dtype=np.float64))
@@ -103,7 +108,7 @@ class HOTRG:
         self.beta = betas
         self.h = hs
         o = _opts(precision, batch, fp64_steps, max_steps, wait_timeout_s, x6_steps, kblock, graphs, fold_group,
-                  derivatives, impurities, z2, max_sweeps, group)
+                  derivatives, impurities, z2, max_sweeps, group, cta_group)
         n = c_size_t(0)
         check(lib.hotrg_workspace_size(d, Dcut, byref(o), byref(n)), "hotrg_workspace_size")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -211,11 +216,12 @@ class HOTRG:
         check(_lib.load().hotrg_state_load(self._ctx, blob, len(blob)), "hotrg_state_load")
 
     def autotune(self) -> dict:
-        """Pick the squeeze GEMM's k-block and tile raster for the current step shape (call after
-        a steady-state split-precision step)."""
+        """Pick the squeeze GEMM's k-block, tile raster and CTA group for the current step shape
+        (call after a steady-state split-precision step)."""
         t = _lib.Tuning()
         check(_lib.load().hotrg_autotune(self._ctx, byref(t)), "hotrg_autotune")
-        return {"kblock": t.kblock, "group_m": t.group_m, "fold_group": t.fold_group, "ms": t.ms}
+        return {"kblock": t.kblock, "group_m": t.group_m, "fold_group": t.fold_group, "ms": t.ms,
+                "cta_group": t.cta_group}
 
     def timing_start(self) -> None:
         check(_lib.load().hotrg_timing_start(self._ctx), "hotrg_timing_start")

@@ -19,7 +19,8 @@ class Opts(ctypes.Structure):
                 ("workspace", c_void_p), ("workspace_bytes", c_size_t), ("max_steps", c_int),
                 ("kblock", c_int), ("fold_group", c_int), ("derivatives", c_int), ("impurities", c_int),
                 ("z2", c_int), ("graphs", c_int),
-                ("wait_timeout_s", c_double), ("max_sweeps", c_int), ("group", c_int)]
+                ("wait_timeout_s", c_double), ("max_sweeps", c_int), ("group", c_int),
+                ("cta_group", c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -38,7 +39,8 @@ class Timing(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("kblock", c_int), ("group_m", c_int), ("fold_group", c_int), ("ms", c_double)]
+    _fields_ = [("kblock", c_int), ("group_m", c_int), ("fold_group", c_int), ("ms", c_double),
+                ("cta_group", c_int)]
 
 
 _SIGS = {

@@ -26,7 +26,7 @@
 // k-block's partial sum is folded into an FP32 register accumulator with round-to-nearest adds.
 //
 // Kernel structure (one CTA per SM, persistent over output tiles, 320 threads):
-//   warp 0      TMA producer: per k-block loads every bf16 plane of the 128 x BK A tile and
+//   warp 0      TMA producer: per k-block loads every 16-bit plane of the 128 x BK A tile and
 //               of the 256 x BK B tile (BK*2-byte swizzle) into one stage of a shared-memory
 //               ring, so the passes of a k-block reuse the same stage (BK = 64 or 32).
 //   warp 1      MMA issuer: one thread issues tcgen05.mma.cta_group::1.kind::f16 (M=128,
@@ -35,6 +35,17 @@
 //   warps 2-9   fold/epilogue: warp w reads TMEM lanes 32*(w%4).. (its hardware quadrant),
 //               columns 128*((w-2)/4).. of the buffer, adds them into 128 FP32 registers per
 //               thread and frees the buffer; after the last k-block it stores its 128 columns.
+//
+// CTA pairs (CG = 2, a thread-block cluster of two CTAs on two SMs, one 256 x 256 output tile):
+// each CTA stages its own 128 A rows and half (128) of the tile's B rows per k-block, so a stage
+// is 64 KB instead of 96 KB at BK = 64 (three stages fit instead of two) and each SM moves 2/3 of
+// the shared-memory operand bytes per MMA flop. The first CTA's thread issues
+// tcgen05.mma.cta_group::2 (M = 256): the tensor cores of both SMs read A from their own CTA and B
+// from both, and each CTA's TMEM receives its 128 rows. Both CTAs' TMA copies count on the first
+// CTA's stage barriers (which it arms for both); its commits reach the stage-free and TMEM-full
+// barriers of both CTAs (multicast); the fold warps of both report freed TMEM buffers to the first
+// CTA. Measured reason: a single CTA's 128 x 256 MMA chain, with operands already resident and
+// nothing else running, kept the tensor pipe busy about 2/3 of the time; pairs lift that limit.
 // Every mbarrier wait is bounded by a timeout; on expiry the CTA records ST_TIMEOUT, drains
 // the copies and MMAs it issued (waits bounded by max(timeout, 1 s): issued work always
 // completes, so a short caller limit never lets the CTA exit before it), frees TMEM and returns.
@@ -56,23 +67,26 @@ constexpr int TC_THREADS = 320;
 constexpr int TC_FOLD_THREADS = 256;  // warps 2-9
 constexpr uint32_t TMEM_COLS = 2 * TC_BN;
 
-// k-block width BK (bf16 elements per tile row): 64 -> 128-byte swizzle, 4 stages;
-// 32 -> 64-byte swizzle, 8 stages. The accumulator is folded once per k-block.
-template <int BK, int NPL>
+// k-block width BK (16-bit elements per tile row): 64 -> 128-byte swizzle, 32 -> 64-byte
+// swizzle. A stage holds every plane of one k-block of the CTA's A rows (128) and B rows (256, or
+// 128 for a CTA pair); as many stages as fit 216 KB, at most 6. The accumulator is folded once per
+// k-block (or fold group).
+template <int BK, int NPL, int CG>
 struct Cfg {
   static constexpr uint32_t A_TILE = TC_BM * BK * 2;
-  static constexpr uint32_t B_TILE = TC_BN * BK * 2;
+  static constexpr uint32_t B_TILE = (TC_BN / CG) * BK * 2;
   static constexpr uint32_t STAGE_BYTES = NPL * (A_TILE + B_TILE);
-  static constexpr int STAGES = (int)((216u * 1024u) / STAGE_BYTES) > 4 ? 4 : (int)((216u * 1024u) / STAGE_BYTES);
+  static constexpr int STAGES = (int)((216u * 1024u) / STAGE_BYTES) > 6 ? 6 : (int)((216u * 1024u) / STAGE_BYTES);
   static constexpr size_t SMEM = 1024 + STAGES * STAGE_BYTES + 256;
 };
 
 // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A and B format (bits 7-9, 10-12:
 // 1 = BF16, 0 = F16; A and B always of the same type), both K-major, N >> 3 at bits 17-22,
-// M >> 4 at bits 24-28.
-constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                                ((uint32_t)(TC_BM >> 4) << 24);
-constexpr uint32_t IDESC_F16 = (1u << 4) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+// M >> 4 at bits 24-28 (M = 128 for one CTA, 256 for a CTA pair: 128 rows in each).
+constexpr uint32_t idesc_for(bool f16, int cg) {
+  return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(TC_BN >> 3) << 17) |
+         ((uint32_t)((TC_BM * cg) >> 4) << 24);
+}
 
 struct TmapSet {
   CUtensorMap a[3];
@@ -109,7 +123,7 @@ struct TcParams {
   unsigned long long timeout_ns;
   int vec4;
   const GemmBlocks* blk;  // null: one dense product over M x N x K
-  uint32_t idesc;         // IDESC_BF16 or IDESC_F16 (both operands in the same format)
+  uint32_t idesc;         // idesc_for(fp16 operands, CTA group)
   // fp16 operands carry power-of-two scales 2^eA, 2^eB (see Planes): the epilogue multiplies by
   // 2^-(eA + eB). Null amax: no scaling.
   const unsigned* amaxA;
@@ -132,8 +146,9 @@ struct Blk {
 };
 
 // The (at most two) blocks of instance `inst`: from its device descriptor of a block-sparse
-// product (clamped to the operand extents), or the single dense block.
-template <int BK>
+// product (clamped to the operand extents), or the single dense block. Output tiles are
+// (128 CG) x 256: a CTA pair (CG = 2) computes 256 rows.
+template <int BK, int CG>
 __device__ __forceinline__ int load_blocks(const TcParams& p, int inst, Blk* b) {
   int nb = 1;
   if (p.blk) {
@@ -156,7 +171,7 @@ __device__ __forceinline__ int load_blocks(const TcParams& p, int inst, Blk* b) 
     b[0].num_kb = p.num_kb;
   }
   for (int i = 0; i < nb; ++i) {
-    b[i].num_m = (b[i].mc + TC_BM - 1) / TC_BM;
+    b[i].num_m = (b[i].mc + TC_BM * CG - 1) / (TC_BM * CG);
     b[i].num_n = (b[i].nc + TC_BN - 1) / TC_BN;
     b[i].tiles = b[i].num_m * b[i].num_n;
   }
@@ -217,6 +232,39 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
+// The same load for one CTA of a pair: the copy lands in this CTA's shared memory and its bytes
+// are counted on the barrier `bar` of the pair's first CTA (a shared::cluster address from mapa).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
+                                                 int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+// shared::cluster address of this CTA's shared-memory location `a` in cluster CTA `rank`
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of both CTAs of the cluster (release / acquire at cluster scope)
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// arrive on a barrier of another CTA of the cluster (shared::cluster address)
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// count `bytes` as arrived on a local barrier (a copy that will never be issued)
+__device__ __forceinline__ void mbar_complete_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -226,16 +274,45 @@ __device__ __forceinline__ void tc_fence_after() {
 // No "memory" clobber: the MMA reads shared memory the async proxy filled and writes TMEM; its
 // order against the mbarrier waits and tcgen05.commit around it is kept because all of these are
 // volatile asm statements, which the compiler does not reorder among themselves.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+// CG = 2: issued by the pair's first CTA; A rows and B rows come from both CTAs' shared memory
+// (the same offsets), each CTA's tensor memory receives its 128 rows of D.
+template <int CG>
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  if constexpr (CG == 1)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+// Arrive on `bar` once the MMAs this thread issued so far have completed. CG = 2: on the barrier
+// at the same offset in both CTAs of the pair.
+template <int CG>
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
+  if constexpr (CG == 1)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+  else
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"((uint16_t)3)
+        : "memory");
+}
+// the same, on this CTA's barrier only
+template <int CG>
+__device__ __forceinline__ void mma_commit_local(uint32_t bar) {
+  if constexpr (CG == 1)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
 }
 // Shared-memory matrix descriptor, K-major operand staged by TMA with a BK*2-byte swizzle:
 // start address >> 4 (bits 0-13), leading byte offset 16 B (unused for these layouts, bits
@@ -279,13 +356,13 @@ __device__ __forceinline__ void raster(int tile, int num_m, int num_n, int group
 // Tile -> (instance, block, M-tile, N-tile). Instances' tiles are numbered one after the other
 // (prefix[i] = first tile of instance i, for block-sparse launches), and inside an instance the
 // blocks' tiles one after the other.
-template <int BK>
+template <int BK, int CG>
 __device__ __forceinline__ void locate(const TcParams& p, const int* prefix, int tile, int& inst, Blk& bk, int& mt,
                                        int& nt) {
   Blk b[2];
   int local;
   if (!p.blk) {
-    load_blocks<BK>(p, 0, b);
+    load_blocks<BK, CG>(p, 0, b);
     inst = tile / b[0].tiles;
     local = tile - inst * b[0].tiles;
     bk = b[0];
@@ -298,7 +375,7 @@ __device__ __forceinline__ void locate(const TcParams& p, const int* prefix, int
     }
     inst = lo;
     local = tile - prefix[lo];
-    const int nb = load_blocks<BK>(p, inst, b);
+    const int nb = load_blocks<BK, CG>(p, inst, b);
     const int bi = (nb > 1 && local >= b[0].tiles) ? 1 : 0;
     if (bi) local -= b[0].tiles;
     bk = b[bi];
@@ -306,14 +383,16 @@ __device__ __forceinline__ void locate(const TcParams& p, const int* prefix, int
   raster(local, bk.num_m, bk.num_n, p.group_m, mt, nt);
 }
 
-template <int BK, int NPL, int NPASS, int FG>
+template <int BK, int NPL, int NPASS, int FG, int CG>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_split(const __grid_constant__ TmapSet maps, TcParams p) {
-  using C = Cfg<BK, NPL>;
+  using C = Cfg<BK, NPL, CG>;
   static_assert(FG == 1 || FG <= C::STAGES - 1, "a fold group leaves one stage to the producer");
+  static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair");
   constexpr int TC_STAGES = C::STAGES;
   constexpr uint32_t A_TILE = C::A_TILE, B_TILE = C::B_TILE, STAGE_BYTES = C::STAGE_BYTES;
   constexpr int TC_BK = BK;
+  constexpr int B_ROWS = TC_BN / CG;  // B rows this CTA stages per k-block
   static_assert(TC_STAGES >= 2, "ring needs two stages");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -324,6 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* peer_issued = reinterpret_cast<volatile int*>(tmem_slot + 2);  // CG = 2, first CTA
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t full0 = smem_u32(bars);
@@ -331,6 +411,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tfull0 = empty0 + 8 * TC_STAGES;
   const uint32_t tempty0 = tfull0 + 16;
   const uint32_t final_bar = tempty0 + 16;
+  // CTA pair: rank 0 issues the MMAs and owns the stage-full and TMEM-empty barriers both CTAs
+  // signal; every CTA walks the same tiles (one per cluster)
+  const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  const int cta0 = (int)blockIdx.x / CG, ncta = (int)gridDim.x / CG;
 
   __shared__ int s_prefix[kMaxGemmBatch + 1];
   __shared__ int s_total;
@@ -341,13 +426,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int t = 0;
       for (int i = 0; i < p.batch; ++i) {
         s_prefix[i] = t;
-        const int nb = load_blocks<BK>(p, i, b);
+        const int nb = load_blocks<BK, CG>(p, i, b);
         t += b[0].tiles + (nb > 1 ? b[1].tiles : 0);
       }
       s_prefix[p.batch] = t;
       s_total = t;
     } else {
-      load_blocks<BK>(p, 0, b);
+      load_blocks<BK, CG>(p, 0, b);
       s_total = b[0].tiles * p.batch;
     }
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -356,10 +441,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, TC_FOLD_THREADS / 32);
+      mbar_init(tempty0 + 8 * b, CG * TC_FOLD_THREADS / 32);
     }
     mbar_init(final_bar, 1);
     *abort_flag = 0;
+    *peer_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0 && lane < 2 * NPL) {
@@ -367,67 +453,96 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (CG == 1) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    } else {
+      // one warp of each CTA of the pair allocates collectively: the same columns in both
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (CG == 1) __syncthreads();
+  else cluster_sync();  // the peer's copies and arrivals target barriers initialised above
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
   const int total = s_total;
+  long long issued = 0;  // stages this CTA's producer filled (or began to fill)
 
   if (warp == 0) {
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      long long issued = 0;
       bool ok = !p.stall;
-      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+      for (int tile = cta0; tile < total && ok; tile += ncta) {
         int inst, mt, nt;
         Blk bk;
-        locate<BK>(p, s_prefix, tile, inst, bk, mt, nt);
+        locate<BK, CG>(p, s_prefix, tile, inst, bk, mt, nt);
+        const int arow = bk.m0 + mt * TC_BM * CG + (int)rank * TC_BM;
+        const int brow = bk.n0 + nt * TC_BN + (int)rank * B_ROWS;
         for (int kb = 0; kb < bk.num_kb; ++kb) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.timeout_ns)) { ok = false; break; }
           const uint32_t fb = full0 + 8 * stage;
-          mbar_expect_tx(fb, STAGE_BYTES);
           const int kx = bk.k0 + kb * TC_BK;
+          if constexpr (CG == 1) {
+            mbar_expect_tx(fb, STAGE_BYTES);
 #pragma unroll
-          for (int pl = 0; pl < NPL; ++pl) {
-            tma_load_3d(smem_u32(a_tile(stage, pl)), &maps.a[pl], fb, kx, bk.m0 + mt * TC_BM, inst);
-            tma_load_3d(smem_u32(b_tile(stage, pl)), &maps.b[pl], fb, kx, bk.n0 + nt * TC_BN, inst);
+            for (int pl = 0; pl < NPL; ++pl) {
+              tma_load_3d(smem_u32(a_tile(stage, pl)), &maps.a[pl], fb, kx, arow, inst);
+              tma_load_3d(smem_u32(b_tile(stage, pl)), &maps.b[pl], fb, kx, brow, inst);
+            }
+          } else {
+            // both CTAs' bytes count on the first CTA's barrier, which it arms for both
+            if (leader) mbar_expect_tx(fb, 2 * STAGE_BYTES);
+            const uint32_t rfb = mapa_rank(fb, 0);
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl) {
+              tma_load_3d_pair(smem_u32(a_tile(stage, pl)), &maps.a[pl], rfb, kx, arow, inst);
+              tma_load_3d_pair(smem_u32(b_tile(stage, pl)), &maps.b[pl], rfb, kx, brow, inst);
+            }
           }
           ++issued;
           if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
         }
       }
-      // Drain, on every exit path: the last min(STAGES, issued) loads must land before the CTA
-      // exits (a consumer that gave up may never have waited for them). Each stage holds at most
-      // one load in flight, and issued copies always complete, so these waits use a floor of one
-      // second whatever the caller's limit (after a normal run they return at once).
-      for (long long i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i)
-        mbar_wait(full0 + 8 * (int)(i % TC_STAGES), (uint32_t)((i / TC_STAGES) & 1), abort_flag,
-                  drain_ns(p.timeout_ns), false);
+      if constexpr (CG == 1) {
+        // Drain, on every exit path: the last min(STAGES, issued) loads must land before the CTA
+        // exits (a consumer that gave up may never have waited for them). Each stage holds at most
+        // one load in flight, and issued copies always complete, so these waits use a floor of one
+        // second whatever the caller's limit (after a normal run they return at once).
+        for (long long i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i)
+          mbar_wait(full0 + 8 * (int)(i % TC_STAGES), (uint32_t)((i / TC_STAGES) & 1), abort_flag,
+                    drain_ns(p.timeout_ns), false);
+      } else if (!leader) {
+        // the pair's drain runs on the first CTA, which needs to know how far this CTA got
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(mapa_rank(smem_u32(tmem_slot + 2), 0)),
+                     "r"((uint32_t)issued)
+                     : "memory");
+      }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       int stage = 0;
       uint32_t phase = 0;
       int buf = 0;
       uint32_t bphase = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+      for (int tile = cta0; tile < total && ok; tile += ncta) {
         int inst_, mt_, nt_;
         Blk bk_;
-        locate<BK>(p, s_prefix, tile, inst_, bk_, mt_, nt_);
+        locate<BK, CG>(p, s_prefix, tile, inst_, bk_, mt_, nt_);
         const int num_kb = bk_.num_kb;
         // Descriptors differ only in their start-address field (bits 0-13, address >> 4), so each
         // one is a base descriptor plus the tile's byte offset >> 4 (all offsets are multiples of
         // 16 bytes and the shared window is < 256 KB, so the field never carries over). Passes,
         // planes and the fold group are compile-time: a group's MMAs unroll into straight-line
-        // issue code with constant offsets.
+        // issue code with constant offsets. A pair's MMA reads the same offsets in both CTAs.
         const uint64_t desc_base = smem_desc<BK>(smem_u32(smem));
         const uint32_t idesc = p.idesc;
         constexpr uint32_t B_OFF = NPL * A_TILE;
@@ -457,38 +572,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint64_t db = desc_base + ((so[i] + B_OFF + (uint32_t)pass_plane_b(NPASS, ps) * B_TILE) >> 4);
 #pragma unroll
                 for (int k = 0; k < TC_BK / 16; ++k)
-                  mma_bf16(d_tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), idesc,
-                           (ps == 0 && i == 0 && k == 0) ? 0u : 1u);
+                  mma_f16<CG>(d_tmem, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), idesc,
+                              (ps == 0 && i == 0 && k == 0) ? 0u : 1u);
               }
             }
           }
           for (int i = 0; i < g; ++i) {
-            mma_commit(empty0 + 8 * stage);
+            mma_commit<CG>(empty0 + 8 * stage);  // frees the stage in both CTAs of a pair
             if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
           }
-          mma_commit(tfull0 + 8 * buf);
+          mma_commit<CG>(tfull0 + 8 * buf);
           if (++buf == 2) { buf = 0; bphase ^= 1; }
         }
       }
       // all MMAs issued by this thread complete before TMEM is released (issued MMAs always
       // complete: the wait has the drain's floor, not the caller's limit)
-      mma_commit(final_bar);
+      mma_commit_local<CG>(final_bar);
       mbar_wait(final_bar, 0, abort_flag, drain_ns(p.timeout_ns), false);
     }
   } else {
     const int q = warp & 3;          // TMEM lane quadrant this warp may access
     const int half = (warp - 2) >> 2;  // which 128 of the 256 columns
+    // where this warp reports a freed TMEM buffer: the MMA-issuing CTA's barriers (contiguous in
+    // its shared memory, so buffer b's barrier is 8 b bytes further in either address window)
+    const uint32_t tempty_dst = CG == 2 && !leader ? mapa_rank(tempty0, 0) : tempty0;
     int buf = 0;
     uint32_t bphase = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+    for (int tile = cta0; tile < total && ok; tile += ncta) {
       int num_kb;
       {
         // only the k-block count stays live through the k loop (the accumulator holds 128
         // registers); the tile is located again for the store
         int inst, mt, nt;
         Blk bk;
-        locate<BK>(p, s_prefix, tile, inst, bk, mt, nt);
+        locate<BK, CG>(p, s_prefix, tile, inst, bk, mt, nt);
         num_kb = bk.num_kb;
       }
       float acc[128];
@@ -516,13 +634,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty0 + 8 * buf);  // one arrive per warp
+        if (lane == 0) {  // one arrive per warp
+          const uint32_t bar = tempty_dst + 8 * buf;
+          if constexpr (CG == 1) mbar_arrive(bar);
+          else if (leader) mbar_arrive(bar);
+          else mbar_arrive_remote(bar);
+        }
         if (++buf == 2) { buf = 0; bphase ^= 1; }
       }
       if (!ok) break;
       int inst, mt, nt;
       Blk bk;
-      locate<BK>(p, s_prefix, tile, inst, bk, mt, nt);
+      locate<BK, CG>(p, s_prefix, tile, inst, bk, mt, nt);
       if (p.amaxA) {
         // undo the operands' power-of-two scales (exact): the exponents the operand builders used
         const float unscale =
@@ -531,7 +654,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 128; ++j) acc[j] *= unscale;
       }
-      const long long row = (long long)bk.m0 + (long long)mt * TC_BM + q * 32 + lane;
+      const long long row = (long long)bk.m0 + (long long)mt * TC_BM * CG + (long long)rank * TC_BM + q * 32 + lane;
       const long long col0 = (long long)bk.n0 + (long long)nt * TC_BN + half * 128;
       const long long row_end = (long long)bk.m0 + bk.mc, col_end = (long long)bk.n0 + bk.nc;
       if (row < row_end && col0 < col_end) {
@@ -548,12 +671,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0 && *abort_flag) atomic_status(p.status, ST_TIMEOUT);
-  if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
-                 : "memory");
+  if constexpr (CG == 1) {
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) atomic_status(p.status, ST_TIMEOUT);
+    if (warp == 1) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                   : "memory");
+    }
+  } else {
+    __syncwarp();
+    // every role of both CTAs is done, the pair's MMAs have completed, and the first CTA knows how
+    // many stages the other one filled
+    cluster_sync();
+    if (warp == 0 && lane == 0 && leader) {
+      // Drain for the pair, on every exit path: the last loads of both CTAs must land before either
+      // exits. The two producers' counts differ by at most STAGES (each waits on a stage the other's
+      // bytes completed), so only the last STAGES stages can still be in flight. A stage this CTA
+      // never armed gets armed for the other CTA's bytes alone; a stage the other CTA never filled
+      // has its share counted as arrived. Issued copies always complete: waits with the drain floor.
+      const long long iP = *peer_issued;
+      const long long hi = issued > iP ? issued : iP;
+      for (long long i = (hi > TC_STAGES ? hi - TC_STAGES : 0); i < hi; ++i) {
+        const uint32_t fb = full0 + 8 * (int)(i % TC_STAGES);
+        if (i >= issued) mbar_expect_tx(fb, STAGE_BYTES);
+        else if (i >= iP) mbar_complete_tx(fb, STAGE_BYTES);
+        mbar_wait(fb, (uint32_t)((i / TC_STAGES) & 1), abort_flag, drain_ns(p.timeout_ns), false);
+      }
+    }
+    cluster_sync();
+    if (threadIdx.x == 0 && *abort_flag) atomic_status(p.status, ST_TIMEOUT);
+    if (warp == 1) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                   : "memory");
+    }
   }
 }
 
@@ -603,32 +755,65 @@ bool make_map(CUtensorMap* m, const __nv_bfloat16* ptr, long long rows, long lon
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Encodes the tensor maps and launches one kernel variant. The maps' box width, the stage slot
-// sizes and the expected transaction bytes all derive from the same compile-time BK and NPL,
-// so a TMA copy can never be larger than the stage slot it lands in.
-template <int BK, int NPL, int NPASS, int FG>
-int launch_variant(int grid, const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
+// SM count of the current device (cached per device)
+int num_sms();
+
+// Encodes the tensor maps and launches one kernel variant. The maps' box sizes, the stage slot
+// sizes and the expected transaction bytes all derive from the same compile-time BK, NPL and CG,
+// so a TMA copy can never be larger than the stage slot it lands in. Persistent launch: as many
+// CTAs (CG = 2: clusters of two) as can be resident at once, one per SM, and no more than the
+// tiles (tiles < 0: counted on the device).
+template <int BK, int NPL, int NPASS, int FG, int CG>
+int launch_variant(long long tiles, const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                    long long ldb, long long a_inst, long long b_inst, const TcParams& p, cudaStream_t s) {
-  static_assert(Cfg<BK, NPL>::STAGE_BYTES == NPL * (TC_BM + TC_BN) * BK * 2, "stage holds exactly the boxes");
+  using Cf = Cfg<BK, NPL, CG>;
+  static_assert(Cf::STAGE_BYTES == NPL * (TC_BM + TC_BN / CG) * BK * 2, "stage holds exactly the boxes");
   TmapSet maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int i = 0; i < NPL; ++i)
     if (!make_map(&maps.a[i], A.p[i], p.M, p.K, lda, p.batch, a_inst, TC_BM, BK, A.fmt == 1) ||
-        !make_map(&maps.b[i], B.p[i], p.N, p.K, ldb, p.batch, b_inst, TC_BN, BK, B.fmt == 1))
+        !make_map(&maps.b[i], B.p[i], p.N, p.K, ldb, p.batch, b_inst, TC_BN / CG, BK, B.fmt == 1))
       return HOTRG_EDEVICE;
+  auto kern = k_gemm_split<BK, NPL, NPASS, FG, CG>;
   // the dynamic shared-memory limit is a per-device attribute of the kernel: set it once on each
-  // device this variant launches on
-  static std::atomic<bool> attr[kMaxDevices];
+  // device this variant launches on; so is the number of resident CTAs or clusters
+  static std::atomic<int> resident[kMaxDevices];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HOTRG_EDEVICE;
-  if (!attr[dev].load()) {
-    if (cudaFuncSetAttribute(k_gemm_split<BK, NPL, NPASS, FG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg<BK, NPL>::SMEM) != cudaSuccess)
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CG;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = Cf::SMEM;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = CG > 1 ? 1 : 0;
+  int n = resident[dev].load();
+  if (n <= 0) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM) != cudaSuccess)
       return HOTRG_EDEVICE;
-    attr[dev].store(true);
+    if (CG == 1) {
+      n = num_sms();
+    } else {
+      cfg.gridDim = dim3((unsigned)(CG * std::max(1, num_sms() / CG)));
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return HOTRG_EDEVICE;
+      }
+    }
+    resident[dev].store(n);
   }
-  k_gemm_split<BK, NPL, NPASS, FG><<<grid, TC_THREADS, Cfg<BK, NPL>::SMEM, s>>>(maps, p);
-  return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_EDEVICE;
+  const long long units = tiles >= 0 && tiles < n ? (tiles > 0 ? tiles : 1) : n;
+  cfg.gridDim = dim3((unsigned)(units * CG));
+  if (cudaLaunchKernelEx(&cfg, kern, maps, p) != cudaSuccess) {
+    cudaGetLastError();
+    return HOTRG_EDEVICE;
+  }
+  return HOTRG_OK;
 }
 
 // SM count of the current device (cached per device)
@@ -655,8 +840,10 @@ int num_sms() {
 int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Planes<__nv_bfloat16>& B,
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
                       int npass, int* status, double timeout_s, cudaStream_t s, int bk, int group_m,
-                      int fold_group, const GemmBlocks* blk, const GemmBatch* bat, bool stall) {
+                      int fold_group, const GemmBlocks* blk, const GemmBatch* bat, bool stall, int cta_group) {
   if (bk != 32 && bk != 64) return HOTRG_EINVAL;
+  if (cta_group == 0) cta_group = kDefaultCtaGroup;
+  if (cta_group != 1 && cta_group != 2) return HOTRG_EINVAL;
   if (group_m < 1 || group_m > 64 || fold_group < 1) return HOTRG_EINVAL;
   if (M < TC_BM || N < TC_BN || K < 64 || (npass != 1 && npass != 3 && npass != 4 && npass != 6))
     return HOTRG_EINVAL;
@@ -694,7 +881,7 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
   p.timeout_ns = (unsigned long long)(timeout_s * 1e9);
   p.vec4 = ((ldc % 4) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
   p.blk = blk;
-  p.idesc = A.fmt == 1 ? IDESC_F16 : IDESC_BF16;
+  p.idesc = idesc_for(A.fmt == 1, cta_group);
   p.amaxA = A.fmt == 1 ? A.amax : nullptr;
   p.amaxB = A.fmt == 1 ? B.amax : nullptr;
   p.multA = A.amax_mult;
@@ -703,16 +890,19 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
   p.c_inst = bat ? bat->c_inst : 0;
   p.amax_inst = bat ? bat->amax_inst : 0;
   p.stall = stall ? 1 : 0;
-  const long long tiles = (long long)p.num_m * p.num_n * batch;
+  // output tiles: 128 x 256 per CTA, 256 x 256 per CTA pair
+  const long long tiles = (long long)((M + (long long)TC_BM * cta_group - 1) / ((long long)TC_BM * cta_group)) *
+                          p.num_n * batch;
   if (tiles > 0x7fffffffLL) return HOTRG_EINVAL;
-  // with device-side blocks the tile count is known only on the device: one CTA per SM
-  const int grid = blk ? num_sms() : (int)(tiles < num_sms() ? tiles : num_sms());
   // supported variants (fold groups beyond a variant's maximum are clamped to it)
   const int fg = std::max(1, std::min(fold_group, max_fold_group(npass, bk)));
+  // with device-side blocks the tile count is known only on the device
+  const long long t = blk ? -1 : tiles;
   int rc = HOTRG_EINVAL;
-#define HOTRG_GEMM_VARIANT(BK_, NPL_, NP_, FG_)                                          \
-  if (bk == BK_ && nplanes == NPL_ && npass == NP_ && fg == FG_)                        \
-    rc = launch_variant<BK_, NPL_, NP_, FG_>(grid, A, lda, B, ldb, a_inst, b_inst, p, s);
+#define HOTRG_GEMM_VARIANT(BK_, NPL_, NP_, FG_)                                                        \
+  if (bk == BK_ && nplanes == NPL_ && npass == NP_ && fg == FG_)                                      \
+    rc = cta_group == 2 ? launch_variant<BK_, NPL_, NP_, FG_, 2>(t, A, lda, B, ldb, a_inst, b_inst, p, s) \
+                        : launch_variant<BK_, NPL_, NP_, FG_, 1>(t, A, lda, B, ldb, a_inst, b_inst, p, s);
   HOTRG_GEMM_VARIANT(64, 1, 1, 1)
   HOTRG_GEMM_VARIANT(64, 1, 1, 2)
   HOTRG_GEMM_VARIANT(64, 2, 3, 1)

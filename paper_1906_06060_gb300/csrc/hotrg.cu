@@ -30,6 +30,8 @@ struct hotrg_ctx {
   int d = 0, Dcut = 0, batch = 1, precision = HOTRG_FP64, fp64_steps = 2, x6_steps = 0, max_steps = 64;
   int kblock = 64;
   bool kblock_fixed = false;  // the caller fixed the k-block (else the autotuner may change it)
+  int cta_group = 1;          // CTAs per squeeze-GEMM output tile (1 or 2)
+  bool cta_group_fixed = false;
   int group_m = 16;
   int fold_group = 0;  // k-blocks per accumulator fold (0: one)
   // shape of the last split-precision GEMM launched (what the autotuner times)
@@ -767,7 +769,7 @@ int squeeze(hotrg_ctx* c, const Group& G, const Geom& g, const Geom& gn, int a, 
       const int rc = launch_gemm_split(blocks(S0.Y, y_plane, ablk, 1, S0.amax), ld,
                                        blocks(S0.Bt, bt_plane, bblk, 0, S0.amax), ld, reinterpret_cast<float*>(C),
                                        ldO, P, ldO, K, npass, c->status, c->timeout_s, s, c->kblock, c->group_m,
-                                       fold_group_for(c, npass), nullptr, batp);
+                                       fold_group_for(c, npass), nullptr, batp, false, c->cta_group);
       if (rc) return rc;
       if (c->timing) c->t_gemm_tflops += 2.0 * P * (double)ldO * K * npass * ng;
     } else {
@@ -1016,7 +1018,8 @@ int squeeze_z2(hotrg_ctx* c, const Group& G, const Geom& g, const Geom& gn, int 
       if constexpr (mixed) {
         const int rc = launch_gemm_split(pl(S0.Y, y_plane, 1, S0.amax), ldz, pl(S0.Bt, bt_plane, 0, S0.amax), ldz,
                                          static_cast<float*>(S0.O), ldO, P, ldO, ldz, npass, c->status, c->timeout_s,
-                                         s, c->kblock, c->group_m, fold_group_for(c, npass), S0.z2blk, batp);
+                                         s, c->kblock, c->group_m, fold_group_for(c, npass), S0.z2blk, batp, false,
+                                         c->cta_group);
         if (rc) return rc;
         // what the autotuner replays: slot 0's operands and block descriptor of this chunk
         c->last_gemm.M = P;
@@ -1124,6 +1127,7 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   if (opt->precision < HOTRG_FP64 || opt->precision > HOTRG_FP16X4) return HOTRG_EINVAL;
   if (opt->derivatives < 0 || opt->derivatives > 2) return HOTRG_EINVAL;
   if (opt->max_sweeps < 0 || opt->max_sweeps > 1000) return HOTRG_EINVAL;
+  if (opt->cta_group < 0 || opt->cta_group > 2) return HOTRG_EINVAL;
   if (opt->group < 0) return HOTRG_EINVAL;
   std::vector<double> vb(opt->batch), vh(opt->batch);
   for (int i = 0; i < opt->batch; ++i) {
@@ -1164,6 +1168,8 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->group = group_for(opt);
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->max_sweeps = opt->max_sweeps > 0 ? opt->max_sweeps : 40;
+  c->cta_group = opt->cta_group ? opt->cta_group : kDefaultCtaGroup;
+  c->cta_group_fixed = opt->cta_group != 0;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
   c->h = vh;
@@ -1860,23 +1866,28 @@ int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
   else if (c->kblock_fixed) kbs = {c->kblock};
   else kbs = {64, 32};
   const int groups[5] = {4, 8, 16, 32, 64};
+  std::vector<int> cgs;
+  if (c->cta_group_fixed) cgs = {c->cta_group};
+  else cgs = {2, 1};
   struct Cand {
-    int kb, fg, gm;
+    int kb, fg, gm, cg;
   };
   std::vector<Cand> cands;
-  for (int kb : kbs)
-    for (int fg = 1; fg <= (kb == 32 ? 2 : 1); ++fg)
-      for (int gm : groups) cands.push_back({kb, fg, gm});
+  for (int cg : cgs)
+    for (int kb : kbs)
+      for (int fg = 1; fg <= (kb == 32 ? 2 : 1); ++fg)
+        for (int gm : groups) cands.push_back({kb, fg, gm, cg});
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HOTRG_EDEVICE;
   double best = 1e300;
-  int best_kb = c->kblock, best_g = c->group_m, best_fg = std::max(1, c->fold_group);
+  int best_kb = c->kblock, best_g = c->group_m, best_fg = std::max(1, c->fold_group), best_cg = c->cta_group;
   for (const Cand& cd : cands) {
     double t_min = 1e300;
     for (int rep = 0; rep < 2; ++rep) {
       cudaEventRecord(e0, c->stream);
       const int r = launch_gemm_split(Y, lg.ldk, Bt, lg.ldk, static_cast<float*>(c->O), lg.N, lg.M, lg.N, lg.K,
-                                      lg.npass, c->status, c->timeout_s, c->stream, cd.kb, cd.gm, cd.fg, lg.blk);
+                                      lg.npass, c->status, c->timeout_s, c->stream, cd.kb, cd.gm, cd.fg, lg.blk,
+                                      nullptr, false, cd.cg);
       cudaEventRecord(e1, c->stream);
       float ms = 0.f;
       if (r || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -1892,6 +1903,7 @@ int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
       best_kb = cd.kb;
       best_g = cd.gm;
       best_fg = cd.fg;
+      best_cg = cd.cg;
     }
   }
   cudaEventDestroy(e0);
@@ -1903,6 +1915,7 @@ int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
   if (lg.npass != 6) c->kblock = best_kb;
   c->group_m = best_g;
   c->fold_group = best_fg;
+  c->cta_group = best_cg;
   for (int a = 0; a < kMaxD; ++a)
     if (c->graph_exec[a]) {
       cudaGraphExecDestroy(c->graph_exec[a]);  // captured with the previous choice
@@ -1913,6 +1926,7 @@ int hotrg_autotune(hotrg_ctx* c, hotrg_tuning* out) {
     out->group_m = best_g;
     out->fold_group = best_fg;
     out->ms = best;
+    out->cta_group = best_cg;
   }
   return HOTRG_OK;
 }

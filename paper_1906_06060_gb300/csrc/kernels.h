@@ -196,9 +196,12 @@ int launch_gemm_split(const Planes<__nv_bfloat16>& A, long long lda, const Plane
                       long long ldb, float* C, long long ldc, long long M, long long N, long long K,
                       int npass, int* status, double timeout_s, cudaStream_t s, int bk = 64,
                       int group_m = 16, int fold_group = 1, const GemmBlocks* blk = nullptr,
-                      const GemmBatch* bat = nullptr, bool stall = false);
+                      const GemmBatch* bat = nullptr, bool stall = false, int cta_group = 0);
 // stall (test of the bounded waits): the kernel's producer issues no copies, so every CTA's first
 // wait for a stage runs out after timeout_s and the launch ends with ST_TIMEOUT in *status.
+// cta_group: 1 = one CTA per 128 x 256 output tile, 2 = a CTA pair (cluster of two) per 256 x 256
+// tile with tcgen05 cta_group::2 MMAs, each CTA staging half the B rows; 0 = kDefaultCtaGroup.
+constexpr int kDefaultCtaGroup = 1;
 // Largest fold group the kernel variant for (npass, bk) accepts.
 int max_fold_group(int npass, int bk);
 void launch_split_rows(const float* X, long long ldx, long long rows, long long cols,

@@ -297,6 +297,40 @@ def test_grouped_squeeze_is_bitwise_the_instance_by_instance_squeeze(precision, 
         assert res[0][3] == other[3]
 
 
+@pytest.mark.parametrize("precision,fp64_steps,x6_steps,kblock,fold_group,batch", [
+    ("fp16x3", 2, 4, 64, 1, 3),   # six-product steps 3-4, then FP16X3; a group of three instances
+    ("bf16x4", 2, 0, 32, 2, 1),   # four products, 32-wide stages, two per fold
+    ("bf16x3", 1, 0, 32, 1, 2),
+])
+def test_cta_pairs_and_single_ctas_give_bitwise_identical_flows(precision, fp64_steps, x6_steps, kblock, fold_group,
+                                                               batch):
+    """The squeeze GEMM on CTA pairs (256 x 256 output tiles, cta_group::2 MMAs reading A rows from
+    both CTAs and half of the B rows from each) against one CTA per 128 x 256 tile: every output
+    element is the same sequence of K = 16 MMA steps and register folds, so the flows agree bit for
+    bit, ragged tiles (P = 625 rows: the last pair tile has 113 rows, the last single tile 113)
+    included."""
+    betas = [0.1497, 0.16, 0.14][:batch]
+    hs = [0.0, 1e-5, -2e-5][:batch]
+    res = []
+    for cg in (2, 1):
+        with flow(4, betas, hs, 5, precision=precision, fp64_steps=fp64_steps, x6_steps=x6_steps, kblock=kblock,
+                  fold_group=fold_group, cta_group=cg, group=batch) as f:
+            for _ in range(6):
+                f.step()
+            res.append((f.free_energy()[0], [f.ln_norms(i) for i in range(batch)], f.get_tensor(batch - 1)))
+    assert np.array_equal(res[0][0], res[1][0])
+    for a, b in zip(res[0][1], res[1][1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(res[0][2], res[1][2])
+
+
+def test_invalid_cta_group_is_refused():
+    from paper_1906_06060_gb300 import HotrgError, _lib
+    with pytest.raises(HotrgError) as e:
+        flow(4, 0.15, 0.0, 4, precision="bf16x3", cta_group=3)
+    assert e.value.code == _lib.HOTRG_EINVAL
+
+
 def test_group_larger_than_batch_and_invalid_group():
     from paper_1906_06060_gb300 import HotrgError, _lib
     with flow(4, [0.15, 0.16], 0.0, 4, group=64) as f:  # capped at the batch
@@ -390,7 +424,7 @@ def test_autotune_picks_a_candidate_and_keeps_accuracy():
             f.step()
         t = f.autotune()
         assert t["kblock"] in (32, 64) and t["group_m"] in (4, 8, 16, 32, 64) and t["ms"] > 0
-        assert t["fold_group"] in (1, 2)
+        assert t["fold_group"] in (1, 2) and t["cta_group"] in (1, 2)
         for _ in range(4):
             f.step()
         lnz = f.free_energy()[0][0]

@@ -172,6 +172,25 @@ def test_z2_grouped_squeeze_is_bitwise_the_instance_by_instance_squeeze(precisio
         assert np.array_equal(res[0][2], other[2])
 
 
+@pytest.mark.parametrize("Dcut,precision,fp64_steps,x6_steps,batch", [(5, "fp16x3", 2, 4, 3), (8, "bf16x3", 2, 0, 1)])
+def test_z2_cta_pairs_and_single_ctas_give_bitwise_identical_flows(Dcut, precision, fp64_steps, x6_steps, batch):
+    """Block-sparse squeeze on CTA pairs (256-row tiles of each block, both CTAs reading their rows
+    at the block's offsets) against one CTA per 128-row tile: bit for bit, over instances with their
+    own block descriptors and (Dcut = 8) the benchmark's block shapes scaled down."""
+    betas = [0.1497, 0.16, 0.14][:batch]
+    res = []
+    for cg in (2, 1):
+        with hotrg(4, betas, 0.0, Dcut, precision=precision, fp64_steps=fp64_steps, x6_steps=x6_steps, z2=True,
+                   group=batch, cta_group=cg, max_steps=7) as f:
+            for _ in range(7 if Dcut == 5 else 5):
+                f.step()
+            res.append((f.free_energy()[0], [f.ln_norms(i) for i in range(batch)], f.get_tensor(batch - 1)))
+    assert np.array_equal(res[0][0], res[1][0])
+    for a, b in zip(res[0][1], res[1][1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(res[0][2], res[1][2])
+
+
 def test_z2_batched_instances_match_separate_runs():
     """Each instance carries its own parity counts. Dcut = 5: no cut of these flows splits a
     degenerate multiplet (at Dcut = 6 one does, and the Gram's batch-dependent summation order
