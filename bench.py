@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--kblock", type=int, default=64)
     ap.add_argument("--fold-group", type=int, default=0)
+    ap.add_argument("--cta-group", type=int, default=0, choices=[0, 1, 2],
+                    help="CTAs per squeeze-GEMM output tile: 2 = CTA pairs (256 x 256 tiles), 1 = single CTAs "
+                         "(128 x 256); 0 = the library default (pairs for the block-sparse squeeze), autotuned")
     ap.add_argument("--x6-steps", type=int, default=6)
     ap.add_argument("--workload", default="flow", choices=["flow", "scan", "deriv", "accuracy", "gemm", "phase"])
     ap.add_argument("--temps", default="6.650355,6.650375",
@@ -157,7 +160,7 @@ def workload_config(a):
             "fp64_steps": a.fp64_steps, "x6_steps": a.x6_steps, "kblock": a.kblock,
             "z2_block_sparse": use_z2(a),
             "contexts": [{"instances": len(g[0]), "z2": g[2]} for g in groups(a)],
-            "fold_group": a.fold_group,
+            "fold_group": a.fold_group, "cta_group": a.cta_group,
             "l2": "inputs larger than L2 (T 800 MB fp64, GEMM operands several GB per step)",
             "parallelism": "replicas" if a.gpus > 1 else "single GPU"}
 
@@ -332,7 +335,8 @@ def run_ours(a, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
-    kw = dict(precision=a.precision, fp64_steps=a.fp64_steps, x6_steps=a.x6_steps, kblock=a.kblock, fold_group=a.fold_group, stream=stream)
+    kw = dict(precision=a.precision, fp64_steps=a.fp64_steps, x6_steps=a.x6_steps, kblock=a.kblock, fold_group=a.fold_group,
+              cta_group=a.cta_group, stream=stream)
 
     def barrier():
         if dist:
@@ -621,7 +625,7 @@ def e2e(a):
     nsteps = a.warmup + a.steps
     t0 = time.perf_counter()
     flow = HOTRG(4, a.beta, a.h, a.dcut, precision=a.precision, fp64_steps=a.fp64_steps, x6_steps=a.x6_steps,
-                 kblock=a.kblock, fold_group=a.fold_group, z2=use_z2(a))
+                 kblock=a.kblock, fold_group=a.fold_group, cta_group=a.cta_group, z2=use_z2(a))
     flops = 0.0
     dims = [2, 2, 2, 2]
     records = []

@@ -114,8 +114,9 @@ typedef struct hotrg_opts {
   int cta_group;          /* split modes: CTAs per squeeze-GEMM output tile. 2 = a pair of CTAs (a
                              thread-block cluster of two SMs) per 256 x 256 tile, whose tcgen05
                              MMAs read A rows from both CTAs and half of the B rows from each;
-                             1 = one CTA per 128 x 256 tile. Both give identical results. 0 = 1
-                             (default; the autotuner may change it), 1 or 2 fix it; EINVAL
+                             1 = one CTA per 128 x 256 tile. Both give identical results. 0 =
+                             default: 2 with opts.z2, else 1 (the faster at the Dcut = 10
+                             shapes); the autotuner may change it. 1 or 2 fix it; EINVAL
                              otherwise */
 } hotrg_opts;
 

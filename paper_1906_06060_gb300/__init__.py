@@ -85,7 +85,7 @@ class HOTRG:
     group: instances squeezed together, one GEMM launch per chunk for each group (0: up to 8; the
     workspace holds that many copies of the per-step buffers).
     cta_group: CTAs per squeeze-GEMM output tile, 2 (a CTA pair, 256 x 256 tiles) or 1 (128 x 256);
-    0: 1, and the autotuner may change it.
+    0: pairs with z2, else single CTAs, and the autotuner may change it.
     """
 
     def __init__(self, d: int, beta, h, Dcut: int, precision: str = "fp64", fp64_steps: int = 2,

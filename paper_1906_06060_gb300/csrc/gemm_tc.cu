@@ -41,11 +41,14 @@
 // is 64 KB instead of 96 KB at BK = 64 (three stages fit instead of two) and each SM moves 2/3 of
 // the shared-memory operand bytes per MMA flop. The first CTA's thread issues
 // tcgen05.mma.cta_group::2 (M = 256): the tensor cores of both SMs read A from their own CTA and B
-// from both, and each CTA's TMEM receives its 128 rows. Both CTAs' TMA copies count on the first
-// CTA's stage barriers (which it arms for both); its commits reach the stage-free and TMEM-full
-// barriers of both CTAs (multicast); the fold warps of both report freed TMEM buffers to the first
-// CTA. Measured reason: a single CTA's 128 x 256 MMA chain, with operands already resident and
-// nothing else running, kept the tensor pipe busy about 2/3 of the time; pairs lift that limit.
+// from both, and each CTA's TMEM receives its 128 rows. The first CTA's producer issues the TMA
+// copies of both CTAs (the second CTA's land in its shared memory through mapa addresses) and all
+// bytes count on the first CTA's stage barriers, so stage hand-over never crosses SMs; the MMA
+// commits free the stage there and reach the TMEM-full barriers of both CTAs (multicast); the
+// fold warps of both report freed TMEM buffers to the first CTA. Measured reasons: a single CTA's
+// 128 x 256 MMA chain, with operands resident and nothing else running, kept the tensor pipe busy
+// about 2/3 of the time (pairs: about 3/4); and a pair whose second CTA issued its own copies,
+// counted remotely on the first CTA's barrier, lost a quarter of its rate to the cross-SM hand-over.
 // Every mbarrier wait is bounded by a timeout; on expiry the CTA records ST_TIMEOUT, drains
 // the copies and MMAs it issued (waits bounded by max(timeout, 1 s): issued work always
 // completes, so a short caller limit never lets the CTA exit before it), frees TMEM and returns.
@@ -232,8 +235,8 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
-// The same load for one CTA of a pair: the copy lands in this CTA's shared memory and its bytes
-// are counted on the barrier `bar` of the pair's first CTA (a shared::cluster address from mapa).
+// The same load for a CTA pair, issued by the pair's first CTA: `dst` is a shared::cluster address in
+// either CTA (mapa for the second), the bytes count on the first CTA's barrier `bar`.
 __device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
                                                  int z) {
   asm volatile(
@@ -260,10 +263,6 @@ __device__ __forceinline__ void cluster_sync() {
 // arrive on a barrier of another CTA of the cluster (shared::cluster address)
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t bar) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-// count `bytes` as arrived on a local barrier (a copy that will never be issued)
-__device__ __forceinline__ void mbar_complete_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -403,7 +402,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile int* peer_issued = reinterpret_cast<volatile int*>(tmem_slot + 2);  // CG = 2, first CTA
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t full0 = smem_u32(bars);
@@ -445,7 +443,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     mbar_init(final_bar, 1);
     *abort_flag = 0;
-    *peer_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0 && lane < 2 * NPL) {
@@ -473,12 +470,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
 
   const int total = s_total;
-  long long issued = 0;  // stages this CTA's producer filled (or began to fill)
 
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       int stage = 0;
       uint32_t phase = 0;
+      long long issued = 0;  // stages this thread filled
       bool ok = !p.stall;
       for (int tile = cta0; tile < total && ok; tile += ncta) {
         int inst, mt, nt;
@@ -498,33 +495,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               tma_load_3d(smem_u32(b_tile(stage, pl)), &maps.b[pl], fb, kx, brow, inst);
             }
           } else {
-            // both CTAs' bytes count on the first CTA's barrier, which it arms for both
-            if (leader) mbar_expect_tx(fb, 2 * STAGE_BYTES);
-            const uint32_t rfb = mapa_rank(fb, 0);
+            // this CTA fills the stage in both CTAs of the pair (the second CTA's copies land at the
+            // same offsets of its shared memory); all bytes count on this CTA's barrier
+            mbar_expect_tx(fb, 2 * STAGE_BYTES);
 #pragma unroll
             for (int pl = 0; pl < NPL; ++pl) {
-              tma_load_3d_pair(smem_u32(a_tile(stage, pl)), &maps.a[pl], rfb, kx, arow, inst);
-              tma_load_3d_pair(smem_u32(b_tile(stage, pl)), &maps.b[pl], rfb, kx, brow, inst);
+              const uint32_t sa = smem_u32(a_tile(stage, pl)), sb = smem_u32(b_tile(stage, pl));
+              tma_load_3d_pair(sa, &maps.a[pl], fb, kx, arow, inst);
+              tma_load_3d_pair(sb, &maps.b[pl], fb, kx, brow, inst);
+              tma_load_3d_pair(mapa_rank(sa, 1), &maps.a[pl], fb, kx, arow + TC_BM, inst);
+              tma_load_3d_pair(mapa_rank(sb, 1), &maps.b[pl], fb, kx, brow + B_ROWS, inst);
             }
           }
           ++issued;
           if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
         }
       }
-      if constexpr (CG == 1) {
-        // Drain, on every exit path: the last min(STAGES, issued) loads must land before the CTA
-        // exits (a consumer that gave up may never have waited for them). Each stage holds at most
-        // one load in flight, and issued copies always complete, so these waits use a floor of one
-        // second whatever the caller's limit (after a normal run they return at once).
-        for (long long i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i)
-          mbar_wait(full0 + 8 * (int)(i % TC_STAGES), (uint32_t)((i / TC_STAGES) & 1), abort_flag,
-                    drain_ns(p.timeout_ns), false);
-      } else if (!leader) {
-        // the pair's drain runs on the first CTA, which needs to know how far this CTA got
-        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(mapa_rank(smem_u32(tmem_slot + 2), 0)),
-                     "r"((uint32_t)issued)
-                     : "memory");
-      }
+      // Drain, on every exit path: the last min(STAGES, issued) loads must land before the CTA (or
+      // either CTA of a pair: the second waits at the final cluster barrier) exits - a consumer that
+      // gave up may never have waited for them. Each stage holds at most one load in flight, and
+      // issued copies always complete, so these waits use a floor of one second whatever the
+      // caller's limit (after a normal run they return at once).
+      for (long long i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i)
+        mbar_wait(full0 + 8 * (int)(i % TC_STAGES), (uint32_t)((i / TC_STAGES) & 1), abort_flag,
+                  drain_ns(p.timeout_ns), false);
     }
   } else if (warp == 1) {
     if (lane == 0 && leader) {
@@ -578,7 +572,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
           }
           for (int i = 0; i < g; ++i) {
-            mma_commit<CG>(empty0 + 8 * stage);  // frees the stage in both CTAs of a pair
+            mma_commit_local<CG>(empty0 + 8 * stage);  // frees the stage (its copies are issued here)
             if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
           }
           mma_commit<CG>(tfull0 + 8 * buf);
@@ -681,24 +675,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     __syncwarp();
-    // every role of both CTAs is done, the pair's MMAs have completed, and the first CTA knows how
-    // many stages the other one filled
-    cluster_sync();
-    if (warp == 0 && lane == 0 && leader) {
-      // Drain for the pair, on every exit path: the last loads of both CTAs must land before either
-      // exits. The two producers' counts differ by at most STAGES (each waits on a stage the other's
-      // bytes completed), so only the last STAGES stages can still be in flight. A stage this CTA
-      // never armed gets armed for the other CTA's bytes alone; a stage the other CTA never filled
-      // has its share counted as arrived. Issued copies always complete: waits with the drain floor.
-      const long long iP = *peer_issued;
-      const long long hi = issued > iP ? issued : iP;
-      for (long long i = (hi > TC_STAGES ? hi - TC_STAGES : 0); i < hi; ++i) {
-        const uint32_t fb = full0 + 8 * (int)(i % TC_STAGES);
-        if (i >= issued) mbar_expect_tx(fb, STAGE_BYTES);
-        else if (i >= iP) mbar_complete_tx(fb, STAGE_BYTES);
-        mbar_wait(fb, (uint32_t)((i / TC_STAGES) & 1), abort_flag, drain_ns(p.timeout_ns), false);
-      }
-    }
+    // every role of both CTAs is done: the pair's copies have landed (the first CTA's drain) and its
+    // MMAs have completed, so neither CTA's shared or tensor memory is still in use
     cluster_sync();
     if (threadIdx.x == 0 && *abort_flag) atomic_status(p.status, ST_TIMEOUT);
     if (warp == 1) {

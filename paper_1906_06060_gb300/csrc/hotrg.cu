@@ -1168,7 +1168,9 @@ int hotrg_init(hotrg_ctx** out, int d, double beta, double h, int Dcut, const ho
   c->group = group_for(opt);
   c->timeout_s = opt->wait_timeout_s > 0 ? opt->wait_timeout_s : 4.0;
   c->max_sweeps = opt->max_sweeps > 0 ? opt->max_sweeps : 40;
-  c->cta_group = opt->cta_group ? opt->cta_group : kDefaultCtaGroup;
+  // the faster of the two at the Dcut = 10 shapes: pairs for the two-block squeeze (A rows of a block
+  // fit L2), single CTAs for the dense one
+  c->cta_group = opt->cta_group ? opt->cta_group : (c->z2 ? 2 : 1);
   c->cta_group_fixed = opt->cta_group != 0;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->beta = vb;
