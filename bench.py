@@ -277,9 +277,19 @@ def run_reference(a, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def traffic_from_profile(z2):
+def effective_cta_group(a, tuned):
+    """CTAs per squeeze-GEMM tile in the timed steps: the autotuner's choice, else --cta-group,
+    else the library default (pairs for the block-sparse squeeze)."""
+    for t in tuned or []:
+        if isinstance(t, dict) and "cta_group" in t:
+            return int(t["cta_group"])
+    return a.cta_group or (2 if use_z2(a) else 1)
+
+
+def traffic_from_profile(z2, cta_group):
     """Per-launch DRAM bytes of the squeeze GEMM (dense or block-sparse launch) from the
-    committed ncu summary, valid only if the kernel source is unchanged since the capture."""
+    committed ncu summary, valid only if the kernel source is unchanged since the capture and the
+    launch uses the capture's CTA group (pairs and single CTAs move different bytes)."""
     try:
         with open(PROFILE[bool(z2)]) as fh:
             text = fh.read()
@@ -292,7 +302,7 @@ def traffic_from_profile(z2):
         if "=" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("gemm_tc_sha") != sha:
+    if kv.get("gemm_tc_sha") != sha or kv.get("cta_group", "1") != str(cta_group):
         return None
     try:
         return float(kv["traffic_bytes_per_launch_full"])
@@ -402,7 +412,7 @@ def run_ours(a, rank, world, dist):
             "frac": achieved / peak,
             # the committed ncu summaries are of the steady-step three-product GEMM (fp16 and bf16
             # planes move the same bytes), scaled to Dcut = 10
-            "traffic": (traffic_from_profile(use_z2(a))
+            "traffic": (traffic_from_profile(use_z2(a), effective_cta_group(a, tuned))
                         if (a.workload == "flow" and a.dcut == 10 and a.precision in ("bf16x3", "fp16x3"))
                         else None),
             "peak_source": f"{src} bf16 sustained (kernel timed inside long steps)",

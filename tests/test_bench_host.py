@@ -63,10 +63,24 @@ def test_traffic_is_read_only_while_the_kernel_source_is_unchanged(tmp_path, mon
     monkeypatch.setattr(bench, "GEMM_SRC", str(src))
     monkeypatch.setattr(bench, "PROFILE", {True: _profile(tmp_path, sha, "1.2300e+10"),
                                            False: str(tmp_path / "missing.md")})
-    assert bench.traffic_from_profile(True) == pytest.approx(1.23e10)
-    assert bench.traffic_from_profile(False) is None          # no summary
+    assert bench.traffic_from_profile(True, 1) == pytest.approx(1.23e10)  # no cta_group line: single CTAs
+    assert bench.traffic_from_profile(True, 2) is None        # counters taken with the other CTA group
+    assert bench.traffic_from_profile(False, 1) is None       # no summary
     src.write_bytes(b"// kernel source, changed\n")
-    assert bench.traffic_from_profile(True) is None           # counters taken on another kernel
+    assert bench.traffic_from_profile(True, 1) is None        # counters taken on another kernel
+
+
+def test_effective_cta_group_follows_the_autotuner_then_the_flag_then_the_default(monkeypatch):
+    class A:
+        cta_group = 0
+    a = A()
+    monkeypatch.setattr(bench, "use_z2", lambda _: True)
+    assert bench.effective_cta_group(a, [{"kblock": 64, "cta_group": 1}]) == 1
+    assert bench.effective_cta_group(a, "off") == 2          # block-sparse default: pairs
+    monkeypatch.setattr(bench, "use_z2", lambda _: False)
+    assert bench.effective_cta_group(a, []) == 1             # dense default: single CTAs
+    a.cta_group = 2
+    assert bench.effective_cta_group(a, []) == 2
 
 
 def test_committed_profiles_parse():
