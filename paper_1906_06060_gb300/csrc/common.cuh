@@ -120,4 +120,32 @@ __device__ __forceinline__ void store_planes(const Planes<__nv_bfloat16>& o, lon
 }
 __device__ __forceinline__ void store_planes(const Planes<double>& o, long long i, double x) { o.p[0][i] = x; }
 
+// The same with the fp16 scale 2^e read once by the caller (plane_scale), for kernels that store
+// many entries per thread; the plane pointers are indexed with compile-time indices only.
+__device__ __forceinline__ float plane_scale(const Planes<__nv_bfloat16>& o) {
+  return o.fmt ? pow2f(f16_scale_exponent(plane_bound(o.amax, o.amax_mult))) : 1.f;
+}
+__device__ __forceinline__ float plane_scale(const Planes<double>&) { return 1.f; }
+__device__ __forceinline__ void store_planes_sc(const Planes<__nv_bfloat16>& o, long long i, float x, float sc) {
+  if (o.fmt) {
+    const float xs = x * sc;
+    const __half hi = __float2half_rn(xs);
+    const __half lo = __float2half_rn(xs - __half2float(hi));
+    o.p[0][i] = __ushort_as_bfloat16(__half_as_ushort(hi));
+    if (o.nparts > 1) o.p[1][i] = __ushort_as_bfloat16(__half_as_ushort(lo));
+    return;
+  }
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  o.p[0][i] = h;
+  if (o.nparts > 1) {
+    const float r1 = x - __bfloat162float(h);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    o.p[1][i] = mid;
+    if (o.nparts > 2) o.p[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+  }
+}
+__device__ __forceinline__ void store_planes_sc(const Planes<double>& o, long long i, double x, float) {
+  o.p[0][i] = x;
+}
+
 }  // namespace hotrg

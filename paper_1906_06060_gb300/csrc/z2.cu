@@ -151,52 +151,64 @@ __global__ void k_z2_advance(int* ev, const int* ev_new, int batch, unsigned tra
 }
 
 // A operand of one chunk, parity-blocked: Y[rank(m)][kcol(k)] = X[R(k) + C(m)] where
-// parity(m) + parity(k) = pi (the other entries of X are zero and not stored).
+// parity(m) + parity(k) = pi (the other entries of X are zero and not stored). A block covers 32
+// columns k and Y_MT x 32 rows m: warp 0 decomposes its 32 k (offset R(k), operand column, parity),
+// warps 1..Y_MT its rows (offset C(m), rank, parity) at the same time, in 32-bit index arithmetic
+// (P < 2^31); then every thread issues its 4 Y_MT loads before its stores (the tile's rows share
+// L1 sectors where X is contiguous along m).
+constexpr int Y_MT = 4;
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(256) k_build_y_z2(const Tin* __restrict__ X, Planes<Tout> out,
                                                     long long ld, Geom g, int a, const int* __restrict__ rank_tab,
                                                     const int* __restrict__ kcol_tab, const Z2Layout* Lp,
                                                     const int* pi_ptr) {
-  __shared__ long long Rk[32], Cm[32];
-  __shared__ int rowr[32], colk[32], parm[32], park[32];
-  const long long P = g.P;
+  __shared__ long long Rk[32], Cm[32 * Y_MT];
+  __shared__ int rowr[32 * Y_MT], colk[32], parm[32 * Y_MT], park[32];
+  const int P = (int)g.P;
+  const long long PP = g.P;
   const int ncls0 = Lp->ncls[0];
   const int pi = *pi_ptr;
-  const long long m0 = (long long)blockIdx.y * 32, k0 = (long long)blockIdx.x * 32;
-  if (threadIdx.y == 0) {
-    const long long k = k0 + threadIdx.x, m = m0 + threadIdx.x;
-    long long rk = 0, cm = 0;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int m0 = blockIdx.y * 32 * Y_MT, k0 = blockIdx.x * 32;
+  if (ty == 0) {
+    const int k = k0 + tx;
+    long long rk = 0;
     for (int b = 0; b < g.d; ++b) {
-      const long long kb = (k / g.Sn[b]) % g.D[b];
-      const long long mb = (m / g.Sn[b]) % g.D[b];
-      if (b == a) { rk += kb * g.Sn[b]; cm += mb * g.Sn[b] * P; }
-      else        { rk += kb * g.Sn[b] * P; cm += mb * g.Sn[b]; }
+      const int sb = (int)g.Sn[b];
+      const long long kb = (k / sb) % g.D[b];
+      rk += b == a ? kb * sb : kb * sb * PP;
     }
-    Rk[threadIdx.x] = rk;
-    Cm[threadIdx.x] = cm;
+    Rk[tx] = rk;
+    colk[tx] = k < P ? kcol_tab[k] : 0;
+    park[tx] = k < P ? (rank_tab[k] >= ncls0 ? 1 : 0) : 0;
+  } else if (ty <= Y_MT) {
+    const int r = (ty - 1) * 32 + tx;
+    const int m = m0 + r;
+    long long cm = 0;
+    for (int b = 0; b < g.d; ++b) {
+      const int sb = (int)g.Sn[b];
+      const long long mb = (m / sb) % g.D[b];
+      cm += b == a ? mb * sb * PP : mb * sb;
+    }
+    Cm[r] = cm;
     const int rm = m < P ? rank_tab[m] : 0;
-    const int ck = k < P ? kcol_tab[k] : 0;
-    rowr[threadIdx.x] = rm;
-    parm[threadIdx.x] = rm >= ncls0 ? 1 : 0;
-    colk[threadIdx.x] = ck;
-    park[threadIdx.x] = k < P ? (rank_tab[k] >= ncls0 ? 1 : 0) : 0;
+    rowr[r] = rm;
+    parm[r] = rm >= ncls0 ? 1 : 0;
   }
   __syncthreads();
-  // the thread's four loads first, then the stores (reads along m share L1 sectors between the
-  // tile's rows when X is contiguous along m)
-  ZAcc<Tout> v[4];
-  bool w[4];
-  const long long k = k0 + threadIdx.x;
+  ZAcc<Tout> v[4 * Y_MT];
+  bool w[4 * Y_MT];
+  const int k = k0 + tx;
+  const float sc = plane_scale(out);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = threadIdx.y + 8 * q;
-    const long long m = m0 + r;
-    w[q] = m < P && k < P && (parm[r] ^ park[threadIdx.x]) == pi;
-    v[q] = w[q] ? (ZAcc<Tout>)X[Rk[threadIdx.x] + Cm[r]] : (ZAcc<Tout>)0;
+  for (int q = 0; q < 4 * Y_MT; ++q) {
+    const int r = ty + 8 * q;
+    w[q] = m0 + r < P && k < P && (parm[r] ^ park[tx]) == pi;
+    v[q] = w[q] ? (ZAcc<Tout>)X[Rk[tx] + Cm[r]] : (ZAcc<Tout>)0;
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (w[q]) store_planes(out, (long long)rowr[threadIdx.y + 8 * q] * ld + colk[threadIdx.x], v[q]);
+  for (int q = 0; q < 4 * Y_MT; ++q)
+    if (w[q]) store_planes_sc(out, (long long)rowr[ty + 8 * q] * ld + colk[tx], v[q], sc);
 }
 
 // B operand, parity-blocked: Bt[colpos(j, n)][kcol(k)] = sum_x U3[j][k_c3][x] Tt[n][k | c3 := x]
@@ -464,7 +476,7 @@ void launch_z2_advance(int* ev, const int* ev_new, int batch, unsigned trans_mas
 template <class Tin, class Tout>
 void launch_build_y_z2(const Tin* X, const Planes<Tout>& out, long long ld, Geom g, int a,
                        const int* rank_tab, const int* kcol_tab, const Z2Layout* L, const int* pi, cudaStream_t s) {
-  dim3 grid((unsigned)((g.P + 31) / 32), (unsigned)((g.P + 31) / 32));
+  dim3 grid((unsigned)((g.P + 31) / 32), (unsigned)((g.P + 32 * Y_MT - 1) / (32 * Y_MT)));
   k_build_y_z2<Tin, Tout><<<grid, dim3(32, 8), 0, s>>>(X, out, ld, g, a, rank_tab, kcol_tab, L, pi);
   count_launches(1);
 }
