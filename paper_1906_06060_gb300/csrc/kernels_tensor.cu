@@ -385,44 +385,69 @@ __global__ void __launch_bounds__(256) k_build_bt(const Tin* __restrict__ Tt, Pl
 
 // ---------------------------------------------------------------------------- A operand
 // Y[m][k] = X[R(k) + C(m)], R(k) = sum_{b!=a} k_b Sn_b P + k_a Sn_a, C(m) = sum_{b!=a} m_b Sn_b + m_a Sn_a P.
-// Tiles of 32 x 32; when a is the fastest slot the source is contiguous along k (no transpose),
-// otherwise along m (transpose through shared memory).
+// Tiles of 32 columns x (32 kYMT) rows; when a is the fastest slot the source is contiguous along k
+// (no transpose), otherwise along m (transpose through shared memory, one 32 x 32 tile at a time).
+// Warp 0 decomposes the tile's 32 k, warps 1..kYMT its rows, at the same time, in 32-bit index
+// arithmetic (P < 2^31); the fp16 scale of the planes is read once per thread.
+constexpr int kYMT = 4;
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(256) k_build_y(const Tin* __restrict__ X, Planes<Tout> out, long long ld,
                                                  Geom g, int a) {
   using Acc = AccT<Tout>;
   __shared__ Acc tile[32][33];
-  __shared__ long long Rk[32], Cm[32];
-  const long long P = g.P;
-  const long long m0 = (long long)blockIdx.y * 32, k0 = (long long)blockIdx.x * 32;
-  if (threadIdx.y == 0) {
-    const long long k = k0 + threadIdx.x, m = m0 + threadIdx.x;
-    long long rk = 0, cm = 0;
+  __shared__ long long Rk[32], Cm[32 * kYMT];
+  const int P = (int)g.P;
+  const long long PP = g.P;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int m0 = blockIdx.y * 32 * kYMT, k0 = blockIdx.x * 32;
+  if (ty == 0) {
+    const int k = k0 + tx;
+    long long rk = 0;
     for (int b = 0; b < g.d; ++b) {
-      const long long kb = (k / g.Sn[b]) % g.D[b];
-      const long long mb = (m / g.Sn[b]) % g.D[b];
-      if (b == a) { rk += kb * g.Sn[b]; cm += mb * g.Sn[b] * P; }
-      else        { rk += kb * g.Sn[b] * P; cm += mb * g.Sn[b]; }
+      const int sb = (int)g.Sn[b];
+      const long long kb = (k / sb) % g.D[b];
+      rk += b == a ? kb * sb : kb * sb * PP;
     }
-    Rk[threadIdx.x] = rk;
-    Cm[threadIdx.x] = cm;
+    Rk[tx] = rk;
+  } else if (ty <= kYMT) {
+    const int r = (ty - 1) * 32 + tx;
+    const int m = m0 + r;
+    long long cm = 0;
+    for (int b = 0; b < g.d; ++b) {
+      const int sb = (int)g.Sn[b];
+      const long long mb = (m / sb) % g.D[b];
+      cm += b == a ? mb * sb * PP : mb * sb;
+    }
+    Cm[r] = cm;
   }
   __syncthreads();
-  const bool a_fast = (a == g.d - 1);
-  if (a_fast) {
-    for (int r = threadIdx.y; r < 32; r += 8) {
-      const long long m = m0 + r, k = k0 + threadIdx.x;
-      if (m < P && k < P) store_planes(out, m * ld + k, (Acc)X[Rk[threadIdx.x] + Cm[r]]);
+  const float sc = plane_scale(out);
+  const int k = k0 + tx;
+  if (a == g.d - 1) {
+    // contiguous along k: the thread's 4 kYMT loads first, then the stores
+    Acc v[4 * kYMT];
+#pragma unroll
+    for (int q = 0; q < 4 * kYMT; ++q) {
+      const int m = m0 + ty + 8 * q;
+      v[q] = (m < P && k < P) ? (Acc)X[Rk[tx] + Cm[ty + 8 * q]] : (Acc)0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4 * kYMT; ++q) {
+      const int m = m0 + ty + 8 * q;
+      if (m < P && k < P) store_planes_sc(out, (long long)m * ld + k, v[q], sc);
     }
   } else {
-    for (int r = threadIdx.y; r < 32; r += 8) {  // r indexes k, threadIdx.x indexes m
-      const long long k = k0 + r, m = m0 + threadIdx.x;
-      if (m < P && k < P) tile[r][threadIdx.x] = (Acc)X[Rk[r] + Cm[threadIdx.x]];
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += 8) {  // r indexes m, threadIdx.x indexes k
-      const long long m = m0 + r, k = k0 + threadIdx.x;
-      if (m < P && k < P) store_planes(out, m * ld + k, tile[threadIdx.x][r]);
+    for (int t = 0; t < kYMT; ++t) {
+      for (int r = ty; r < 32; r += 8) {  // r indexes k, tx indexes m
+        const int kr = k0 + r, m = m0 + t * 32 + tx;
+        if (m < P && kr < P) tile[r][tx] = (Acc)X[Rk[r] + Cm[t * 32 + tx]];
+      }
+      __syncthreads();
+      for (int r = ty; r < 32; r += 8) {  // r indexes m, tx indexes k
+        const int m = m0 + t * 32 + r;
+        if (m < P && k < P) store_planes_sc(out, (long long)m * ld + k, tile[tx][r], sc);
+      }
+      __syncthreads();
     }
   }
 }
@@ -647,7 +672,7 @@ void launch_build_bt(const Tin* Tt, const Planes<Tout>& out, long long ld, Geom 
 template <class Tin, class Tout>
 void launch_build_y(const Tin* X, const Planes<Tout>& out, long long ld, Geom g, int a,
                     cudaStream_t s) {
-  dim3 grid((unsigned)((g.P + 31) / 32), (unsigned)((g.P + 31) / 32));
+  dim3 grid((unsigned)((g.P + 31) / 32), (unsigned)((g.P + 32 * kYMT - 1) / (32 * kYMT)));
   k_build_y<Tin, Tout><<<grid, dim3(32, 8), 0, s>>>(X, out, ld, g, a);
   count_launches(1);
 }
