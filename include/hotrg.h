@@ -319,13 +319,14 @@ int hotrg_gemm_split_f16(const float *A, long long lda, const float *Bt, long lo
                          long long ldc, long long M, long long N, long long K, int npass, int kblock,
                          int fold_group, void *scratch, size_t scratch_bytes, void *stream);
 
-/* Failure-detection probe of the bounded device-side waits (the paper has no counterpart): one
- * launch of the tensor-core GEMM (one 128 x 256 tile, BF16X3) whose copy-issuing thread issues no
- * copies, so that the first wait for operand data can never be satisfied. The wait gives up after
- * timeout_s (0 < timeout_s <= 10), the kernel records the timeout, frees its tensor memory and
- * returns; nothing is left in flight. `scratch` (device, 256-B aligned) holds at least
- * hotrg_gemm_wait_probe_bytes() bytes. Synchronises `stream` and returns the launch's status:
- * HOTRG_ETIMEOUT when the waits work as intended. Other errors: EINVAL, EDEVICE. */
+/* Failure-detection probe of the bounded device-side waits (the paper has no counterpart): two
+ * launches of the tensor-core GEMM (BF16X3, one output tile: first on one CTA, then on a CTA pair)
+ * whose copy-issuing thread issues no copies, so that the first wait for operand data can never
+ * be satisfied. The waits give up after timeout_s (0 < timeout_s <= 10), each kernel records the
+ * timeout, frees its tensor memory and returns; nothing is left in flight. `scratch` (device,
+ * 256-B aligned) holds at least hotrg_gemm_wait_probe_bytes() bytes. Synchronises `stream`;
+ * returns HOTRG_ETIMEOUT when both launches timed out as intended, else the first other status.
+ * Other errors: EINVAL, EDEVICE. */
 size_t hotrg_gemm_wait_probe_bytes(void);
 int hotrg_gemm_wait_probe(double timeout_s, void *scratch, size_t scratch_bytes, void *stream);
 

@@ -2066,11 +2066,16 @@ int hotrg_gemm_wait_probe(double timeout_s, void* scratch, size_t scratch_bytes,
     p += round_up(N * K * 2, kAlign);
   }
   float* C = reinterpret_cast<float*>(p);
-  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return HOTRG_EDEVICE;
-  const int rc = launch_gemm_split(Ap, K, Bp, K, C, N, M, N, K, 3, status, timeout_s, s, 64, 16, 1, nullptr, nullptr,
-                                   true);
-  if (rc) return rc;
-  return hotrg_gemm_status(scratch, stream);
+  // one CTA per tile, then a CTA pair (whose waits span both CTAs and end at a cluster barrier)
+  for (int cg = 1; cg <= 2; ++cg) {
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return HOTRG_EDEVICE;
+    const int rc = launch_gemm_split(Ap, K, Bp, K, C, N, M, N, K, 3, status, timeout_s, s, 64, 16, 1, nullptr,
+                                     nullptr, true, cg);
+    if (rc) return rc;
+    const int st = hotrg_gemm_status(scratch, stream);
+    if (st != HOTRG_ETIMEOUT) return st;
+  }
+  return HOTRG_ETIMEOUT;
 }
 
 int hotrg_gemm_status(const void* scratch, void* stream) {

@@ -1,8 +1,8 @@
 """Failure detection through the C ABI: every failure is made on the host or by a wait limit
 that runs out, never by a GPU fault.
 
-* HOTRG_ETIMEOUT: a probe launch of the tensor-core GEMM whose copy-issuing thread issues no
-  copies, so that a wait is on data that never arrives (a short limit alone does not do it: a
+* HOTRG_ETIMEOUT: probe launches of the tensor-core GEMM (one CTA, then a CTA pair) whose
+  copy-issuing thread issues no copies, so that a wait is on data that never arrives (a short limit alone does not do it: a
   wait that the hardware lets block for a while is satisfied by real copies first). The wait
   gives up, the kernel frees its tensor memory and returns; the host reads the status word.
 * HOTRG_ENUMERIC: a tensor with a NaN entry, loaded from the host (its Gram matrices and the norm
@@ -43,10 +43,10 @@ def _fresh_context_still_matches_the_oracle():
 
 
 def test_wait_that_nothing_satisfies_gives_etimeout_and_a_usable_device():
-    """The GEMM's bounded waits: a probe launch whose copy-issuing thread issues no copies, so the
-    first wait for operand data can never be satisfied. It must give up after its limit, record
-    HOTRG_ETIMEOUT and leave the device usable: a normal GEMM on the same stream afterwards is
-    correct, and so is a new flow context."""
+    """The GEMM's bounded waits: probe launches (one CTA per tile, then a CTA pair) whose
+    copy-issuing thread issues no copies, so the first wait for operand data can never be
+    satisfied. Each must give up after its limit, record HOTRG_ETIMEOUT and leave the device
+    usable: a normal GEMM on the same stream afterwards is correct, and so is a new flow context."""
     import torch
     from ctypes import c_void_p
     from paper_1906_06060_gb300 import _lib, gemm_split
