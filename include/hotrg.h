@@ -279,7 +279,8 @@ const char *hotrg_strerror(int code);
  * width of a pipeline stage (0 = 64; the 6-pass GEMM always uses 32). fold_group: stages whose
  * products share one tensor-core accumulator before it is folded into FP32 registers with
  * round-to-nearest adds (0 = 1; larger values are clamped to what the kernel variant's ring
- * allows, at most 2).
+ * allows, at most 2). The launch uses one CTA per 128 x 256 output tile (the flow contexts can
+ * also run CTA pairs: opts.cta_group).
  * Enqueued on `stream`; not synchronised. Errors: EINVAL (sizes, npass, kblock, alignment),
  * EDEVICE. */
 size_t hotrg_gemm_scratch_bytes(long long M, long long N, long long K);
